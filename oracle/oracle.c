@@ -1,0 +1,454 @@
+/*
+ * CPU oracle for the frequency-domain stationary-phase (SPA) mode sum of
+ * "Fast and Fourier: EMRI waveforms in the frequency domain" (arXiv 2307.12585).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct
+ * reference that the CUDA path is checked against.  Only tests, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header, table or constant generator with the CUDA library.
+ *
+ * Arithmetic: IEEE binary64 throughout.  The only extension is double-double
+ * (error-free transformations of Dekker 1971 / Knuth TAOCP vol. 2) for the
+ * phase 2 pi f t - Phi(t), whose terms reach 1e7 rad while the result is
+ * needed to ~1e-12 rad; build with -ffp-contract=off so that no implicit FMA
+ * changes roundings.
+ *
+ * What is computed (one waveform):
+ *  1. Every knot series (Phi_phi, Phi_r, Omega_phi, Omega_r, Re A, Im A of
+ *     each voice) is an independent not-a-knot cubic spline in t (Sec. 2.1:
+ *     amplitudes, phases and frequencies are interpolated with not-a-knot
+ *     cubic splines on the sparse trajectory).  Solved densely: the K x K
+ *     system for the knot second derivatives by Gaussian elimination with
+ *     partial pivoting (one LU, one solve per series).
+ *  2. Voices (Eq. 2): mode (l,m,n) gives H_V(t) = prefactor A(t) Y_lm(theta,phi)
+ *     and Phi_V = m Phi_phi + n Phi_r (Eq. 1 with k = 0, Schwarzschild);
+ *     with conj_partners each m >= 0 mode also gives the voice (l,-m,-n) with
+ *     amplitude (-1)^l conj(A) (Schwarzschild reflection symmetry).
+ *  3. Voice frequency F_V(t) = (m Omega_phi + n Omega_r)/(2 pi) (Sec. 2.2);
+ *     per spline segment it is the cubic of Eq. 6.
+ *  4. For a signed frequency g, every real root t_j of F_V(t) = g in the
+ *     trajectory contributes H_V(t_j) exp(i[2 pi g t_j - Phi_V(t_j)
+ *     - sgn(Fdot_j) pi/4]) / sqrt|Fdot_j|: the Fourier integral of Eq. 3
+ *     with the phase expanded to second order (Eq. 4) and the Fresnel
+ *     integral done exactly; it is the standard-SPA limit of Eq. 10 (Fddot
+ *     -> 0), summed over the N roots of Eq. 9.  Roots are bracketed on the
+ *     monotone pieces of each segment (split where Fdot = 0, at most one
+ *     turnover per segment in practice, Sec. 2.2) and found by bisection
+ *     to the last bit.  A root with Fdot == 0 exactly contributes 0.
+ *  5. Output at f > 0 (h = h+ - i hx, Eq. 1; Fourier sign of Eq. 3):
+ *     h+(f) = [H(f) + conj H(-f)]/2,  hx(f) = i [H(f) - conj H(-f)]/2.
+ *
+ * Ownership of a frequency by a monotone piece [tau_a, tau_b) with end
+ * frequencies Fa, Fb: increasing pieces own [Fa, Fb), decreasing pieces own
+ * (Fb, Fa].  Knot frequencies are always (m*Om_phi_k + n*Om_r_k)/(2 pi)
+ * evaluated in that order, so every frequency crossing of the whole track is
+ * counted exactly once.  Interior turnover frequencies come from the cubic.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_TWO_PI_HI 6.283185307179586232
+#define OR_TWO_PI_LO 2.449293598294706e-16
+#define OR_QPI_HI 0.7853981633974483096
+#define OR_QPI_LO 3.061616997868383e-17
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------ */
+/* double-double helpers (Dekker 1971; Knuth TAOCP 4.2.2)               */
+/* ------------------------------------------------------------------ */
+typedef struct { double hi, lo; } dd_t;
+
+static dd_t two_sum(double a, double b) {
+  dd_t r; double s = a + b; double bb = s - a;
+  r.hi = s; r.lo = (a - (s - bb)) + (b - bb); return r;
+}
+static dd_t two_prod(double a, double b) {
+  dd_t r; r.hi = a * b; r.lo = fma(a, b, -r.hi); return r;
+}
+static dd_t dd_norm(double hi, double lo) { return two_sum(hi, lo); }
+static dd_t dd_add(dd_t a, dd_t b) {
+  dd_t s = two_sum(a.hi, b.hi);
+  double lo = s.lo + a.lo + b.lo;
+  return dd_norm(s.hi, lo);
+}
+static dd_t dd_add_d(dd_t a, double b) {
+  dd_t s = two_sum(a.hi, b);
+  return dd_norm(s.hi, s.lo + a.lo);
+}
+static dd_t dd_neg(dd_t a) { dd_t r; r.hi = -a.hi; r.lo = -a.lo; return r; }
+static dd_t dd_mul_d(dd_t a, double b) {
+  dd_t p = two_prod(a.hi, b);
+  return dd_norm(p.hi, p.lo + a.lo * b);
+}
+static dd_t dd_mul(dd_t a, dd_t b) {
+  dd_t p = two_prod(a.hi, b.hi);
+  return dd_norm(p.hi, p.lo + (a.hi * b.lo + a.lo * b.hi));
+}
+static dd_t dd_from(double a) { dd_t r; r.hi = a; r.lo = 0.0; return r; }
+
+/* ------------------------------------------------------------------ */
+/* 1. not-a-knot cubic spline, dense Gaussian elimination               */
+/* ------------------------------------------------------------------ */
+/* System for the knot second derivatives M_0..M_{K-1}:
+ *   rows 1..K-2 (C2 continuity):
+ *     h_{k-1} M_{k-1} + 2 (h_{k-1}+h_k) M_k + h_k M_{k+1}
+ *        = 6 [ (y_{k+1}-y_k)/h_k - (y_k-y_{k-1})/h_{k-1} ]
+ *   row 0 (not-a-knot at t_1, third derivative continuous):
+ *     (M_1 - M_0)/h_0 - (M_2 - M_1)/h_1 = 0, times h_0 h_1
+ *   row K-1 (not-a-knot at t_{K-2}):
+ *     (M_{K-2} - M_{K-3})/h_{K-3} - (M_{K-1} - M_{K-2})/h_{K-2} = 0, times h_{K-3} h_{K-2}
+ * Segment k, tau = t - t_k in [0, h_k]:
+ *   S = y_k + b tau + c tau^2 + d tau^3,
+ *   b = (y_{k+1}-y_k)/h_k - h_k (2 M_k + M_{k+1})/6, c = M_k/2,
+ *   d = (M_{k+1} - M_k)/(6 h_k).                                         */
+typedef struct { int K; double* LU; int* piv; const double* t; } spl_sys_t;
+
+static int spl_factor(spl_sys_t* S, int K, const double* t) {
+  S->K = K; S->t = t;
+  S->LU = (double*)calloc((size_t)K * K, sizeof(double));
+  S->piv = (int*)malloc(sizeof(int) * K);
+  if (!S->LU || !S->piv) return -1;
+  double* A = S->LU;
+#define AA(i, j) A[(size_t)(i) * K + (j)]
+  for (int k = 1; k <= K - 2; k++) {
+    double h0 = t[k] - t[k - 1], h1 = t[k + 1] - t[k];
+    AA(k, k - 1) = h0; AA(k, k) = 2.0 * (h0 + h1); AA(k, k + 1) = h1;
+  }
+  /* not-a-knot rows multiplied through by h_0 h_1 (resp. h_{K-3} h_{K-2}) so
+   * that their entries have the scale of the interior rows */
+  { double h0 = t[1] - t[0], h1 = t[2] - t[1];
+    AA(0, 0) = -h1; AA(0, 1) = h0 + h1; AA(0, 2) = -h0; }
+  { double ha = t[K - 2] - t[K - 3], hb = t[K - 1] - t[K - 2];
+    AA(K - 1, K - 3) = -hb; AA(K - 1, K - 2) = ha + hb; AA(K - 1, K - 1) = -ha; }
+  /* LU with partial pivoting (row exchanges recorded in piv). */
+  for (int c = 0; c < K; c++) {
+    int p = c; double best = fabs(AA(c, c));
+    for (int r = c + 1; r < K; r++) if (fabs(AA(r, c)) > best) { best = fabs(AA(r, c)); p = r; }
+    S->piv[c] = p;
+    if (best == 0.0) return -2;
+    if (p != c) for (int j = 0; j < K; j++) { double tmp = AA(c, j); AA(c, j) = AA(p, j); AA(p, j) = tmp; }
+    for (int r = c + 1; r < K; r++) {
+      double f = AA(r, c) / AA(c, c);
+      AA(r, c) = f;
+      for (int j = c + 1; j < K; j++) AA(r, j) -= f * AA(c, j);
+    }
+  }
+#undef AA
+  return 0;
+}
+
+static void spl_free(spl_sys_t* S) { free(S->LU); free(S->piv); }
+
+/* Solve for M given y, then write coef[k*4 + {0,1,2,3}] = (a, b, c, d). */
+static void spl_coef(const spl_sys_t* S, const double* y, double* coef, double* work) {
+  int K = S->K; const double* t = S->t; const double* A = S->LU;
+  double* M = work;
+  for (int k = 0; k < K; k++) M[k] = 0.0;
+  for (int k = 1; k <= K - 2; k++) {
+    double h0 = t[k] - t[k - 1], h1 = t[k + 1] - t[k];
+    M[k] = 6.0 * ((y[k + 1] - y[k]) / h1 - (y[k] - y[k - 1]) / h0);
+  }
+  /* the factorization swapped whole rows (multipliers included), so apply
+   * every recorded interchange to the right-hand side first, in order */
+  for (int c = 0; c < K; c++) { int p = S->piv[c]; if (p != c) { double tmp = M[c]; M[c] = M[p]; M[p] = tmp; } }
+  for (int c = 0; c < K; c++)
+    for (int r = c + 1; r < K; r++) M[r] -= A[(size_t)r * K + c] * M[c];
+  for (int r = K - 1; r >= 0; r--) {
+    double s = M[r];
+    for (int j = r + 1; j < K; j++) s -= A[(size_t)r * K + j] * M[j];
+    M[r] = s / A[(size_t)r * K + r];
+  }
+  for (int k = 0; k < K - 1; k++) {
+    double h = t[k + 1] - t[k];
+    coef[4 * k + 0] = y[k];
+    coef[4 * k + 1] = (y[k + 1] - y[k]) / h - h * (2.0 * M[k] + M[k + 1]) / 6.0;
+    coef[4 * k + 2] = M[k] / 2.0;
+    coef[4 * k + 3] = (M[k + 1] - M[k]) / (6.0 * h);
+  }
+}
+
+/* Public: spline coefficients of one series; returns 0 on success. */
+int oracle_spline_coef(int K, const double* t, const double* y, double* coef) {
+  if (K < 4) return -1;
+  spl_sys_t S; if (spl_factor(&S, K, t)) { spl_free(&S); return -2; }
+  double* w = (double*)malloc(sizeof(double) * K);
+  spl_coef(&S, y, coef, w);
+  free(w); spl_free(&S); return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* spin-weighted spherical harmonic, Goldberg et al. 1967 sum formula   */
+/* sY_lm = (-1)^m sqrt[(l+m)!(l-m)!(2l+1) / (4 pi (l+s)!(l-s)!)]
+ *         sin^{2l}(theta/2) sum_r C(l-s,r) C(l+s,r+s-m) (-1)^{l-r-s}
+ *         e^{i m phi} cot^{2r+s-m}(theta/2)                               */
+/* ------------------------------------------------------------------ */
+static double fact(int n) { double f = 1.0; for (int i = 2; i <= n; i++) f *= i; return f; }
+static double binom(int n, int k) { if (k < 0 || k > n) return 0.0; return fact(n) / (fact(k) * fact(n - k)); }
+
+void oracle_swsh(int s, int l, int m, double theta, double phi, double* out) {
+  double pre = ((m & 1) ? -1.0 : 1.0) *
+               sqrt(fact(l + m) * fact(l - m) * (2.0 * l + 1.0) / (4.0 * OR_PI * fact(l + s) * fact(l - s)));
+  double sh = sin(0.5 * theta), ch = cos(0.5 * theta);
+  double sum = 0.0;
+  for (int r = 0; r <= l - s; r++) {
+    double c = binom(l - s, r) * binom(l + s, r + s - m);
+    if (c == 0.0) continue;
+    int k = 2 * r + s - m;                 /* power of cot(theta/2), >= 0 for nonzero terms */
+    double term = c * (((l - r - s) & 1) ? -1.0 : 1.0) * pow(sh, 2 * l - k) * pow(ch, k);
+    sum += term;
+  }
+  out[0] = pre * sum * cos(m * phi);
+  out[1] = pre * sum * sin(m * phi);
+}
+
+/* ------------------------------------------------------------------ */
+/* 2-5. the SPA sum                                                     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  int l, m, n;            /* voice mode numbers (m may be negative for partners) */
+  double Y[2];            /* -2Y_lm(theta, phi) */
+  const double* are;      /* amplitude spline coef, Re, [K-1][4] */
+  const double* aim;      /* amplitude spline coef, Im */
+} voice_t;
+
+typedef struct {
+  int voice, seg;
+  double ta, tb;          /* monotone piece [ta, tb] inside the segment */
+  int dir;                /* +1 increasing, -1 decreasing */
+  long long lo[2], hi[2]; /* owned bin ranges for g = +f (index 0) and g = -f (index 1) */
+} piece_t;
+
+static long long lower_bound(const double* f, long long nf, double x) {
+  long long a = 0, b = nf; while (a < b) { long long c = a + (b - a) / 2; if (f[c] < x) a = c + 1; else b = c; } return a;
+}
+static long long upper_bound(const double* f, long long nf, double x) {
+  long long a = 0, b = nf; while (a < b) { long long c = a + (b - a) / 2; if (f[c] <= x) a = c + 1; else b = c; } return a;
+}
+
+typedef struct {
+  int K; const double* t;
+  const double *cPp, *cPr, *cOp, *cOr;   /* fundamental spline coefs [K-1][4] */
+  const double *Op, *Or;                 /* knot values of Omega_phi, Omega_r */
+  double prefactor;
+} traj_t;
+
+/* voice frequency at knot k: the ownership rule's exact expression */
+static double knot_freq(const traj_t* T, int mv, int nv, int k) {
+  return ((double)mv * T->Op[k] + (double)nv * T->Or[k]) / OR_TWO_PI_HI;
+}
+
+/* cubic coefficients of F_V in segment k: (F_k, B, C, D) */
+static void voice_fcubic(const traj_t* T, int mv, int nv, int k, double* c4) {
+  c4[0] = knot_freq(T, mv, nv, k);
+  for (int j = 1; j < 4; j++)
+    c4[j] = ((double)mv * T->cOp[4 * k + j] + (double)nv * T->cOr[4 * k + j]) / OR_TWO_PI_HI;
+}
+static double cubic(const double* c, double x) { return c[0] + x * (c[1] + x * (c[2] + x * c[3])); }
+static double dcubic(const double* c, double x) { return c[1] + x * (2.0 * c[2] + x * 3.0 * c[3]); }
+
+/* roots of c1 + 2 c2 x + 3 c3 x^2 in the open interval (0, h), ascending; returns count */
+static int turnovers(const double* c, double h, double* r) {
+  double a = 3.0 * c[3], b = 2.0 * c[2], cc = c[1];
+  double x[2]; int nx = 0;
+  if (a == 0.0) {
+    if (b != 0.0) x[nx++] = -cc / b;
+  } else {
+    double disc = b * b - 4.0 * a * cc;
+    if (disc >= 0.0) {
+      double sq = sqrt(disc);
+      double q = -0.5 * (b + (b >= 0.0 ? sq : -sq));
+      if (q != 0.0) { x[nx++] = q / a; x[nx++] = cc / q; }
+      else x[nx++] = 0.0;          /* b = 0 and disc = 0: double root at 0 */
+    }
+  }
+  int n = 0;
+  for (int i = 0; i < nx; i++) if (x[i] > 0.0 && x[i] < h) r[n++] = x[i];
+  if (n == 2 && r[1] < r[0]) { double tmp = r[0]; r[0] = r[1]; r[1] = tmp; }
+  if (n == 2 && r[1] == r[0]) n = 1;
+  return n;
+}
+
+/* bisection for F(x) = g on [a, b], F monotone with direction dir */
+static double bisect(const double* c, double g, double a, double b, int dir) {
+  double lo = a, hi = b;
+  for (int it = 0; it < 400; it++) {
+    double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    double v = cubic(c, mid) - g;
+    if (dir * v < 0.0) lo = mid; else hi = mid;
+  }
+  double vl = fabs(cubic(c, lo) - g), vh = fabs(cubic(c, hi) - g);
+  return (vh < vl) ? hi : lo;
+}
+
+/* Phi spline value in double-double at tau in segment k */
+static dd_t dd_spline(const double* c4, double x) {
+  dd_t r = dd_from(c4[3]);
+  r = dd_add_d(dd_mul_d(r, x), c4[2]);
+  r = dd_add_d(dd_mul_d(r, x), c4[1]);
+  r = dd_add_d(dd_mul_d(r, x), c4[0]);
+  return r;
+}
+
+/* contribution of one root: adds H_V e^{i psi}/sqrt|Fdot| to acc[0..1] */
+static int contrib(const traj_t* T, const voice_t* V, int k, const double* fc, double g, double x, double* acc) {
+  double Fd = dcubic(fc, x);
+  if (Fd == 0.0) return 1;
+  /* phase psi = 2 pi g (t_k + x) - Phi_V(t_k + x) - sgn(Fdot) pi / 4 in double-double */
+  dd_t tt = two_sum(T->t[k], x);
+  dd_t gt = dd_mul_d(tt, g);
+  dd_t twopi; twopi.hi = OR_TWO_PI_HI; twopi.lo = OR_TWO_PI_LO;
+  dd_t wgt = dd_mul(gt, twopi);
+  dd_t Pp = dd_spline(T->cPp + 4 * k, x), Pr = dd_spline(T->cPr + 4 * k, x);
+  dd_t PV = dd_add(dd_mul_d(Pp, (double)V->m), dd_mul_d(Pr, (double)V->n));
+  dd_t psi = dd_add(wgt, dd_neg(PV));
+  dd_t qpi; qpi.hi = OR_QPI_HI; qpi.lo = OR_QPI_LO;
+  psi = dd_add(psi, Fd > 0.0 ? dd_neg(qpi) : qpi);
+  /* reduce modulo 2 pi */
+  double kk = nearbyint(psi.hi / OR_TWO_PI_HI);
+  psi = dd_add(psi, dd_neg(dd_mul_d(twopi, kk)));
+  double cs = cos(psi.hi) - psi.lo * sin(psi.hi);
+  double sn = sin(psi.hi) + psi.lo * cos(psi.hi);
+  /* H_V(t) = prefactor A(t) Y */
+  double are = cubic(V->are + 4 * k, x), aim = cubic(V->aim + 4 * k, x);
+  double hr = T->prefactor * (are * V->Y[0] - aim * V->Y[1]);
+  double hi = T->prefactor * (are * V->Y[1] + aim * V->Y[0]);
+  double w = 1.0 / sqrt(fabs(Fd));
+  acc[0] += w * (hr * cs - hi * sn);
+  acc[1] += w * (hr * sn + hi * cs);
+  return 0;
+}
+
+/* Build the monotone pieces of every voice, with owned bin ranges. */
+static piece_t* build_pieces(const traj_t* T, const voice_t* V, int nv, const double* freqs, long long nf, long long* npieces) {
+  int K = T->K;
+  size_t cap = (size_t)nv * (K - 1) * 3 + 1, np = 0;
+  piece_t* P = (piece_t*)malloc(sizeof(piece_t) * cap);
+  if (!P) return NULL;
+  for (int v = 0; v < nv; v++) {
+    for (int k = 0; k < K - 1; k++) {
+      double fc[4]; voice_fcubic(T, V[v].m, V[v].n, k, fc);
+      double h = T->t[k + 1] - T->t[k];
+      double r[2]; int nr = turnovers(fc, h, r);
+      double xs[4], Fs[4]; int nx = 0;
+      xs[nx] = 0.0; Fs[nx++] = fc[0];
+      for (int i = 0; i < nr; i++) { xs[nx] = r[i]; Fs[nx++] = cubic(fc, r[i]); }
+      xs[nx] = h; Fs[nx++] = knot_freq(T, V[v].m, V[v].n, k + 1);
+      for (int i = 0; i + 1 < nx; i++) {
+        double Fa = Fs[i], Fb = Fs[i + 1];
+        if (Fa == Fb) continue;
+        piece_t p; p.voice = v; p.seg = k; p.ta = xs[i]; p.tb = xs[i + 1];
+        if (Fa < Fb) {
+          p.dir = 1;
+          p.lo[0] = lower_bound(freqs, nf, Fa);  p.hi[0] = lower_bound(freqs, nf, Fb);   /* Fa <= f < Fb */
+          p.lo[1] = upper_bound(freqs, nf, -Fb); p.hi[1] = upper_bound(freqs, nf, -Fa);  /* Fa <= -f < Fb */
+        } else {
+          p.dir = -1;
+          p.lo[0] = upper_bound(freqs, nf, Fb);  p.hi[0] = upper_bound(freqs, nf, Fa);   /* Fb < f <= Fa */
+          p.lo[1] = lower_bound(freqs, nf, -Fa); p.hi[1] = lower_bound(freqs, nf, -Fb);  /* Fb < -f <= Fa */
+        }
+        if (p.hi[0] > p.lo[0] || p.hi[1] > p.lo[1]) P[np++] = p;
+      }
+    }
+  }
+  *npieces = (long long)np;
+  return P;
+}
+
+/*
+ * oracle_sum_modes: one waveform.
+ *   K knots t[K]; phi_phi, phi_r, omega_phi, omega_r [K];
+ *   nm modes l, m, n [nm]; amp [nm][K][2] (re, im interleaved);
+ *   theta, phi, prefactor; conj_partners (0/1);
+ *   nf ascending freqs (> 0); outputs hp, hc [nf][2];
+ *   stats[0] = contributions evaluated, stats[1] = roots with Fdot == 0,
+ *   stats[2] = number of monotone pieces.
+ * Returns 0 on success, < 0 on bad input.
+ */
+int oracle_sum_modes(int K, const double* t, const double* phi_phi, const double* phi_r,
+                     const double* omega_phi, const double* omega_r,
+                     int nm, const int* l, const int* m, const int* n, const double* amp,
+                     double theta, double phi, double prefactor, int conj_partners,
+                     long long nf, const double* freqs, double* hp, double* hc,
+                     long long* stats, int nthreads) {
+  if (K < 4 || nm < 0 || nf < 0) return -1;
+  for (int k = 0; k + 1 < K; k++) if (!(t[k + 1] > t[k])) return -2;
+  for (long long i = 0; i < nf; i++) if (!(freqs[i] > 0.0) || (i && !(freqs[i] > freqs[i - 1]))) return -3;
+  for (int j = 0; j < nm; j++) if (l[j] < 2 || abs(m[j]) > l[j] || (conj_partners && m[j] < 0)) return -4;
+
+  spl_sys_t S; if (spl_factor(&S, K, t)) { spl_free(&S); return -5; }
+  double* work = (double*)malloc(sizeof(double) * K);
+  double* y = (double*)malloc(sizeof(double) * K);
+  size_t sc = (size_t)(K - 1) * 4;
+  double* cf = (double*)malloc(sizeof(double) * sc * 4);
+  int nv = conj_partners ? 2 * nm : nm;
+  double* ac = (double*)malloc(sizeof(double) * sc * 2 * (size_t)nv);
+  voice_t* V = (voice_t*)malloc(sizeof(voice_t) * (size_t)(nv > 0 ? nv : 1));
+  traj_t T; T.K = K; T.t = t; T.Op = omega_phi; T.Or = omega_r; T.prefactor = prefactor;
+  spl_coef(&S, phi_phi, cf + 0 * sc, work); spl_coef(&S, phi_r, cf + 1 * sc, work);
+  spl_coef(&S, omega_phi, cf + 2 * sc, work); spl_coef(&S, omega_r, cf + 3 * sc, work);
+  T.cPp = cf; T.cPr = cf + sc; T.cOp = cf + 2 * sc; T.cOr = cf + 3 * sc;
+  int iv = 0;
+  for (int j = 0; j < nm; j++) {
+    for (int part = 0; part < (conj_partners ? 2 : 1); part++) {
+      voice_t* v = &V[iv];
+      v->l = l[j]; v->m = part ? -m[j] : m[j]; v->n = part ? -n[j] : n[j];
+      double sgn = (l[j] & 1) ? -1.0 : 1.0;
+      double* cre = ac + (size_t)iv * 2 * sc; double* cim = cre + sc;
+      for (int k = 0; k < K; k++) y[k] = part ? sgn * amp[((size_t)j * K + k) * 2 + 0] : amp[((size_t)j * K + k) * 2 + 0];
+      spl_coef(&S, y, cre, work);
+      for (int k = 0; k < K; k++) y[k] = part ? -sgn * amp[((size_t)j * K + k) * 2 + 1] : amp[((size_t)j * K + k) * 2 + 1];
+      spl_coef(&S, y, cim, work);
+      v->are = cre; v->aim = cim;
+      oracle_swsh(-2, v->l, v->m, theta, phi, v->Y);
+      iv++;
+    }
+  }
+  long long np = 0;
+  piece_t* P = build_pieces(&T, V, nv, freqs, nf, &np);
+  double* Hpos = (double*)calloc((size_t)(nf > 0 ? nf : 1) * 2, sizeof(double));
+  double* Hneg = (double*)calloc((size_t)(nf > 0 ? nf : 1) * 2, sizeof(double));
+  long long nev = 0, nzero = 0;
+  if (nthreads < 1) nthreads = 1;
+  /* Parallel over contiguous chunks of bins; every bin sums its voices in
+   * ascending voice order, so the result does not depend on nthreads. */
+  long long nchunk = nthreads * 8LL;
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1) reduction(+ : nev, nzero)
+  for (long long ch = 0; ch < nchunk; ch++) {
+    long long b0 = nf * ch / nchunk, b1 = nf * (ch + 1) / nchunk;
+    if (b0 >= b1) continue;
+    for (long long ip = 0; ip < np; ip++) {
+      const piece_t* p = &P[ip];
+      const voice_t* v = &V[p->voice];
+      double fc[4];
+      int have_fc = 0;
+      for (int sgn = 0; sgn < 2; sgn++) {
+        long long lo = p->lo[sgn] > b0 ? p->lo[sgn] : b0;
+        long long hi = p->hi[sgn] < b1 ? p->hi[sgn] : b1;
+        if (lo >= hi) continue;
+        if (!have_fc) { voice_fcubic(&T, v->m, v->n, p->seg, fc); have_fc = 1; }
+        double* H = sgn ? Hneg : Hpos;
+        for (long long b = lo; b < hi; b++) {
+          double g = sgn ? -freqs[b] : freqs[b];
+          double x = bisect(fc, g, p->ta, p->tb, p->dir);
+          nzero += contrib(&T, v, p->seg, fc, g, x, H + 2 * b);
+          nev++;
+        }
+      }
+    }
+  }
+  for (long long b = 0; b < nf; b++) {
+    double pr = Hpos[2 * b], pi = Hpos[2 * b + 1], nr = Hneg[2 * b], ni = -Hneg[2 * b + 1]; /* conj H(-f) */
+    hp[2 * b] = 0.5 * (pr + nr);   hp[2 * b + 1] = 0.5 * (pi + ni);
+    /* hx = i/2 (H(f) - conj H(-f)) */
+    hc[2 * b] = -0.5 * (pi - ni);  hc[2 * b + 1] = 0.5 * (pr - nr);
+  }
+  if (stats) { stats[0] = nev; stats[1] = nzero; stats[2] = np; }
+  free(Hpos); free(Hneg); free(P); free(V); free(ac); free(cf); free(y); free(work); spl_free(&S);
+  return 0;
+}
