@@ -1,0 +1,288 @@
+"""Benchmark of the frequency-domain SPA mode sum on GB300.
+
+One step = one emri_fd_sum_modes call (the whole hot path: input checks,
+not-a-knot spline solves, per-segment records, turnovers and monotone
+branches, and the SPA output kernel) over one paper-shaped waveform: T = 2 yr,
+200 knots, 2000 (l, m, n) modes (l <= 10, |n| <= 30), 3,155,760 bins at
+df = 1/T (dt-equivalent 10 s), FP64, complex128 h+ and hx.  Eight such
+waveforms (seeds 1-8) are resident in HBM and rotated, so every step's
+working set (~200 MB) exceeds the 129 MB L2.
+
+Metric: waveforms/s (whole job; with N ranks each rank sums its own
+waveforms, weak scaling), plus mode-bin evaluations/s.
+`--impl reference` times the CPU oracle instead (bounded samples of the
+same workload, extrapolated).  See the design doc for the roofline arithmetic.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("paper-shaped FP64 single waveform: T=2 yr, K=200 knots, 2000 modes (l=2..10, m=1..l, "
+            "|n|<=30, top mean power of 3294), 3,155,760 bins f=i/T, conjugate partners implied")
+FP64_OPS_PER_MODE_BIN = 42       # FP64-pipe instructions per mode-bin in the FP64 output kernel
+FP64_FLOPS_PER_MODE_BIN = 68     # of which 26 are FMA (2 flops) and 16 single-flop
+FP64_PER_CLK_PER_SM = 2          # GB300 FP64 issue rate (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--waveforms", type=int, default=8)
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(w, budget_s=15.0, stride0=64):
+    """The CPU oracle on a strided sample of the waveform's bins (bins are
+    independent, so the sample extrapolates); returns waveforms/s, threads, sample text."""
+    from oracle import oracle as O
+    O.build()
+    threads = O.default_threads()
+    stride = stride0
+    while True:
+        sel = w.freqs[::stride]
+        t0 = time.perf_counter()
+        O.sum_modes(w, freqs=sel, nthreads=threads)
+        dt = time.perf_counter() - t0
+        if dt > 0.5 * budget_s / 4 or stride <= 1:
+            break
+        stride = max(1, int(stride / max(2.0, (0.5 * budget_s / 4) / max(dt, 1e-3))))
+    # final timed sample sized to the budget
+    frac = min(1.0, dt / budget_s)
+    stride = max(1, int(stride * frac)) if frac < 1.0 else stride
+    sel = w.freqs[::stride]
+    t0 = time.perf_counter()
+    O.sum_modes(w, freqs=sel, nthreads=threads)
+    dt = time.perf_counter() - t0
+    per_wave = dt * (w.n_freqs / sel.shape[0])
+    return 1.0 / per_wave, threads, "every %d-th bin (%d of %d bins), %.1f s" % (stride, sel.shape[0], w.n_freqs, dt)
+
+
+def reference_arm(args, rank, world):
+    """CPU oracle timed as the reference implementation (rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_2307_12585_gb300 import synth
+    from oracle import oracle as O
+    O.build()
+    w = synth.paper_config(1)
+    threads = O.default_threads()
+    stride = 400
+    sel = w.freqs[::stride]
+    for _ in range(args.warmup):
+        O.sum_modes(w, freqs=sel, nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.sum_modes(w, freqs=sel, nthreads=threads)
+    dt = (time.perf_counter() - t0) / args.steps
+    val = 1.0 / (dt * w.n_freqs / sel.shape[0])
+    line = {"impl": "reference", "metric": "waveforms/s", "value": val, "unit": "waveforms/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference": "CPU FP64 oracle (oracle/oracle.c)"},
+            "cpu_baseline": {"value": val, "unit": "waveforms/s", "cores": threads, "kind": "oracle",
+                             "sample": "every %d-th bin per step (%d of %d bins), extrapolated" % (
+                                 stride, sel.shape[0], w.n_freqs)},
+            "e2e": {"value": val, "unit": "waveforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2307_12585_gb300 import api, build, synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    nw = args.waveforms
+    seeds = [1 + rank * nw + i for i in range(nw)]
+    wfs = [synth.paper_config(s) for s in seeds]
+    plan = api.Plan(args.precision, conj_partners=True, max_waveforms=1, max_knots=200,
+                    max_modes_total=2000, max_bins_total=wfs[0].n_freqs)
+    dev = [plan.upload(synth.concat([w])) for w in wfs]
+    nf = wfs[0].n_freqs
+    outs = [(torch.empty(nf, dtype=plan.out_dtype, device="cuda"), torch.empty(nf, dtype=plan.out_dtype, device="cuda"))
+            for _ in range(2)]
+    # per-waveform mode-bin counts (exact, from the plan)
+    mode_bins = []
+    for i, b in enumerate(dev):
+        plan.sum_modes(b, out=outs[0])
+        mode_bins.append(plan.stats()["mode_bins"])
+    for i in range(args.warmup):
+        plan.sum_modes(dev[i % nw], out=outs[i % 2], check=False)
+    plan.sync()
+    clk = ClockSampler(local)
+    plan.profile(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    stream = plan.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mb = 0
+    for i in range(args.steps):
+        plan.sum_modes(dev[i % nw], out=outs[i % 2], check=False)
+        mb += mode_bins[i % nw]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    plan.sync()
+    st = plan.stats()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sec = ms * 1e-3
+    value = world * args.steps / sec
+    spa_s = st["spa_ns"] * 1e-9 / max(1, st["timed_calls"])
+    mb_per_launch = mb / args.steps
+    clk_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tflops = FP64_PER_CLK_PER_SM * 2 * n_sms * clk_hz / 1e12
+    achieved = FP64_FLOPS_PER_MODE_BIN * mb_per_launch / spa_s / 1e12
+    issue = FP64_OPS_PER_MODE_BIN * mb_per_launch / spa_s / (FP64_PER_CLK_PER_SM * n_sms * clk_hz)
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI with pinned HOST buffers: H2D of the inputs and
+        # D2H of h+ and hx happen inside every timed step
+        hb = []
+        for w in wfs[:2]:
+            b = api.host_batch(synth.concat([w]))
+            for k in list(b):
+                if isinstance(b[k], np.ndarray) and k not in ("knot_off", "mode_off", "freq_off"):
+                    b[k] = torch.from_numpy(b[k]).pin_memory()
+            hb.append(b)
+        cdt = torch.complex128 if args.precision == "fp64" else torch.complex64
+        hout = [(torch.empty(nf, dtype=cdt).pin_memory(), torch.empty(nf, dtype=cdt).pin_memory()) for _ in range(2)]
+        h2d = sum(int(v.numel() * v.element_size()) for k, v in hb[0].items() if hasattr(v, "numel"))
+        d2h = 2 * nf * (16 if args.precision == "fp64" else 8)
+        for i in range(2):
+            plan.sum_modes_host(hb[i % 2], out=hout[i % 2])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        esteps = max(3, args.steps // 2)
+        for i in range(esteps):
+            plan.sum_modes_host(hb[i % 2], out=hout[i % 2])
+        torch.cuda.synchronize()
+        edt = time.perf_counter() - t0
+        e2e = {"value": world * esteps / edt, "unit": "waveforms/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": esteps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, sample = cpu_oracle_rate(wfs[0])
+        cpu = {"value": v, "unit": "waveforms/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": "waveforms/s", "value": value, "unit": "waveforms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision, "waveforms_resident": nw,
+                       "l2": "inputs larger than L2: %d resident waveforms rotated, ~200 MB touched per step" % nw,
+                       "parallelism": "independent waveforms per GPU"},
+            "mode_bin_evals_per_s": world * mb / sec,
+            "mode_bins_per_waveform": mb_per_launch,
+            "spa_kernel_ms": spa_s * 1e3, "prep_ms": st["prep_ns"] * 1e-6 / max(1, st["timed_calls"]),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tflops, "traffic": None,
+                         "issue_frac": issue,
+                         "note": "FP64 pipe: %d FP64 flops (%d FP64 instructions) per mode-bin; peak = %d FP64 FMA/clk/SM x 2 x SMs x median SM clock" % (
+                             FP64_FLOPS_PER_MODE_BIN, FP64_OPS_PER_MODE_BIN, FP64_PER_CLK_PER_SM)},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"], "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

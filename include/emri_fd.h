@@ -1,0 +1,165 @@
+/*
+ * emri_fd.h -- C ABI of the GB300 (sm_103a) frequency-domain EMRI mode sum.
+ *
+ * Method: arXiv 2307.12585 ("Fast and Fourier"), Sec. 2.2.  The strain is a
+ * sum of voices h = h+ - i hx = sum_V H_V(t) exp(-i Phi_V(t)) (Eq. 1-2), one
+ * per (l, m, n) harmonic of a Schwarzschild eccentric inspiral, with
+ * H_V = prefactor A_lmn(t) -2Y_lm(theta, phi) and Phi_V = m Phi_phi + n Phi_r.
+ * Its Fourier transform (sign convention of Eq. 3) is evaluated on an
+ * arbitrary ascending frequency grid by the stationary-phase approximation:
+ * for every voice and frequency bin, t(f) is obtained by inverting the
+ * voice's cubic-spline frequency track F_V(t) = (m Omega_phi + n Omega_r)/2pi
+ * segment by segment (Eq. 6), on each monotone branch (voices whose dF/dt
+ * vanishes are split at the turnover, Sec. 2.2), and each root contributes
+ * H_V(t) exp(i[2 pi f t - Phi_V(t) - sgn(Fdot) pi/4]) / sqrt|Fdot|  (the
+ * standard-SPA limit of Eq. 10).
+ *
+ * Conventions shared by every entry point
+ *  - Units: seconds, rad, rad/s, Hz.  The caller converts the paper's
+ *    dimensionless Omega/M (Sec. 2.1) to rad/s.
+ *  - Every series is interpolated by an independent not-a-knot cubic spline
+ *    in t over the waveform's knots (Sec. 2.1).
+ *  - With conj_partners = 1, each mode (l, m, n) (m >= 0) also stands for the
+ *    voice (l, -m, -n) with amplitude (-1)^l conj(A) (Schwarzschild reflection
+ *    symmetry); callers list one mode of each pair.  With conj_partners = 0
+ *    every listed mode is one voice, any m in [-l, l].
+ *  - Output bins f > 0 receive h+(f) = [H(f) + conj H(-f)]/2 and
+ *    hx(f) = i [H(f) - conj H(-f)]/2, H(g) the voice-sum transform at signed
+ *    frequency g, so voices whose frequency is negative contribute through
+ *    conj H(-f).
+ *  - Batches: n_waveforms independent waveforms share one call.  Their
+ *    arrays are concatenated; knot_off, mode_off and freq_off (int64,
+ *    [n_waveforms + 1], HOST memory, starting at 0, non-decreasing) give each
+ *    waveform's slice.
+ *  - Data pointers may be device memory (the fast path; required while a
+ *    stream is being captured into a CUDA graph) or host memory, in which
+ *    case the call stages them through plan-owned device buffers and, for
+ *    host outputs, synchronises the stream before returning.
+ *  - Ownership: the caller owns every array passed in; the plan owns its
+ *    scratch (spline coefficients, branch lists, work counters), sized at plan
+ *    creation from the descriptor's maxima and never reallocated by a call on
+ *    device data.
+ *  - Errors: calls return an emri_fd_status.  Host-side checks (null
+ *    pointers, sizes above the plan's maxima, offsets) are reported before
+ *    anything is launched.  Value checks (non-increasing knots or
+ *    frequencies, non-finite values, bad mode numbers) run on the device:
+ *    they latch a status word in the plan, the output kernel of the call
+ *    then writes nothing (outputs are unspecified), and the status is
+ *    returned by emri_fd_sync() (which also clears it).  Every kernel keeps
+ *    its indices in bounds whatever the values.  No C++ exception crosses
+ *    this interface.
+ *  - Calls are asynchronous on the plan's stream; two calls on one plan must
+ *    not overlap in time on different streams.
+ */
+#ifndef EMRI_FD_H
+#define EMRI_FD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct emri_fd_plan_s* emri_fd_plan_t;
+
+typedef enum {
+  EMRI_FD_OK = 0,
+  EMRI_FD_ERR_ARG = 1,        /* null pointer, negative size, bad descriptor or offsets */
+  EMRI_FD_ERR_KNOTS = 2,      /* fewer than 4 knots, or knot times not strictly increasing */
+  EMRI_FD_ERR_FREQ = 3,       /* frequencies not strictly increasing, or f <= 0 */
+  EMRI_FD_ERR_MODE = 4,       /* l < 2, l > EMRI_FD_MAX_L, |m| > l, or m < 0 with conj_partners */
+  EMRI_FD_ERR_NONFINITE = 5,  /* NaN or Inf in a knot, amplitude, angle or prefactor */
+  EMRI_FD_ERR_CAPACITY = 6,   /* a size above the plan's maxima, or branch storage exhausted */
+  EMRI_FD_ERR_CUDA = 7,       /* a CUDA runtime call failed */
+  EMRI_FD_ERR_OOM = 8,        /* device allocation failed */
+  EMRI_FD_ERR_TIMEOUT = 9     /* a bounded device wait ran out */
+} emri_fd_status;
+
+enum { EMRI_FD_FP64 = 0, EMRI_FD_MIXED = 1 };
+
+#define EMRI_FD_MAX_L 20
+
+typedef struct {
+  int precision;            /* EMRI_FD_FP64: FP64 throughout, complex128 outputs.
+                               EMRI_FD_MIXED: FP64 root and phase, FP32 amplitude,
+                               weight, sincos and compensated accumulation;
+                               complex64 outputs. */
+  int conj_partners;        /* 0 or 1, see above */
+  int max_waveforms;        /* 1 .. 65535 */
+  int max_knots;            /* per waveform, >= 4 */
+  long long max_knots_total;/* sum of K over a call (0: max_waveforms * max_knots) */
+  long long max_modes_total;/* sum of N_m over a call, >= 1 */
+  long long max_bins_total; /* sum of N_f over a call, >= 1 */
+  int tile_bins;            /* output bins per work tile; 0 = default (64) */
+  int reserved[7];          /* must be zero */
+} emri_fd_desc;
+
+/*
+ * Create a plan.  out: receives the handle.  desc: sizes and precision.
+ * stream: a cudaStream_t (NULL = legacy default stream) on the current device;
+ * every call of the plan is ordered on it.  Allocates all scratch up front.
+ * Errors: EMRI_FD_ERR_ARG (bad desc), EMRI_FD_ERR_OOM, EMRI_FD_ERR_CUDA.
+ */
+emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* desc, void* stream);
+
+/*
+ * The SPA sum (Sec. 2.2; Eq. 2, 3, 6, 10 in its standard-SPA limit) of
+ * n_waveforms waveforms.
+ *   knot_off, mode_off, freq_off: HOST int64 [n_waveforms + 1] slice offsets.
+ *   t:                 [sum K] knot times (s), strictly increasing per waveform.
+ *   phi_phi, phi_r:    [sum K] azimuthal and radial orbital phases (rad).
+ *   omega_phi, omega_r:[sum K] azimuthal and radial frequencies (rad/s).
+ *   l, m, n:           [sum N_m] int32 mode numbers.
+ *   amp:               [sum over waveforms of N_m * K] complex128 amplitude
+ *                      knots (re, im interleaved), mode-major then knot.
+ *   theta, phi:        [n_waveforms] source-frame viewing angles (rad).
+ *   prefactor:         [n_waveforms] real amplitude prefactor (mu / d_L).
+ *   freqs:             [sum N_f] output frequencies (Hz), strictly increasing
+ *                      and > 0 per waveform.
+ *   h_plus, h_cross:   [sum N_f] outputs, complex128 (FP64 plan) or complex64
+ *                      (mixed plan), every bin written.
+ * Returns EMRI_FD_OK once the work is enqueued (device-side value errors are
+ * reported by emri_fd_sync).
+ */
+emri_fd_status emri_fd_sum_modes(emri_fd_plan_t plan, int n_waveforms,
+                                 const long long* knot_off, const long long* mode_off,
+                                 const long long* freq_off,
+                                 const double* t, const double* phi_phi, const double* phi_r,
+                                 const double* omega_phi, const double* omega_r,
+                                 const int* l, const int* m, const int* n, const double* amp,
+                                 const double* theta, const double* phi, const double* prefactor,
+                                 const double* freqs, void* h_plus, void* h_cross);
+
+/*
+ * Wait for the plan's stream and return (and clear) the status latched by the
+ * device-side checks of the calls since the last sync.
+ */
+emri_fd_status emri_fd_sync(emri_fd_plan_t plan);
+
+/*
+ * Counters (synchronises the stream).  out[0..n), n <= 8:
+ *   0: mode-bin evaluations of the last call (one per (mode, root, bin); a
+ *      conjugate-partner pair counts once), 1: monotone branches ("runs")
+ *      of the last call, 2: work tiles of the last call, 3: reserved (0),
+ *   4: calls timed since emri_fd_profile(plan, 1) (at most 1024),
+ *   5: total duration of their output (SPA) kernels in ns, 6: total duration
+ *      of their preparation kernels in ns (both from CUDA events recorded on
+ *      the plan's stream), 7: kernels launched since that emri_fd_profile.
+ */
+emri_fd_status emri_fd_stats(emri_fd_plan_t plan, long long* out, int n);
+
+/*
+ * Start (enable = 1) or stop (0) event timing of the following calls and
+ * reset the timing counters of emri_fd_stats.  Synchronises the stream.
+ * Timing adds three event records per call on the plan's stream.
+ */
+emri_fd_status emri_fd_profile(emri_fd_plan_t plan, int enable);
+
+/* Release the plan and its device memory (synchronises its stream first). */
+void emri_fd_plan_destroy(emri_fd_plan_t plan);
+
+/* Static, human-readable name of a status code. */
+const char* emri_fd_strerror(emri_fd_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMRI_FD_H */

@@ -1,0 +1,245 @@
+"""Python binding of the C ABI in include/emri_fd.h (argument marshalling only).
+
+Functions with the C names take raw pointers (ints); ``Plan`` wraps them for
+torch CUDA tensors / numpy arrays.  Every step of the computation runs in
+libemri_fd.so: there is no CPU or PyTorch fallback, and using the binding
+without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+EMRI_FD_FP64, EMRI_FD_MIXED = 0, 1
+STATUS = {0: "EMRI_FD_OK", 1: "EMRI_FD_ERR_ARG", 2: "EMRI_FD_ERR_KNOTS", 3: "EMRI_FD_ERR_FREQ",
+          4: "EMRI_FD_ERR_MODE", 5: "EMRI_FD_ERR_NONFINITE", 6: "EMRI_FD_ERR_CAPACITY",
+          7: "EMRI_FD_ERR_CUDA", 8: "EMRI_FD_ERR_OOM", 9: "EMRI_FD_ERR_TIMEOUT"}
+EXPORTS = ("emri_fd_plan", "emri_fd_sum_modes", "emri_fd_sync", "emri_fd_stats", "emri_fd_profile",
+           "emri_fd_plan_destroy", "emri_fd_strerror")
+
+
+class EmriFdError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = int(code)
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(self.code, "?"), _strerror(self.code)))
+
+
+class emri_fd_desc(C.Structure):
+    _fields_ = [("precision", C.c_int), ("conj_partners", C.c_int), ("max_waveforms", C.c_int),
+                ("max_knots", C.c_int), ("max_knots_total", C.c_longlong), ("max_modes_total", C.c_longlong),
+                ("max_bins_total", C.c_longlong), ("tile_bins", C.c_int), ("reserved", C.c_int * 7)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libemri_fd.so (built in-tree by build.build()); raises if absent."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libemri_fd.so is not built (%s); call __graft_entry__.build() -- "
+                               "the CUDA library is the only implementation" % path)
+        L = C.CDLL(path)
+        vp, ll, dp, ip = C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p
+        L.emri_fd_plan.argtypes = [C.POINTER(C.c_void_p), C.POINTER(emri_fd_desc), vp]
+        L.emri_fd_plan.restype = C.c_int
+        L.emri_fd_sum_modes.argtypes = [vp, C.c_int, vp, vp, vp] + [dp] * 5 + [ip] * 3 + [dp] * 5 + [vp, vp]
+        L.emri_fd_sum_modes.restype = C.c_int
+        L.emri_fd_sync.argtypes = [vp]
+        L.emri_fd_sync.restype = C.c_int
+        L.emri_fd_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
+        L.emri_fd_stats.restype = C.c_int
+        L.emri_fd_profile.argtypes = [vp, C.c_int]
+        L.emri_fd_profile.restype = C.c_int
+        L.emri_fd_plan_destroy.argtypes = [vp]
+        L.emri_fd_plan_destroy.restype = None
+        L.emri_fd_strerror.argtypes = [C.c_int]
+        L.emri_fd_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _strerror(code):
+    try:
+        return lib().emri_fd_strerror(int(code)).decode()
+    except Exception:
+        return "?"
+
+
+def _check(code, where):
+    if code != 0:
+        raise EmriFdError(code, where)
+
+
+# ---------------------------------------------------------------- C names
+def emri_fd_plan(desc: emri_fd_desc, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(lib().emri_fd_plan(C.byref(h), C.byref(desc), C.c_void_p(stream)), "emri_fd_plan")
+    return h.value
+
+
+def emri_fd_sum_modes(plan, n_waveforms, knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r,
+                      l, m, n, amp, theta, phi, prefactor, freqs, h_plus, h_cross) -> int:
+    """All array arguments are raw addresses (ints); returns the status code."""
+    return lib().emri_fd_sum_modes(C.c_void_p(plan), int(n_waveforms), *[C.c_void_p(int(x)) for x in (
+        knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r, l, m, n, amp, theta, phi,
+        prefactor, freqs, h_plus, h_cross)])
+
+
+def emri_fd_sync(plan) -> int:
+    return lib().emri_fd_sync(C.c_void_p(plan))
+
+
+def emri_fd_stats(plan) -> dict:
+    out = (C.c_longlong * 8)()
+    _check(lib().emri_fd_stats(C.c_void_p(plan), out, 8), "emri_fd_stats")
+    return {"mode_bins": int(out[0]), "runs": int(out[1]), "tiles": int(out[2]),
+            "timed_calls": int(out[4]), "spa_ns": int(out[5]), "prep_ns": int(out[6]), "launches": int(out[7])}
+
+
+def emri_fd_profile(plan, enable: bool) -> None:
+    _check(lib().emri_fd_profile(C.c_void_p(plan), int(bool(enable))), "emri_fd_profile")
+
+
+def emri_fd_strerror(code) -> str:
+    return _strerror(code)
+
+
+def emri_fd_plan_destroy(plan) -> None:
+    lib().emri_fd_plan_destroy(C.c_void_p(plan))
+
+
+# ---------------------------------------------------------------- wrapper
+_KEYS_D = ("t", "phi_phi", "phi_r", "omega_phi", "omega_r", "theta", "phi", "prefactor", "freqs")
+_KEYS_I = ("l", "m", "n")
+
+
+def _addr(x):
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+class Plan:
+    """A plan of the C library bound to a torch CUDA stream.
+
+    precision: "fp64" (complex128 outputs) or "mixed" (complex64 outputs).
+    Batches are dicts in the layout of synth.concat (numpy or torch)."""
+
+    def __init__(self, precision="fp64", conj_partners=True, max_waveforms=1, max_knots=200,
+                 max_modes_total=4096, max_bins_total=1 << 22, max_knots_total=0, tile_bins=0,
+                 device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.precision = EMRI_FD_FP64 if precision in ("fp64", 0) else EMRI_FD_MIXED
+        d = emri_fd_desc()
+        d.precision = self.precision
+        d.conj_partners = int(bool(conj_partners))
+        d.max_waveforms = int(max_waveforms)
+        d.max_knots = int(max_knots)
+        d.max_knots_total = int(max_knots_total)
+        d.max_modes_total = int(max_modes_total)
+        d.max_bins_total = int(max_bins_total)
+        d.tile_bins = int(tile_bins)
+        self.desc = d
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.handle = emri_fd_plan(d, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            emri_fd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def out_dtype(self):
+        return self.torch.complex128 if self.precision == EMRI_FD_FP64 else self.torch.complex64
+
+    def upload(self, batch, non_blocking=False):
+        """numpy batch -> dict of device tensors (offsets stay on the host)."""
+        T = self.torch
+        out = {}
+        for k in ("knot_off", "mode_off", "freq_off"):
+            out[k] = np.ascontiguousarray(np.asarray(batch[k], np.int64))
+        for k in _KEYS_D:
+            out[k] = T.as_tensor(np.ascontiguousarray(batch[k], np.float64)).to(self.device, non_blocking=non_blocking)
+        for k in _KEYS_I:
+            out[k] = T.as_tensor(np.ascontiguousarray(batch[k], np.int32)).to(self.device, non_blocking=non_blocking)
+        amp = np.ascontiguousarray(batch["amp"], np.complex128).view(np.float64)
+        out["amp"] = T.as_tensor(amp).to(self.device, non_blocking=non_blocking)
+        return out
+
+    def sum_modes(self, b, out=None, check=True):
+        """One call of emri_fd_sum_modes on a device batch; returns (h_plus, h_cross)."""
+        T = self.torch
+        n_wf = len(b["knot_off"]) - 1
+        nf = int(b["freq_off"][-1])
+        if out is None:
+            out = (T.empty(nf, dtype=self.out_dtype, device=self.device),
+                   T.empty(nf, dtype=self.out_dtype, device=self.device))
+        ko, mo, fo = (np.ascontiguousarray(np.asarray(b[k], np.int64)) for k in ("knot_off", "mode_off", "freq_off"))
+        code = emri_fd_sum_modes(self.handle, n_wf, ko.ctypes.data, mo.ctypes.data, fo.ctypes.data,
+                                 _addr(b["t"]), _addr(b["phi_phi"]), _addr(b["phi_r"]), _addr(b["omega_phi"]),
+                                 _addr(b["omega_r"]), _addr(b["l"]), _addr(b["m"]), _addr(b["n"]), _addr(b["amp"]),
+                                 _addr(b["theta"]), _addr(b["phi"]), _addr(b["prefactor"]), _addr(b["freqs"]),
+                                 _addr(out[0]), _addr(out[1]))
+        _check(code, "emri_fd_sum_modes")
+        if check:
+            _check(emri_fd_sync(self.handle), "emri_fd_sum_modes (device checks)")
+        return out
+
+    def sum_modes_host(self, b, out=None):
+        """emri_fd_sum_modes with HOST buffers (numpy, or pinned torch CPU tensors): the
+        library stages inputs and outputs itself and synchronises before returning."""
+        n_wf = len(b["knot_off"]) - 1
+        nf = int(b["freq_off"][-1])
+        cdt = np.complex128 if self.precision == EMRI_FD_FP64 else np.complex64
+        if out is None:
+            out = (np.empty(nf, cdt), np.empty(nf, cdt))
+        ko, mo, fo = (np.ascontiguousarray(np.asarray(b[k], np.int64)) for k in ("knot_off", "mode_off", "freq_off"))
+        code = emri_fd_sum_modes(self.handle, n_wf, ko.ctypes.data, mo.ctypes.data, fo.ctypes.data,
+                                 *[_addr(b[k]) for k in ("t", "phi_phi", "phi_r", "omega_phi", "omega_r", "l", "m",
+                                                         "n", "amp", "theta", "phi", "prefactor", "freqs")],
+                                 _addr(out[0]), _addr(out[1]))
+        _check(code, "emri_fd_sum_modes")
+        _check(emri_fd_sync(self.handle), "emri_fd_sum_modes (device checks)")
+        return out
+
+    def sync(self):
+        _check(emri_fd_sync(self.handle), "emri_fd_sync")
+
+    def stats(self):
+        return emri_fd_stats(self.handle)
+
+    def profile(self, enable=True):
+        emri_fd_profile(self.handle, enable)
+
+
+def host_batch(batch):
+    """numpy copy of a synth.concat batch with the dtypes the C ABI expects."""
+    out = dict(batch)
+    for k in _KEYS_D:
+        out[k] = np.ascontiguousarray(batch[k], np.float64)
+    for k in _KEYS_I:
+        out[k] = np.ascontiguousarray(batch[k], np.int32)
+    out["amp"] = np.ascontiguousarray(batch["amp"], np.complex128).view(np.float64)
+    return out

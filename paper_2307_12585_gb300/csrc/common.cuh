@@ -1,0 +1,198 @@
+// Internal definitions of the GB300 SPA mode-sum library (not part of the C ABI).
+//
+// Data layout in HBM, per call (all plan-owned scratch, sized at plan creation):
+//   WfInfo[n_wf]             per-waveform slice offsets and derived bases
+//   ModeInfo[sum N_m]        per-mode numbers, waveform id, polarisation weights
+//   spl_cprime/spl_invm      per-knot factors of each waveform's not-a-knot system
+//   fundM[4][sum K]          knot second derivatives of Phi_phi, Phi_r, Om_phi, Om_r
+//   ampM[sum N_m K][2]       knot second derivatives of Re A, Im A
+//   SegCore[sum N_m (K-1)]   per (mode, segment): frequency cubic, phase polynomial,
+//                            Q0.64 phase offset (112 B, 16-B aligned)
+//   SegAmp64/SegAmp32        per (mode, segment): amplitude cubic (FP64 or FP32 copy)
+//   SegCrit                  per (mode, segment): turnover points of F_V
+//   keyF[sum N_m K]          ordered int64 keys of the knot frequencies F_V(t_k)
+//   Run[...]                 monotone branches ("runs") of every voice track,
+//   RunBins[...]             and their output-bin ranges (int32, for the tile scan)
+//
+// Conventions: u = (t - t_s)/h_s is the normalised time inside segment s;
+// every per-segment polynomial is in u.  Phases in the hot loop are Q0.64
+// fixed-point turns (uint64; wrap-around addition is addition mod 1 turn).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace emrifd {
+
+constexpr int kWarps = 8;                 // warps per CTA of the hot kernel
+constexpr int kThreads = 32 * kWarps;
+constexpr int kTabBits = 12;              // e^{2 pi i k / 4096} table
+constexpr int kTabN = 1 << kTabBits;
+constexpr int kListCap = 2048;            // (run, sign) entries buffered per tile pass
+
+// status bits latched in the plan's device status word
+enum : int {
+  ST_KNOTS = 1, ST_FREQ = 2, ST_MODE = 4, ST_NONFINITE = 8, ST_CAPACITY = 16, ST_TIMEOUT = 32
+};
+
+struct WfInfo {
+  long long ko, K;         // knot slice
+  long long mo, nm;        // mode slice
+  long long fo, nf;        // bin slice
+  long long amp_base;      // first amplitude knot (complex index) = sum_{w'<w} N_m K
+  long long seg_base;      // first (mode, segment) record = sum_{w'<w} N_m (K-1)
+  long long tile_base, ntiles;
+  long long run_base, nruns;  // filled on the device
+};
+
+struct ModeInfo {
+  int wf, l, m, n;
+  long long seg_base;      // first record of this mode
+  long long key_base;      // first knot key / amplitude knot of this mode
+  double alpha, beta;      // h+ += alpha Z, hx += i beta Z (positive branch), see spa.cu
+};
+
+struct __align__(16) SegCore {
+  double A;                // F_V(t_s), knot expression (m*Om_phi_s + n*Om_r_s)/(2 pi)  [Hz]
+  double b, c, d;          // F(u) - A = b u + c u^2 + d u^3                           [Hz]
+  double c2, d3;           // 2c, 3d  (dF/du = b + c2 u + d3 u^2)
+  double Q1, P2, P3;       // phase inside the segment, in turns:
+                           //   g t - Phi_V(t)/2pi = g t_s - Phi_V(t_s)/2pi + u (delta h - Q1 - u (P2 + u P3))
+                           //   with delta = g - A
+  double h;                // segment length [s]
+  double ts;               // segment start time [s]
+  unsigned long long theta0; // Q0.64 of frac(Phi_V(t_s)/2pi - m phi/2pi)
+  float bf, cf, df, pad;   // FP32 copies of b, c, d for the root's initial guess
+};
+static_assert(sizeof(SegCore) == 112, "SegCore layout");
+
+struct __align__(16) SegAmp64 { double re[4], im[4]; };   // prefactor sqrt(h) A(u), cubic in u
+struct __align__(16) SegAmp32 { float re[4], im[4]; };
+struct __align__(16) SegCrit { double u[2]; double F[2]; int n; int pad[3]; };  // 48 B
+
+struct __align__(16) Run {
+  int mode, dir, s0, s1;   // global mode index; +1/-1; first/last segment (local)
+  double u0, u1;           // start u in s0, end u in s1
+};
+struct __align__(16) RunBins { int b0p, b1p, b0n, b1n; };  // global output bins, [b0, b1)
+
+// ----------------------------------------------------------------------------
+// small device helpers (integer work only unless stated)
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ long long ordkey(double x) {
+  // monotone map of doubles to signed int64 (non-NaN); -0 < +0
+  long long u = __double_as_longlong(x);
+  return u ^ ((u >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+
+__device__ __forceinline__ double unordkey(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFLL));
+}
+
+__device__ __forceinline__ float d2f_bits(double x) {
+  // double -> float by truncation, through the bit fields (no FP64-pipe conversion);
+  // values below the float normal range become 0
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  int e = (int)((u >> 52) & 0x7FF) - 1023 + 127;
+  unsigned s = (unsigned)(u >> 32) & 0x80000000u;
+  if (e <= 0) return __uint_as_float(s);
+  if (e >= 255) return __uint_as_float(s | 0x7F800000u | (unsigned)((u >> 29) & 0x7FFFFF));
+  return __uint_as_float(s | ((unsigned)e << 23) | (unsigned)((u >> 29) & 0x7FFFFF));
+}
+
+__device__ __forceinline__ double f2d_bits(float x) {
+  // exact float -> double through the bit fields; float denormals become 0
+  unsigned u = __float_as_uint(x);
+  unsigned e = (u >> 23) & 0xFF;
+  unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0) return __longlong_as_double((long long)s);
+  unsigned long long ed = (e == 255) ? 0x7FFull : (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(s | (ed << 52) | ((unsigned long long)(u & 0x7FFFFF) << 29)));
+}
+
+// frac(x) in Q0.64 turns (x in turns), by the bit fields of x
+__device__ __forceinline__ unsigned long long q64_of(double x) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  int e = (int)((u >> 52) & 0x7FF);
+  if (e == 0) return 0ull;
+  unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+  int sh = e - 1075 + 64;             // value * 2^64 = m * 2^sh
+  unsigned long long r;
+  if (sh >= 64) r = 0ull;
+  else if (sh >= 0) r = m << sh;
+  else if (sh > -64) r = m >> (-sh);
+  else r = 0ull;
+  return (u >> 63) ? (0ull - r) : r;
+}
+
+// frac(a * b) in Q0.64 turns, from the exact 106-bit product of the mantissas
+__device__ __forceinline__ unsigned long long q64_mul(double a, double b) {
+  unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+  int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
+  if (ea == 0 || eb == 0) return 0ull;
+  unsigned long long ma = (ua & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+  unsigned long long mb = (ub & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+  unsigned long long lo = ma * mb, hi = __umul64hi(ma, mb);
+  int sh = ea + eb - 2150 + 64;       // product * 2^64 = (hi:lo) * 2^sh
+  unsigned long long r;
+  if (sh >= 64) r = 0ull;
+  else if (sh > 0) r = lo << sh;
+  else if (sh == 0) r = lo;
+  else if (sh > -64) r = (lo >> (-sh)) | (hi << (64 + sh));
+  else if (sh == -64) r = hi;
+  else if (sh > -128) r = hi >> (-sh - 64);
+  else r = 0ull;
+  return ((ua ^ ub) >> 63) ? (0ull - r) : r;
+}
+
+// ----------------------------------------------------------------------------
+// launchers (defined in prep.cu / spa.cu), all on `st`
+// ----------------------------------------------------------------------------
+struct Scratch;  // defined in emri_fd.cu
+
+struct DevInputs {
+  const double *t, *phi_phi, *phi_r, *omega_phi, *omega_r;
+  const int *l, *m, *n;
+  const double* amp;
+  const double *theta, *phi, *prefactor;
+  const double* freqs;
+  void *h_plus, *h_cross;
+};
+
+struct DevScratch {
+  int* status;
+  unsigned long long* counters;   // [0] tile queue, [1] mode-bins, [2] runs total, [3] busy tiles
+  WfInfo* wf;
+  ModeInfo* modes;
+  double *spl_cp, *spl_im;        // [sum K] Thomas factors per waveform knot
+  double* fundM;                  // [4][sum K]
+  double* ampM;                   // [sum N_m K][2]
+  SegCore* core;
+  SegAmp64* amp64;
+  SegAmp32* amp32;
+  SegCrit* crit;
+  long long* keyF;                // [sum N_m K]
+  int* run_cnt;                   // [sum N_m + 1], exclusive-scanned in place
+  Run* runs;
+  double2* runF;                  // [run_cap] (F at run start, F at run end)
+  RunBins* rbins;
+  long long run_cap;
+  double2* tab;                   // [kTabN] e^{2 pi i k / kTabN}
+};
+
+struct CallShape {
+  int n_wf;
+  long long K_total, nm_total, nf_total, seg_total, tiles_total, amp_total;
+  int max_K;
+  int tile_bins;
+  int conj;
+  int precision;
+};
+
+constexpr int kPrepKernels = 12;   // kernels launched by launch_prep (memsets excluded)
+
+void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st);
+void launch_spa(const CallShape& cs, const DevInputs& in, const DevScratch& s, int num_sms, cudaStream_t st);
+void launch_table(double2* tab, cudaStream_t st);
+
+}  // namespace emrifd

@@ -1,0 +1,355 @@
+// C ABI of the GB300 SPA mode sum: plan lifetime, host-side validation,
+// host-pointer staging and the launch sequence (see include/emri_fd.h).
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/emri_fd.h"
+#include "common.cuh"
+
+using namespace emrifd;
+
+struct emri_fd_plan_s {
+  emri_fd_desc desc;
+  cudaStream_t stream;
+  int device = 0, num_sms = 0;
+  long long cap_K = 0, cap_nm = 0, cap_nf = 0, cap_seg = 0, cap_amp = 0;
+  DevScratch s{};
+  WfInfo* wf_pinned = nullptr;       // host copy uploaded each call
+  cudaEvent_t wf_done = nullptr;     // guards reuse of wf_pinned
+  unsigned long long* cnt_pinned = nullptr;
+  // staging for host-memory inputs / outputs
+  void* stage[16] = {};
+  size_t stage_sz[16] = {};
+  // last call's shape (for stats)
+  long long last_tiles = 0, last_nm = 0;
+  // optional event timing of the output kernel and of the preparation kernels
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;       // triples (prep start, spa start, spa end) per call
+  int ev_used = 0;
+  long long launches = 0;            // kernels launched by calls since the last profile reset
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+
+template <typename T>
+emri_fd_status dalloc(emri_fd_plan_s* p, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_OOM; }
+  p->allocs.push_back(q);
+  *ptr = static_cast<T*>(q);
+  return EMRI_FD_OK;
+}
+
+bool is_device_ptr(const void* ptr) {
+  if (!ptr) return true;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// returns a device pointer holding `bytes` of src (staged through a plan buffer if src is host memory)
+emri_fd_status stage_in(emri_fd_plan_s* p, int slot, const void* src, size_t bytes, const void** out) {
+  if (bytes == 0 || is_device_ptr(src)) { *out = src; return EMRI_FD_OK; }
+  if (p->stage_sz[slot] < bytes) {
+    if (p->stage[slot]) cudaFree(p->stage[slot]);
+    p->stage[slot] = nullptr;
+    p->stage_sz[slot] = 0;
+    if (cudaMalloc(&p->stage[slot], bytes) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_OOM; }
+    p->stage_sz[slot] = bytes;
+  }
+  if (cudaMemcpyAsync(p->stage[slot], src, bytes, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+    return EMRI_FD_ERR_CUDA;
+  *out = p->stage[slot];
+  return EMRI_FD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* emri_fd_strerror(emri_fd_status s) {
+  switch (s) {
+    case EMRI_FD_OK: return "ok";
+    case EMRI_FD_ERR_ARG: return "invalid argument";
+    case EMRI_FD_ERR_KNOTS: return "knots: fewer than 4 or times not strictly increasing";
+    case EMRI_FD_ERR_FREQ: return "frequencies not strictly increasing or not positive";
+    case EMRI_FD_ERR_MODE: return "invalid mode numbers";
+    case EMRI_FD_ERR_NONFINITE: return "non-finite input value";
+    case EMRI_FD_ERR_CAPACITY: return "size above the plan's capacity";
+    case EMRI_FD_ERR_CUDA: return "CUDA runtime error";
+    case EMRI_FD_ERR_OOM: return "device allocation failed";
+    case EMRI_FD_ERR_TIMEOUT: return "bounded device wait timed out";
+  }
+  return "unknown status";
+}
+
+void emri_fd_plan_destroy(emri_fd_plan_t p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->stream);
+  for (void* q : p->allocs) cudaFree(q);
+  for (int i = 0; i < 16; i++) if (p->stage[i]) cudaFree(p->stage[i]);
+  if (p->wf_pinned) cudaFreeHost(p->wf_pinned);
+  if (p->cnt_pinned) cudaFreeHost(p->cnt_pinned);
+  if (p->wf_done) cudaEventDestroy(p->wf_done);
+  for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete p;
+}
+
+emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* stream) {
+  if (!out || !d) return EMRI_FD_ERR_ARG;
+  *out = nullptr;
+  if ((d->precision != EMRI_FD_FP64 && d->precision != EMRI_FD_MIXED) || (d->conj_partners != 0 && d->conj_partners != 1) ||
+      d->max_waveforms < 1 || d->max_waveforms > 65535 || d->max_knots < 4 || d->max_modes_total < 1 || d->max_bins_total < 1 ||
+      d->max_bins_total > 2000000000LL || d->max_knots_total < 0 ||
+      !(d->tile_bins == 0 || d->tile_bins == 32 || d->tile_bins == 64 || d->tile_bins == 128))
+    return EMRI_FD_ERR_ARG;
+  for (int i = 0; i < 7; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
+  emri_fd_plan_s* p = new emri_fd_plan_s();
+  p->desc = *d;
+  if (p->desc.tile_bins == 0) p->desc.tile_bins = 64;
+  p->stream = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&p->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    cudaGetLastError(); delete p; return EMRI_FD_ERR_CUDA;
+  }
+  p->cap_K = d->max_knots_total > 0 ? d->max_knots_total : (long long)d->max_waveforms * d->max_knots;
+  p->cap_nm = d->max_modes_total;
+  p->cap_nf = d->max_bins_total;
+  p->cap_seg = d->max_modes_total * (long long)(d->max_knots - 1);
+  p->cap_amp = d->max_modes_total * (long long)d->max_knots;
+  DevScratch& s = p->s;
+  s.run_cap = 12 * d->max_modes_total + 64;
+  emri_fd_status st = EMRI_FD_OK;
+#define AL(ptr, n) if (st == EMRI_FD_OK) st = dalloc(p, &(ptr), (size_t)(n))
+  AL(s.status, 1);
+  AL(s.counters, 8);
+  AL(s.wf, d->max_waveforms);
+  AL(s.modes, p->cap_nm);
+  AL(s.spl_cp, p->cap_K);
+  AL(s.spl_im, p->cap_K);
+  AL(s.fundM, 4 * p->cap_K);
+  AL(s.ampM, 2 * p->cap_amp);
+  AL(s.core, p->cap_seg);
+  if (d->precision == EMRI_FD_FP64) { AL(s.amp64, p->cap_seg); } else { AL(s.amp32, p->cap_seg); }
+  AL(s.crit, p->cap_seg);
+  AL(s.keyF, p->cap_amp);
+  AL(s.run_cnt, p->cap_nm + 1);
+  AL(s.runs, s.run_cap);
+  AL(s.runF, s.run_cap);
+  AL(s.rbins, s.run_cap);
+  AL(s.tab, kTabN);
+#undef AL
+  if (st == EMRI_FD_OK && (cudaMallocHost(&p->wf_pinned, sizeof(WfInfo) * d->max_waveforms) != cudaSuccess ||
+                           cudaMallocHost(&p->cnt_pinned, sizeof(unsigned long long) * 8) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&p->wf_done, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    st = EMRI_FD_ERR_OOM;
+  }
+  if (st == EMRI_FD_OK) {
+    cudaMemsetAsync(s.status, 0, sizeof(int), p->stream);
+    cudaMemsetAsync(s.counters, 0, 8 * sizeof(unsigned long long), p->stream);
+    launch_table(s.tab, p->stream);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(p->stream) != cudaSuccess) st = EMRI_FD_ERR_CUDA;
+  }
+  if (st != EMRI_FD_OK) { emri_fd_plan_destroy(p); return st; }
+  *out = p;
+  return EMRI_FD_OK;
+}
+
+emri_fd_status emri_fd_sum_modes(emri_fd_plan_t p, int n_wf, const long long* knot_off, const long long* mode_off,
+                                 const long long* freq_off, const double* t, const double* phi_phi,
+                                 const double* phi_r, const double* omega_phi, const double* omega_r, const int* l,
+                                 const int* m, const int* n, const double* amp, const double* theta,
+                                 const double* phi, const double* prefactor, const double* freqs, void* h_plus,
+                                 void* h_cross) {
+  if (!p || n_wf < 1 || !knot_off || !mode_off || !freq_off) return EMRI_FD_ERR_ARG;
+  if (n_wf > p->desc.max_waveforms) return EMRI_FD_ERR_CAPACITY;
+  if (knot_off[0] != 0 || mode_off[0] != 0 || freq_off[0] != 0) return EMRI_FD_ERR_ARG;
+  const int TB = p->desc.tile_bins;
+  // host-side shape checks; the pinned table may still be read by the previous call's copy
+  if (cudaEventSynchronize(p->wf_done) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_CUDA; }
+  CallShape cs{};
+  cs.n_wf = n_wf;
+  cs.tile_bins = TB;
+  cs.conj = p->desc.conj_partners;
+  cs.precision = p->desc.precision;
+  long long amp_base = 0, seg_base = 0, tiles = 0;
+  int maxK = 0;
+  for (int w = 0; w < n_wf; w++) {
+    long long K = knot_off[w + 1] - knot_off[w], nm = mode_off[w + 1] - mode_off[w], nf = freq_off[w + 1] - freq_off[w];
+    if (K < 0 || nm < 0 || nf < 0) return EMRI_FD_ERR_ARG;
+    if (K < 4) return EMRI_FD_ERR_KNOTS;
+    if (K > p->desc.max_knots) return EMRI_FD_ERR_CAPACITY;
+    WfInfo& W = p->wf_pinned[w];
+    W.ko = knot_off[w]; W.K = K; W.mo = mode_off[w]; W.nm = nm; W.fo = freq_off[w]; W.nf = nf;
+    W.amp_base = amp_base; W.seg_base = seg_base;
+    W.tile_base = tiles; W.ntiles = (nf + TB - 1) / TB;
+    W.run_base = 0; W.nruns = 0;
+    amp_base += nm * K;
+    seg_base += nm * (K - 1);
+    tiles += W.ntiles;
+    if (K > maxK) maxK = (int)K;
+  }
+  cs.K_total = knot_off[n_wf];
+  cs.nm_total = mode_off[n_wf];
+  cs.nf_total = freq_off[n_wf];
+  cs.seg_total = seg_base;
+  cs.amp_total = amp_base;
+  cs.tiles_total = tiles;
+  cs.max_K = maxK;
+  if (cs.K_total > p->cap_K || cs.nm_total > p->cap_nm || cs.nf_total > p->cap_nf || cs.seg_total > p->cap_seg ||
+      cs.amp_total > p->cap_amp)
+    return EMRI_FD_ERR_CAPACITY;
+  if (!t || !phi_phi || !phi_r || !omega_phi || !omega_r || !theta || !phi || !prefactor) return EMRI_FD_ERR_ARG;
+  if (cs.nm_total > 0 && (!l || !m || !n || !amp)) return EMRI_FD_ERR_ARG;
+  if (cs.nf_total > 0 && (!freqs || !h_plus || !h_cross)) return EMRI_FD_ERR_ARG;
+  if (cs.nm_total == 0) cs.nm_total = 0;
+
+  DevInputs in{};
+  emri_fd_status st = EMRI_FD_OK;
+  const size_t kb = sizeof(double) * cs.K_total;
+  const void* q;
+#define STG(slot, ptr, bytes, field, type)                            \
+  if (st == EMRI_FD_OK) {                                               \
+    st = stage_in(p, slot, ptr, bytes, &q);                             \
+    in.field = static_cast<type>(q);                                    \
+  }
+  STG(0, t, kb, t, const double*);
+  STG(1, phi_phi, kb, phi_phi, const double*);
+  STG(2, phi_r, kb, phi_r, const double*);
+  STG(3, omega_phi, kb, omega_phi, const double*);
+  STG(4, omega_r, kb, omega_r, const double*);
+  STG(5, l, sizeof(int) * cs.nm_total, l, const int*);
+  STG(6, m, sizeof(int) * cs.nm_total, m, const int*);
+  STG(7, n, sizeof(int) * cs.nm_total, n, const int*);
+  STG(8, amp, 2 * sizeof(double) * cs.amp_total, amp, const double*);
+  STG(9, theta, sizeof(double) * n_wf, theta, const double*);
+  STG(10, phi, sizeof(double) * n_wf, phi, const double*);
+  STG(11, prefactor, sizeof(double) * n_wf, prefactor, const double*);
+  STG(12, freqs, sizeof(double) * cs.nf_total, freqs, const double*);
+#undef STG
+  if (st != EMRI_FD_OK) return st;
+  const size_t ob = (p->desc.precision == EMRI_FD_FP64 ? 16 : 8) * (size_t)cs.nf_total;
+  const bool host_out = cs.nf_total > 0 && (!is_device_ptr(h_plus) || !is_device_ptr(h_cross));
+  in.h_plus = h_plus;
+  in.h_cross = h_cross;
+  if (host_out) {
+    for (int slot = 13; slot <= 14; slot++) {
+      if (p->stage_sz[slot] < ob) {
+        if (p->stage[slot]) cudaFree(p->stage[slot]);
+        p->stage[slot] = nullptr; p->stage_sz[slot] = 0;
+        if (cudaMalloc(&p->stage[slot], ob) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_OOM; }
+        p->stage_sz[slot] = ob;
+      }
+    }
+    in.h_plus = p->stage[13];
+    in.h_cross = p->stage[14];
+  }
+  cudaStream_t stm = p->stream;
+  if (cudaMemcpyAsync(p->s.wf, p->wf_pinned, sizeof(WfInfo) * n_wf, cudaMemcpyHostToDevice, stm) != cudaSuccess ||
+      cudaEventRecord(p->wf_done, stm) != cudaSuccess)
+    return EMRI_FD_ERR_CUDA;
+  cudaMemsetAsync(p->s.counters, 0, 8 * sizeof(unsigned long long), stm);
+  cudaEvent_t* E = nullptr;
+  if (p->profiling && p->ev_used + 3 <= (int)p->ev.size()) {
+    E = &p->ev[p->ev_used];
+    p->ev_used += 3;
+    cudaEventRecord(E[0], stm);
+  }
+  if (cs.nm_total > 0) {
+    launch_prep(cs, in, p->s, stm);
+    p->launches += kPrepKernels;
+  } else {
+    // no modes: every run list is empty
+    cudaMemsetAsync(p->s.run_cnt, 0, sizeof(int), stm);
+  }
+  if (cs.nf_total > 0) {
+    if (cs.nm_total == 0) {
+      cudaMemsetAsync(in.h_plus, 0, ob, stm);
+      cudaMemsetAsync(in.h_cross, 0, ob, stm);
+    } else {
+      if (E) cudaEventRecord(E[1], stm);
+      launch_spa(cs, in, p->s, p->num_sms, stm);
+      if (E) cudaEventRecord(E[2], stm);
+      p->launches += 1;
+    }
+  }
+  if (E && !(cs.nf_total > 0 && cs.nm_total > 0)) {
+    cudaEventRecord(E[1], stm);
+    cudaEventRecord(E[2], stm);
+  }
+  p->last_tiles = cs.tiles_total;
+  p->last_nm = cs.nm_total;
+  if (cudaGetLastError() != cudaSuccess) return EMRI_FD_ERR_CUDA;
+  if (host_out) {
+    if (cudaMemcpyAsync(h_plus, in.h_plus, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess ||
+        cudaMemcpyAsync(h_cross, in.h_cross, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess ||
+        cudaStreamSynchronize(stm) != cudaSuccess)
+      return EMRI_FD_ERR_CUDA;
+  }
+  return EMRI_FD_OK;
+}
+
+emri_fd_status emri_fd_sync(emri_fd_plan_t p) {
+  if (!p) return EMRI_FD_ERR_ARG;
+  int hs = 0;
+  if (cudaMemcpyAsync(&hs, p->s.status, sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return EMRI_FD_ERR_CUDA;
+  }
+  cudaMemsetAsync(p->s.status, 0, sizeof(int), p->stream);
+  cudaStreamSynchronize(p->stream);
+  if (hs & ST_KNOTS) return EMRI_FD_ERR_KNOTS;
+  if (hs & ST_FREQ) return EMRI_FD_ERR_FREQ;
+  if (hs & ST_MODE) return EMRI_FD_ERR_MODE;
+  if (hs & ST_NONFINITE) return EMRI_FD_ERR_NONFINITE;
+  if (hs & ST_CAPACITY) return EMRI_FD_ERR_CAPACITY;
+  if (hs & ST_TIMEOUT) return EMRI_FD_ERR_TIMEOUT;
+  return EMRI_FD_OK;
+}
+
+emri_fd_status emri_fd_stats(emri_fd_plan_t p, long long* out, int nout) {
+  if (!p || !out || nout < 0) return EMRI_FD_ERR_ARG;
+  int runs = 0;
+  cudaMemcpyAsync(p->cnt_pinned, p->s.counters, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->stream);
+  if (p->last_nm > 0) cudaMemcpyAsync(&runs, p->s.run_cnt + p->last_nm, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_CUDA; }
+  double prep_ms = 0.0, spa_ms = 0.0;
+  for (int i = 0; i + 3 <= p->ev_used; i += 3) {
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, p->ev[i], p->ev[i + 1]);
+    cudaEventElapsedTime(&b, p->ev[i + 1], p->ev[i + 2]);
+    prep_ms += a;
+    spa_ms += b;
+  }
+  cudaGetLastError();
+  long long v[8] = {(long long)p->cnt_pinned[1], (long long)runs, p->last_tiles, (long long)p->cnt_pinned[3],
+                    (long long)(p->ev_used / 3), (long long)(spa_ms * 1e6), (long long)(prep_ms * 1e6), p->launches};
+  for (int i = 0; i < nout && i < 8; i++) out[i] = v[i];
+  return EMRI_FD_OK;
+}
+
+emri_fd_status emri_fd_profile(emri_fd_plan_t p, int enable) {
+  if (!p) return EMRI_FD_ERR_ARG;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_CUDA; }
+  if (enable && p->ev.empty()) {
+    p->ev.resize(3 * 1024);
+    for (auto& e : p->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_CUDA; }
+  }
+  p->profiling = enable != 0;
+  p->ev_used = 0;
+  p->launches = 0;
+  return EMRI_FD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,575 @@
+// Preparation kernels of the SPA mode sum: input checks, polarisation weights,
+// not-a-knot spline solves, per-(mode, segment) records, turnovers, and the
+// monotone branches ("runs") of every voice's frequency track.
+//
+// Paper: arXiv 2307.12585, Sec. 2.1 (not-a-knot splines of phases, frequencies
+// and amplitudes on the sparse trajectory), Sec. 2.2 (Eq. 6: per-segment
+// frequency cubic from the fundamental-frequency spline coefficients weighted
+// by the mode numbers; turnovers where dF/dt = 0, at most one per segment in
+// practice; the segment of each frequency is determined before the summation).
+#include "common.cuh"
+
+namespace emrifd {
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586;
+constexpr double kInv2PiHi = 0.15915494309189535;
+constexpr double kInv2PiLo = -9.839338337591243e-18;
+
+// ------------------------------------------------------------------ checks
+__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+__global__ void k_validate_knots(const WfInfo* wf, DevInputs in, int* status) {
+  const WfInfo W = wf[blockIdx.y];
+  int bad = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < W.K; k += (long long)gridDim.x * blockDim.x) {
+    long long i = W.ko + k;
+    double t = in.t[i];
+    if (!(finite(t) && finite(in.phi_phi[i]) && finite(in.phi_r[i]) && finite(in.omega_phi[i]) && finite(in.omega_r[i])))
+      bad |= ST_NONFINITE;
+    if (k + 1 < W.K && !(in.t[i + 1] > t)) bad |= ST_KNOTS;
+  }
+  if (bad) atomicOr(status, bad);
+}
+
+__global__ void k_validate_freqs(const WfInfo* wf, DevInputs in, int* status) {
+  const WfInfo W = wf[blockIdx.y];
+  int bad = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < W.nf; k += (long long)gridDim.x * blockDim.x) {
+    long long i = W.fo + k;
+    double f = in.freqs[i];
+    if (!(f > 0.0) || !finite(f)) bad |= ST_FREQ;
+    if (k + 1 < W.nf && !(in.freqs[i + 1] > f)) bad |= ST_FREQ;
+  }
+  if (bad) atomicOr(status, bad);
+}
+
+__global__ void k_validate_amp(long long n2, const double* amp, int* status) {
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
+    if (!finite(amp[i])) bad = ST_NONFINITE;
+  if (bad) atomicOr(status, bad);
+}
+
+// ---------------------------------------------------- spin-weighted harmonic
+// -2Y_lm(theta, phi) = S_lm(theta) e^{i m phi} with
+// S_lm = (-1)^s sqrt((2l+1)/4pi) d^l_{m,-s}(theta), s = -2, and the Wigner
+// small-d sum  d^l_{a,b}(x) = sum_k (-1)^{a-b+k} sqrt((l+a)!(l-a)!(l+b)!(l-b)!)
+//   / ((l+b-k)! k! (a-b+k)! (l-a-k)!) cos^{2l+b-a-2k}(x/2) sin^{a-b+2k}(x/2).
+__device__ double fact_d(int n) { double f = 1.0; for (int i = 2; i <= n; i++) f *= (double)i; return f; }
+__device__ double ipow(double x, int n) { double r = 1.0; for (int i = 0; i < n; i++) r *= x; return r; }
+
+__device__ double swsh_theta(int l, int m, double theta) {
+  const int a = m, b = 2;
+  double ch = cos(0.5 * theta), sh = sin(0.5 * theta);
+  double root = sqrt(fact_d(l + a) * fact_d(l - a) * fact_d(l + b) * fact_d(l - b));
+  double sum = 0.0;
+  for (int k = 0; k <= 2 * l; k++) {
+    int f0 = l + b - k, f1 = k, f2 = a - b + k, f3 = l - a - k;
+    if (f0 < 0 || f2 < 0 || f3 < 0) continue;
+    double term = root / (fact_d(f0) * fact_d(f1) * fact_d(f2) * fact_d(f3));
+    term *= ipow(ch, 2 * l + b - a - 2 * k) * ipow(sh, a - b + 2 * k);
+    sum += ((a - b + k) & 1) ? -term : term;
+  }
+  // (-1)^s = +1 for s = -2
+  return sqrt((2.0 * l + 1.0) / (2.0 * kTwoPi)) * sum;
+}
+
+__global__ void k_modes(int n_wf, const WfInfo* wf, DevInputs in, int conj, ModeInfo* modes,
+                        long long nm_total, int* status) {
+  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= nm_total) return;
+  int lo = 0, hi = n_wf - 1;     // waveform holding mode j: last w with mo <= j
+  while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (wf[mid].mo <= j) lo = mid; else hi = mid - 1; }
+  const WfInfo W = wf[lo];
+  int l = in.l[j], m = in.m[j], n = in.n[j];
+  ModeInfo M;
+  M.wf = lo; M.l = l; M.m = m; M.n = n;
+  M.seg_base = W.seg_base + (j - W.mo) * (W.K - 1);
+  M.key_base = W.amp_base + (j - W.mo) * W.K;
+  M.alpha = 0.0; M.beta = 0.0;
+  bool ok = (l >= 2 && l <= 20 && m >= -l && m <= l && (!conj || m >= 0) && n > -1000000 && n < 1000000);
+  double th = in.theta[lo];
+  if (!finite(th) || !finite(in.phi[lo]) || !finite(in.prefactor[lo])) atomicOr(status, ST_NONFINITE);
+  if (!ok) {
+    atomicOr(status, ST_MODE);
+  } else {
+    // c+ = alpha e^{i m phi}, cx = i beta e^{i m phi} (the e^{i m phi} goes into the phase)
+    double S = swsh_theta(l, m, th);
+    if (conj) {
+      double Sp = swsh_theta(l, -m, th) * ((l & 1) ? -1.0 : 1.0);
+      M.alpha = 0.5 * (S + Sp);
+      M.beta = 0.5 * (S - Sp);
+    } else {
+      M.alpha = 0.5 * S;
+      M.beta = 0.5 * S;
+    }
+  }
+  modes[j] = M;
+}
+
+// --------------------------------------------------------- not-a-knot splines
+// Unknowns: knot second derivatives M_0..M_{K-1}.  Interior rows (k=1..K-2):
+//   h_{k-1} M_{k-1} + 2(h_{k-1}+h_k) M_k + h_k M_{k+1} = r_k,
+//   r_k = 6[(y_{k+1}-y_k)/h_k - (y_k-y_{k-1})/h_{k-1}].
+// Not-a-knot (third derivative continuous at t_1 and t_{K-2}) gives
+//   M_0 = ((h0+h1) M_1 - h0 M_2)/h1,  M_{K-1} = ((ha+hb) M_{K-2} - hb M_{K-3})/ha
+// (ha = h_{K-3}, hb = h_{K-2}); substituting them turns rows 1 and K-2 into
+//   (h0 + 2 h1) M_1 + (h1 - h0) M_2 = r_1 h1/(h0+h1),
+//   (ha - hb) M_{K-3} + (2 ha + hb) M_{K-2} = r_{K-2} ha/(ha+hb),
+// a diagonally dominant tridiagonal system in M_1..M_{K-2}, solved by the
+// Thomas algorithm.  The forward-sweep factors depend only on the knot times
+// and are computed once per waveform.
+__device__ __forceinline__ void tri_row(const double* t, int K, int i, double& a, double& b, double& c, double& scale) {
+  double h0 = t[i] - t[i - 1], h1 = t[i + 1] - t[i];
+  scale = 1.0;
+  if (i == 1) { a = 0.0; b = h0 + 2.0 * h1; c = h1 - h0; scale = h1 / (h0 + h1); if (K == 4) {} }
+  else if (i == K - 2) {
+    double ha = h0, hb = h1;
+    a = ha - hb; b = 2.0 * ha + hb; c = 0.0; scale = ha / (ha + hb);
+  } else { a = h0; b = 2.0 * (h0 + h1); c = h1; }
+}
+
+__global__ void k_spline_factor(int n_wf, const WfInfo* wf, const double* tall, double* cp, double* im) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n_wf) return;
+  const WfInfo W = wf[w];
+  const double* t = tall + W.ko;
+  int K = (int)W.K;
+  double cprev = 0.0;
+  for (int i = 1; i <= K - 2; i++) {
+    double a, b, c, s;
+    tri_row(t, K, i, a, b, c, s);
+    if (i == 1 && K == 4) { /* row 1 is also followed by the last row: keep c */ }
+    double mm = b - a * cprev;
+    double inv = 1.0 / mm;
+    double cc = (i == K - 2) ? 0.0 : c * inv;
+    cp[W.ko + i] = cc;
+    im[W.ko + i] = inv;
+    cprev = cc;
+  }
+}
+
+// one thread per series; y has stride ys, M is written with stride ms
+__device__ void spline_solve(const double* t, int K, const double* y, long long ys, double* M, long long ms,
+                             const double* cp, const double* im) {
+  double rp = 0.0;
+  for (int i = 1; i <= K - 2; i++) {
+    double h0 = t[i] - t[i - 1], h1 = t[i + 1] - t[i];
+    double r = 6.0 * ((y[(i + 1) * ys] - y[i * ys]) / h1 - (y[i * ys] - y[(i - 1) * ys]) / h0);
+    double a, b, c, s;
+    tri_row(t, K, i, a, b, c, s);
+    rp = (r * s - a * rp) * im[i];
+    M[i * ms] = rp;      // forward-swept right-hand side, overwritten below
+  }
+  double next = M[(K - 2) * ms];
+  for (int i = K - 3; i >= 1; i--) {
+    double v = M[i * ms] - cp[i] * next;
+    M[i * ms] = v;
+    next = v;
+  }
+  double h0 = t[1] - t[0], h1 = t[2] - t[1];
+  M[0] = ((h0 + h1) * M[ms] - h0 * M[2 * ms]) / h1;
+  double ha = t[K - 2] - t[K - 3], hb = t[K - 1] - t[K - 2];
+  M[(K - 1) * ms] = ((ha + hb) * M[(K - 2) * ms] - hb * M[(K - 3) * ms]) / ha;
+}
+
+__global__ void k_spline_solve(int n_wf, const WfInfo* wf, const ModeInfo* modes, long long nm_total, DevInputs in,
+                               const double* cp, const double* im, double* fundM, long long K_total, double* ampM) {
+  long long sid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long nfund = 4LL * n_wf;
+  if (sid < nfund) {
+    int w = (int)(sid >> 2), which = (int)(sid & 3);
+    const WfInfo W = wf[w];
+    const double* y = which == 0 ? in.phi_phi : which == 1 ? in.phi_r : which == 2 ? in.omega_phi : in.omega_r;
+    spline_solve(in.t + W.ko, (int)W.K, y + W.ko, 1, fundM + which * K_total + W.ko, 1, cp + W.ko, im + W.ko);
+    return;
+  }
+  sid -= nfund;
+  if (sid >= 2 * nm_total) return;
+  long long j = sid >> 1;
+  int part = (int)(sid & 1);
+  const ModeInfo Mi = modes[j];
+  const WfInfo W = wf[Mi.wf];
+  spline_solve(in.t + W.ko, (int)W.K, in.amp + 2 * Mi.key_base + part, 2, ampM + 2 * Mi.key_base + part, 2,
+               cp + W.ko, im + W.ko);
+}
+
+// ------------------------------------------------ per (mode, segment) records
+struct dd { double hi, lo; };
+__device__ __forceinline__ dd dd_two_prod(double a, double b) { dd r; r.hi = a * b; r.lo = fma(a, b, -r.hi); return r; }
+__device__ __forceinline__ dd dd_fast(double s, double e) { dd r; r.hi = s + e; r.lo = e - (r.hi - s); return r; }
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  double s = a.hi + b.hi, v = s - a.hi;
+  double e = (a.hi - (s - v)) + (b.hi - v);
+  return dd_fast(s, e + a.lo + b.lo);
+}
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  dd p = dd_two_prod(a.hi, b.hi);
+  return dd_fast(p.hi, p.lo + (a.hi * b.lo + a.lo * b.hi));
+}
+
+// knot frequency of mode (m, n) at knot i: the exact expression shared with
+// the ownership rule, evaluated without contraction
+__device__ __forceinline__ double knot_freq(int m, int n, double om_phi, double om_r) {
+  return __ddiv_rn(__dadd_rn(__dmul_rn((double)m, om_phi), __dmul_rn((double)n, om_r)), kTwoPi);
+}
+
+// spline coefficients in u over [t_s, t_s + h]: a + b u + c u^2 + d u^3
+__device__ __forceinline__ void ucoef(double y0, double y1, double M0, double M1, double h2, double* c) {
+  c[0] = y0;
+  c[1] = (y1 - y0) - h2 * (2.0 * M0 + M1) * (1.0 / 6.0);
+  c[2] = 0.5 * h2 * M0;
+  c[3] = h2 * (M1 - M0) * (1.0 / 6.0);
+}
+
+__global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, DevInputs in, const double* fundM,
+                           long long K_total, const double* ampM, long long seg_total, SegCore* core,
+                           SegAmp64* amp64, SegAmp32* amp32, SegCrit* crit, long long* keyF) {
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= seg_total) return;
+  int lo = 0, hi = n_wf - 1;
+  while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (wf[mid].seg_base <= r) lo = mid; else hi = mid - 1; }
+  const WfInfo W = wf[lo];
+  long long rr = r - W.seg_base;
+  long long Km1 = W.K - 1;
+  long long j = W.mo + rr / Km1;
+  int s = (int)(rr - (rr / Km1) * Km1);
+  const ModeInfo Mi = modes[j];
+  const int m = Mi.m, n = Mi.n;
+  long long i0 = W.ko + s;
+  double ts = in.t[i0], h = in.t[i0 + 1] - ts, h2 = h * h;
+  double cPp[4], cPr[4], cOp[4], cOr[4];
+  ucoef(in.phi_phi[i0], in.phi_phi[i0 + 1], fundM[i0], fundM[i0 + 1], h2, cPp);
+  ucoef(in.phi_r[i0], in.phi_r[i0 + 1], fundM[K_total + i0], fundM[K_total + i0 + 1], h2, cPr);
+  ucoef(in.omega_phi[i0], in.omega_phi[i0 + 1], fundM[2 * K_total + i0], fundM[2 * K_total + i0 + 1], h2, cOp);
+  ucoef(in.omega_r[i0], in.omega_r[i0 + 1], fundM[3 * K_total + i0], fundM[3 * K_total + i0 + 1], h2, cOr);
+  const double dm = (double)m, dn = (double)n;
+  SegCore C;
+  C.A = knot_freq(m, n, in.omega_phi[i0], in.omega_r[i0]);
+  C.b = (dm * cOp[1] + dn * cOr[1]) * kInv2PiHi;
+  C.c = (dm * cOp[2] + dn * cOr[2]) * kInv2PiHi;
+  C.d = (dm * cOp[3] + dn * cOr[3]) * kInv2PiHi;
+  C.c2 = 2.0 * C.c;
+  C.d3 = 3.0 * C.d;
+  double P1 = (dm * cPp[1] + dn * cPr[1]) * kInv2PiHi;
+  C.Q1 = fma(-C.A, h, P1);
+  C.P2 = (dm * cPp[2] + dn * cPr[2]) * kInv2PiHi;
+  C.P3 = (dm * cPp[3] + dn * cPr[3]) * kInv2PiHi;
+  C.h = h;
+  C.ts = ts;
+  // theta0 = frac((m Phi_phi_s + n Phi_r_s - m phi)/2pi), double-double then Q0.64
+  dd ph = dd_add(dd_two_prod(dm, in.phi_phi[i0]), dd_two_prod(dn, in.phi_r[i0]));
+  dd az = dd_two_prod(-dm, in.phi[lo]);
+  ph = dd_add(ph, az);
+  dd inv; inv.hi = kInv2PiHi; inv.lo = kInv2PiLo;
+  dd turns = dd_mul(ph, inv);
+  C.theta0 = q64_of(turns.hi) + q64_of(turns.lo);
+  C.bf = (float)C.b; C.cf = (float)C.c; C.df = (float)C.d; C.pad = 0.f;
+  core[r] = C;
+
+  // amplitude, scaled by prefactor sqrt(h) (the weight is sqrt(h)/sqrt|dF/du|)
+  double sc = in.prefactor[lo] * sqrt(h);
+  const double* am = ampM + 2 * (Mi.key_base + s);
+  const double* ay = in.amp + 2 * (Mi.key_base + s);
+  double cre[4], cim[4];
+  ucoef(ay[0], ay[2], am[0], am[2], h2, cre);
+  ucoef(ay[1], ay[3], am[1], am[3], h2, cim);
+  if (amp64) {
+    SegAmp64 A;
+    for (int q = 0; q < 4; q++) { A.re[q] = sc * cre[q]; A.im[q] = sc * cim[q]; }
+    amp64[r] = A;
+  }
+  if (amp32) {
+    SegAmp32 A;
+    for (int q = 0; q < 4; q++) { A.re[q] = (float)(sc * cre[q]); A.im[q] = (float)(sc * cim[q]); }
+    amp32[r] = A;
+  }
+
+  // turnovers: roots of dF/du = b + 2c u + 3d u^2 in (0, 1)
+  SegCrit X;
+  X.n = 0; X.u[0] = X.u[1] = 0.0; X.F[0] = X.F[1] = 0.0; X.pad[0] = X.pad[1] = X.pad[2] = 0;
+  {
+    double qa = C.d3, qb = C.c2, qc = C.b;
+    double rt[2]; int nr = 0;
+    if (qa == 0.0) {
+      if (qb != 0.0) rt[nr++] = -qc / qb;
+    } else {
+      double disc = qb * qb - 4.0 * qa * qc;
+      if (disc >= 0.0) {
+        double q = -0.5 * (qb + copysign(sqrt(disc), qb));
+        if (q != 0.0) { rt[nr++] = q / qa; rt[nr++] = qc / q; }
+        else rt[nr++] = 0.0;
+      }
+    }
+    for (int i = 0; i < nr; i++)
+      if (rt[i] > 0.0 && rt[i] < 1.0) X.u[X.n++] = rt[i];
+    if (X.n == 2 && X.u[1] < X.u[0]) { double tmp = X.u[0]; X.u[0] = X.u[1]; X.u[1] = tmp; }
+    if (X.n == 2 && X.u[1] == X.u[0]) X.n = 1;
+    for (int i = 0; i < X.n; i++) {
+      double u = X.u[i];
+      X.F[i] = C.A + u * (C.b + u * (C.c + u * C.d));
+    }
+  }
+  crit[r] = X;
+  keyF[Mi.key_base + s] = ordkey(C.A);
+  if (s == Km1 - 1) keyF[Mi.key_base + s + 1] = ordkey(knot_freq(m, n, in.omega_phi[i0 + 1], in.omega_r[i0 + 1]));
+}
+
+// ------------------------------------------------------------------ runs
+// Sub-pieces of segment s: the monotone pieces between 0, its turnovers and 1.
+// Their end frequencies are the knot expressions at u = 0, 1 and the cubic at
+// turnovers.  A run is a maximal sequence of consecutive sub-pieces with the
+// same (non-zero) direction; a flat piece (equal end frequencies) owns no
+// frequency and separates runs.
+struct SubPieces {
+  int n;              // 1..3
+  int dir[3];
+  double ua[3], ub[3], Fa[3], Fb[3];
+};
+
+__device__ __forceinline__ void sub_pieces(const SegCrit& X, double F0, double F1, SubPieces& P) {
+  double us[4], Fs[4];
+  int np = 0;
+  us[np] = 0.0; Fs[np++] = F0;
+  for (int i = 0; i < X.n; i++) { us[np] = X.u[i]; Fs[np++] = X.F[i]; }
+  us[np] = 1.0; Fs[np++] = F1;
+  P.n = np - 1;
+  for (int i = 0; i < P.n; i++) {
+    P.ua[i] = us[i]; P.ub[i] = us[i + 1]; P.Fa[i] = Fs[i]; P.Fb[i] = Fs[i + 1];
+    P.dir[i] = Fs[i + 1] > Fs[i] ? 1 : (Fs[i + 1] < Fs[i] ? -1 : 0);
+  }
+}
+
+// warp per mode; FILL=false counts runs into run_cnt, FILL=true writes them
+template <bool FILL>
+__global__ void k_runs(const WfInfo* wf, const ModeInfo* modes, long long nm_total, const SegCore* core,
+                       const SegCrit* crit, const long long* keyF, const int* run_off, Run* runs, double2* runF, long long run_cap,
+                       int* run_cnt, int* status) {
+  long long j = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (j >= nm_total) return;
+  const ModeInfo Mi = modes[j];
+  const WfInfo W = wf[Mi.wf];
+  const int nseg = (int)(W.K - 1);
+  int carry_dir = 0;          // direction of the last sub-piece before this chunk
+  int carry_cnt = 0;          // runs started before this chunk
+  long long base = FILL ? (long long)run_off[j] : 0;
+  for (int c0 = 0; c0 < nseg; c0 += 32) {
+    int s = c0 + lane;
+    bool valid = s < nseg;
+    SubPieces P; P.n = 0;
+    if (valid) {
+      const SegCore C = core[Mi.seg_base + s];
+      const SegCrit X = crit[Mi.seg_base + s];
+      // segment end frequency: the knot expression F_V(t_{s+1}), kept as a key
+      double F1 = unordkey(keyF[Mi.key_base + s + 1]);
+      sub_pieces(X, C.A, F1, P);
+    }
+    int first_dir = (valid && P.n > 0) ? P.dir[0] : 0;
+    int last_dir = (valid && P.n > 0) ? P.dir[P.n - 1] : 0;
+    int prev_last = __shfl_up_sync(0xffffffffu, last_dir, 1);
+    if (lane == 0) prev_last = carry_dir;
+    int next_first = __shfl_down_sync(0xffffffffu, first_dir, 1);
+    if (lane == 31 || s + 1 >= nseg) next_first = 0;   // next chunk's first handled by its own start test
+    int starts = 0;
+    int pd = prev_last;
+    for (int i = 0; i < P.n; i++) {
+      if (P.dir[i] != 0 && P.dir[i] != pd) starts++;
+      pd = P.dir[i];
+    }
+    // inclusive warp scan of starts
+    int incl = starts;
+    for (int o = 1; o < 32; o <<= 1) {
+      int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int excl = incl - starts;
+    int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (FILL && valid) {
+      int idx = carry_cnt + excl;     // runs started before this segment (within the mode)
+      pd = prev_last;
+      for (int i = 0; i < P.n; i++) {
+        int d = P.dir[i];
+        if (d != 0 && d != pd) {
+          long long rid = base + idx;
+          if (rid < run_cap) {
+            // start fields only: the end fields may be written by another lane
+            runs[rid].mode = (int)j;
+            runs[rid].dir = d;
+            runs[rid].s0 = s;
+            runs[rid].u0 = P.ua[i];
+            runF[rid].x = P.Fa[i];
+          }
+          idx++;
+        }
+        // end of a run: next sub-piece (in this segment or the next) has another direction
+        int nd = (i + 1 < P.n) ? P.dir[i + 1] : (s + 1 < nseg ? -2 : 0);
+        bool ends;
+        if (nd == -2) {
+          // first sub-piece of segment s+1: taken from the next lane, or re-derived at a chunk edge
+          int nf = next_first;
+          if (lane == 31) {
+            const SegCore C2 = core[Mi.seg_base + s + 1];
+            const SegCrit X2 = crit[Mi.seg_base + s + 1];
+            double F2 = unordkey(keyF[Mi.key_base + s + 2]);
+            SubPieces P2; sub_pieces(X2, C2.A, F2, P2);
+            nf = P2.dir[0];
+          }
+          ends = (d != 0 && nf != d);
+        } else {
+          ends = (d != 0 && nd != d);
+        }
+        if (ends) {
+          long long rid = base + idx - 1;
+          if (rid < run_cap) {
+            runs[rid].s1 = s;
+            runs[rid].u1 = P.ub[i];
+            runF[rid].y = P.Fb[i];
+          }
+        }
+        pd = d;
+      }
+    }
+    carry_cnt += total;
+    carry_dir = __shfl_sync(0xffffffffu, last_dir, 31);
+    if (c0 + 32 > nseg) {
+      // the chunk was partial: the true last direction is at lane nseg-1-c0
+      carry_dir = __shfl_sync(0xffffffffu, last_dir, (nseg - 1 - c0) & 31);
+    }
+  }
+  if (!FILL && lane == 0) run_cnt[j] = carry_cnt;
+  if (FILL && lane == 0 && base + carry_cnt > run_cap) atomicOr(status, ST_CAPACITY);
+}
+
+// exclusive scan of cnt[0..n) in place, total written to cnt[n]; one block
+__global__ void k_scan(int* cnt, long long n) {
+  __shared__ long long part[1024];
+  int tid = threadIdx.x;
+  long long per = (n + blockDim.x - 1) / blockDim.x;
+  long long b = tid * per, e = b + per < n ? b + per : n;
+  long long s = 0;
+  for (long long i = b; i < e; i++) s += cnt[i];
+  part[tid] = s;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    long long v = tid >= o ? part[tid - o] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  long long run = part[tid] - s;
+  for (long long i = b; i < e; i++) { long long c = cnt[i]; cnt[i] = (int)run; run += c; }
+  if (tid == blockDim.x - 1) cnt[n] = (int)part[tid];
+}
+
+__global__ void k_wf_runs(int n_wf, WfInfo* wf, const int* run_off, long long run_cap) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n_wf) return;
+  long long a = run_off[wf[w].mo], b = run_off[wf[w].mo + wf[w].nm];
+  if (a > run_cap) a = run_cap;
+  if (b > run_cap) b = run_cap;
+  wf[w].run_base = a;
+  wf[w].nruns = b - a;
+}
+
+// lower_bound / upper_bound on the ascending bins of one waveform
+__device__ __forceinline__ long long lbound(const double* f, long long n, double x) {
+  long long a = 0, b = n;
+  while (a < b) { long long c = (a + b) >> 1; if (f[c] < x) a = c + 1; else b = c; }
+  return a;
+}
+__device__ __forceinline__ long long ubound(const double* f, long long n, double x) {
+  long long a = 0, b = n;
+  while (a < b) { long long c = (a + b) >> 1; if (f[c] <= x) a = c + 1; else b = c; }
+  return a;
+}
+
+// Output-bin ranges of each run.  Increasing runs own [F_start, F_end),
+// decreasing runs own (F_end, F_start]; the negative-frequency part serves
+// bins f with -f in that range (they enter through conj H(-f)).
+__global__ void k_run_bins(const WfInfo* wf, const ModeInfo* modes, long long nm_total, const int* run_total,
+                           const Run* runs, const double2* runF, long long run_cap, const double* freqs, RunBins* rb,
+                           unsigned long long* counters, int* status) {
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long nr = *run_total;
+  if (nr > run_cap) nr = run_cap;
+  if (r >= nr) return;
+  const Run R = runs[r];
+  RunBins B;
+  // a run whose fields were not all written (cannot happen when the count and
+  // fill passes agree) is made empty, so that no later kernel indexes with it
+  if (R.mode < 0 || R.mode >= nm_total) {
+    B.b0p = B.b1p = B.b0n = B.b1n = 0;
+    rb[r] = B;
+    atomicOr(status, ST_CAPACITY);
+    return;
+  }
+  const WfInfo W = wf[modes[R.mode].wf];
+  if (R.s0 < 0 || R.s1 < R.s0 || R.s1 >= W.K - 1 || R.dir == 0) {
+    B.b0p = B.b1p = B.b0n = B.b1n = (int)W.fo;
+    rb[r] = B;
+    atomicOr(status, ST_CAPACITY);
+    return;
+  }
+  const double* f = freqs + W.fo;
+  double Fs = runF[r].x, Fe = runF[r].y;
+  long long b0p, b1p, b0n, b1n;
+  if (R.dir > 0) {
+    b0p = lbound(f, W.nf, Fs); b1p = lbound(f, W.nf, Fe);
+    b0n = ubound(f, W.nf, -Fe); b1n = ubound(f, W.nf, -Fs);
+  } else {
+    b0p = ubound(f, W.nf, Fe); b1p = ubound(f, W.nf, Fs);
+    b0n = lbound(f, W.nf, -Fs); b1n = lbound(f, W.nf, -Fe);
+  }
+  if (b1p < b0p) b1p = b0p;
+  if (b1n < b0n) b1n = b0n;
+  B.b0p = (int)(W.fo + b0p); B.b1p = (int)(W.fo + b1p);
+  B.b0n = (int)(W.fo + b0n); B.b1n = (int)(W.fo + b1n);
+  rb[r] = B;
+  unsigned long long cnt = (unsigned long long)((b1p - b0p) + (b1n - b0n));
+  if (cnt) atomicAdd(&counters[1], cnt);
+}
+
+__global__ void k_table(double2* tab) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kTabN) return;
+  double s, c;
+  sincospi((double)k / (double)(kTabN / 2), &s, &c);
+  tab[k] = make_double2(c, s);
+}
+
+}  // namespace
+
+void launch_table(double2* tab, cudaStream_t st) { k_table<<<(kTabN + 255) / 256, 256, 0, st>>>(tab); }
+
+void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st) {
+  dim3 gk(8, cs.n_wf);
+  k_validate_knots<<<gk, 256, 0, st>>>(s.wf, in, s.status);
+  dim3 gf(64, cs.n_wf);
+  k_validate_freqs<<<gf, 256, 0, st>>>(s.wf, in, s.status);
+  k_validate_amp<<<256, 256, 0, st>>>(2 * cs.amp_total, in.amp, s.status);
+  k_modes<<<(unsigned)((cs.nm_total + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes, cs.nm_total,
+                                                                  s.status);
+  k_spline_factor<<<(cs.n_wf + 63) / 64, 64, 0, st>>>(cs.n_wf, s.wf, in.t, s.spl_cp, s.spl_im);
+  long long nser = 4LL * cs.n_wf + 2 * cs.nm_total;
+  k_spline_solve<<<(unsigned)((nser + 127) / 128), 128, 0, st>>>(cs.n_wf, s.wf, s.modes, cs.nm_total, in, s.spl_cp,
+                                                                 s.spl_im, s.fundM, cs.K_total, s.ampM);
+  k_seg_prep<<<(unsigned)((cs.seg_total + 127) / 128), 128, 0, st>>>(
+      cs.n_wf, s.wf, s.modes, in, s.fundM, cs.K_total, s.ampM, cs.seg_total, s.core,
+      cs.precision == 0 ? s.amp64 : nullptr, cs.precision == 1 ? s.amp32 : nullptr, s.crit, s.keyF);
+  unsigned wblocks = (unsigned)((cs.nm_total * 32 + 255) / 256);
+  k_runs<false><<<wblocks, 256, 0, st>>>(s.wf, s.modes, cs.nm_total, s.core, s.crit, s.keyF, nullptr, nullptr,
+                                         nullptr, s.run_cap, s.run_cnt, s.status);
+  k_scan<<<1, 1024, 0, st>>>(s.run_cnt, cs.nm_total);
+  k_wf_runs<<<(cs.n_wf + 63) / 64, 64, 0, st>>>(cs.n_wf, s.wf, s.run_cnt, s.run_cap);
+  cudaMemsetAsync(s.runs, 0xFF, sizeof(Run) * (size_t)s.run_cap, st);
+  k_runs<true><<<wblocks, 256, 0, st>>>(s.wf, s.modes, cs.nm_total, s.core, s.crit, s.keyF, s.run_cnt, s.runs,
+                                        s.runF, s.run_cap, nullptr, s.status);
+  k_run_bins<<<(unsigned)((s.run_cap + 255) / 256), 256, 0, st>>>(s.wf, s.modes, cs.nm_total, s.run_cnt + cs.nm_total,
+                                                                  s.runs, s.runF, s.run_cap, in.freqs, s.rbins,
+                                                                  s.counters, s.status);
+}
+
+}  // namespace emrifd
