@@ -38,13 +38,14 @@ FP64_PER_CLK_PER_SM = 2          # GB300 FP64 issue rate (1.25 TFLOP/s nominal a
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--waveforms", type=int, default=8)
+    ap.add_argument("--tile-bins", type=int, default=128)
     return ap.parse_args()
 
 
@@ -106,24 +107,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(w, budget_s=15.0, stride0=64):
+def cpu_oracle_rate(w, budget_s=15.0):
     """The CPU oracle on a strided sample of the waveform's bins (bins are
     independent, so the sample extrapolates); returns waveforms/s, threads, sample text."""
     from oracle import oracle as O
     O.build()
     threads = O.default_threads()
-    stride = stride0
-    while True:
-        sel = w.freqs[::stride]
-        t0 = time.perf_counter()
-        O.sum_modes(w, freqs=sel, nthreads=threads)
-        dt = time.perf_counter() - t0
-        if dt > 0.5 * budget_s / 4 or stride <= 1:
-            break
-        stride = max(1, int(stride / max(2.0, (0.5 * budget_s / 4) / max(dt, 1e-3))))
-    # final timed sample sized to the budget
-    frac = min(1.0, dt / budget_s)
-    stride = max(1, int(stride * frac)) if frac < 1.0 else stride
+    stride = 256
+    sel = w.freqs[::stride]
+    t0 = time.perf_counter()
+    O.sum_modes(w, freqs=sel, nthreads=threads)
+    dt = time.perf_counter() - t0
+    # size the timed sample to about budget_s
+    stride = int(min(64, max(1, stride * dt / budget_s)))
     sel = w.freqs[::stride]
     t0 = time.perf_counter()
     O.sum_modes(w, freqs=sel, nthreads=threads)
@@ -179,7 +175,7 @@ def main():
     seeds = [1 + rank * nw + i for i in range(nw)]
     wfs = [synth.paper_config(s) for s in seeds]
     plan = api.Plan(args.precision, conj_partners=True, max_waveforms=1, max_knots=200,
-                    max_modes_total=2000, max_bins_total=wfs[0].n_freqs)
+                    max_modes_total=2000, max_bins_total=wfs[0].n_freqs, tile_bins=args.tile_bins)
     dev = [plan.upload(synth.concat([w])) for w in wfs]
     nf = wfs[0].n_freqs
     outs = [(torch.empty(nf, dtype=plan.out_dtype, device="cuda"), torch.empty(nf, dtype=plan.out_dtype, device="cuda"))

@@ -88,7 +88,7 @@ typedef struct {
   long long max_knots_total;/* sum of K over a call (0: max_waveforms * max_knots) */
   long long max_modes_total;/* sum of N_m over a call, >= 1 */
   long long max_bins_total; /* sum of N_f over a call, >= 1 */
-  int tile_bins;            /* output bins per work tile; 0 = default (64) */
+  int tile_bins;            /* output bins per work tile: 32, 64 or 128; 0 = default (128) */
   int reserved[7];          /* must be zero */
 } emri_fd_desc;
 

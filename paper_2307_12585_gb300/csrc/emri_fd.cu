@@ -114,7 +114,7 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
   for (int i = 0; i < 7; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
   emri_fd_plan_s* p = new emri_fd_plan_s();
   p->desc = *d;
-  if (p->desc.tile_bins == 0) p->desc.tile_bins = 64;
+  if (p->desc.tile_bins == 0) p->desc.tile_bins = 128;
   p->stream = static_cast<cudaStream_t>(stream);
   if (cudaGetDevice(&p->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
