@@ -153,6 +153,42 @@ emri_fd_status emri_fd_stats(emri_fd_plan_t plan, long long* out, int n);
  */
 emri_fd_status emri_fd_profile(emri_fd_plan_t plan, int enable);
 
+/*
+ * No-allocation variant of emri_fd_sum_modes for one waveform (FP64 form,
+ * complex128 outputs).  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory -- code running while another
+ * component (e.g. a framework's caching allocator) holds the device's memory,
+ * latency-critical code that cannot afford cudaMalloc/cudaFree (which may
+ * synchronise the device), and plug-ins or callbacks that must not call the
+ * allocator.  It calls no cudaMalloc, cudaFree or other allocating routine:
+ * all scratch lives in one file-scope __device__ array of 6,505,984 bytes
+ * (6.2 MiB), which every GPU that loads the library holds until the process
+ * exits.
+ *   Limits: n_knots in [4, EMRI_FD_NOALLOC_MAX_KNOTS], n_modes in
+ *   [1, EMRI_FD_NOALLOC_MAX_MODES], n_freqs in [1, EMRI_FD_NOALLOC_MAX_BINS];
+ *   larger sizes return EMRI_FD_ERR_CAPACITY before anything is launched.
+ *   Arguments: as emri_fd_sum_modes for a single waveform (K = n_knots,
+ *   N_m = n_modes, N_f = n_freqs), with the viewing angles and prefactor
+ *   passed by value.  Every array must be DEVICE memory (host pointers give
+ *   EMRI_FD_ERR_ARG).  stream: a cudaStream_t on the current device.
+ *   Set-up: the first call on a device (with that device current) looks up the
+ *   array's device address and fills a sin/cos table in it; make that first
+ *   call before any stream capture.
+ *   The call waits for its stream and returns the status of the device-side
+ *   checks.  Every call uses the same array and overwrites the previous
+ *   call's contents; calls whose GPU work overlaps in time (e.g. from two host
+ *   threads on two streams) race on it and must be serialised by the caller.
+ */
+#define EMRI_FD_NOALLOC_MAX_KNOTS 200
+#define EMRI_FD_NOALLOC_MAX_MODES 128
+#define EMRI_FD_NOALLOC_MAX_BINS (1LL << 30)
+emri_fd_status emri_fd_sum_modes_noalloc(int conj_partners, long long n_knots, long long n_modes,
+                                         long long n_freqs, const double* t, const double* phi_phi,
+                                         const double* phi_r, const double* omega_phi, const double* omega_r,
+                                         const int* l, const int* m, const int* n, const double* amp,
+                                         double theta, double phi, double prefactor, const double* freqs,
+                                         void* h_plus, void* h_cross, void* stream);
+
 /* Release the plan and its device memory (synchronises its stream first). */
 void emri_fd_plan_destroy(emri_fd_plan_t plan);
 

@@ -19,7 +19,7 @@ STATUS = {0: "EMRI_FD_OK", 1: "EMRI_FD_ERR_ARG", 2: "EMRI_FD_ERR_KNOTS", 3: "EMR
           4: "EMRI_FD_ERR_MODE", 5: "EMRI_FD_ERR_NONFINITE", 6: "EMRI_FD_ERR_CAPACITY",
           7: "EMRI_FD_ERR_CUDA", 8: "EMRI_FD_ERR_OOM", 9: "EMRI_FD_ERR_TIMEOUT"}
 EXPORTS = ("emri_fd_plan", "emri_fd_sum_modes", "emri_fd_sync", "emri_fd_stats", "emri_fd_profile",
-           "emri_fd_plan_destroy", "emri_fd_strerror")
+           "emri_fd_plan_destroy", "emri_fd_strerror", "emri_fd_sum_modes_noalloc")
 
 
 class EmriFdError(RuntimeError):
@@ -61,6 +61,9 @@ def lib():
         L.emri_fd_stats.restype = C.c_int
         L.emri_fd_profile.argtypes = [vp, C.c_int]
         L.emri_fd_profile.restype = C.c_int
+        L.emri_fd_sum_modes_noalloc.argtypes = ([C.c_int, C.c_longlong, C.c_longlong, C.c_longlong] + [dp] * 5 +
+                                                [ip] * 3 + [dp] + [C.c_double] * 3 + [dp, vp, vp, vp])
+        L.emri_fd_sum_modes_noalloc.restype = C.c_int
         L.emri_fd_plan_destroy.argtypes = [vp]
         L.emri_fd_plan_destroy.restype = None
         L.emri_fd_strerror.argtypes = [C.c_int]
@@ -94,6 +97,19 @@ def emri_fd_sum_modes(plan, n_waveforms, knot_off, mode_off, freq_off, t, phi_ph
     return lib().emri_fd_sum_modes(C.c_void_p(plan), int(n_waveforms), *[C.c_void_p(int(x)) for x in (
         knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r, l, m, n, amp, theta, phi,
         prefactor, freqs, h_plus, h_cross)])
+
+
+def emri_fd_sum_modes_noalloc(conj_partners, n_knots, n_modes, n_freqs, t, phi_phi, phi_r, omega_phi, omega_r,
+                              l, m, n, amp, theta, phi, prefactor, freqs, h_plus, h_cross, stream=0) -> int:
+    """The no-allocation single-waveform entry point: for callers that cannot
+    allocate device memory (another allocator owns the device's memory, or the
+    code path must not call cudaMalloc/cudaFree).  Arrays are device addresses
+    (ints); angles and prefactor are floats.  Synchronous; returns the status."""
+    return lib().emri_fd_sum_modes_noalloc(int(conj_partners), int(n_knots), int(n_modes), int(n_freqs),
+                                           *[C.c_void_p(int(x)) for x in (t, phi_phi, phi_r, omega_phi, omega_r,
+                                                                          l, m, n, amp)],
+                                           float(theta), float(phi), float(prefactor), C.c_void_p(int(freqs)),
+                                           C.c_void_p(int(h_plus)), C.c_void_p(int(h_cross)), C.c_void_p(int(stream)))
 
 
 def emri_fd_sync(plan) -> int:
