@@ -360,6 +360,119 @@ static piece_t* build_pieces(const traj_t* T, const voice_t* V, int nv, const do
   return P;
 }
 
+/* ------------------------------------------------------------------ */
+/* shared set-up: splines, voices, monotone pieces                     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  int K, nm, nv, conj;
+  spl_sys_t S;
+  double* cf;          /* fundamental spline coef: Phi_phi, Phi_r, Om_phi, Om_r, each [K-1][4] */
+  double* ac;          /* voice amplitude coef: per voice Re [K-1][4] then Im [K-1][4] */
+  voice_t* V;
+  int* vmode;          /* input mode of each voice */
+  int* vpart;          /* 0: the listed mode, 1: its conjugate partner */
+  traj_t T;
+  piece_t* P;
+  long long np;
+} ctx_t;
+
+static void ctx_free(ctx_t* c) {
+  free(c->cf); free(c->ac); free(c->V); free(c->vmode); free(c->vpart); free(c->P); spl_free(&c->S);
+}
+
+static int ctx_init(ctx_t* c, int K, const double* t, const double* phi_phi, const double* phi_r,
+                    const double* omega_phi, const double* omega_r, int nm, const int* l, const int* m,
+                    const int* n, const double* amp, double theta, double phi, double prefactor,
+                    int conj_partners, long long nf, const double* freqs) {
+  memset(c, 0, sizeof(*c));
+  if (K < 4 || nm < 0 || nf < 0) return -1;
+  for (int k = 0; k + 1 < K; k++) if (!(t[k + 1] > t[k])) return -2;
+  for (long long i = 0; i < nf; i++) if (!(freqs[i] > 0.0) || (i && !(freqs[i] > freqs[i - 1]))) return -3;
+  for (int j = 0; j < nm; j++) if (l[j] < 2 || abs(m[j]) > l[j] || (conj_partners && m[j] < 0)) return -4;
+  c->K = K; c->nm = nm; c->conj = conj_partners;
+  if (spl_factor(&c->S, K, t)) { spl_free(&c->S); return -5; }
+  double* work = (double*)malloc(sizeof(double) * K);
+  double* y = (double*)malloc(sizeof(double) * K);
+  size_t sc = (size_t)(K - 1) * 4;
+  c->cf = (double*)malloc(sizeof(double) * sc * 4);
+  int nv = conj_partners ? 2 * nm : nm;
+  c->nv = nv;
+  c->ac = (double*)malloc(sizeof(double) * sc * 2 * (size_t)(nv > 0 ? nv : 1));
+  c->V = (voice_t*)malloc(sizeof(voice_t) * (size_t)(nv > 0 ? nv : 1));
+  c->vmode = (int*)malloc(sizeof(int) * (size_t)(nv > 0 ? nv : 1));
+  c->vpart = (int*)malloc(sizeof(int) * (size_t)(nv > 0 ? nv : 1));
+  traj_t* T = &c->T;
+  T->K = K; T->t = t; T->Op = omega_phi; T->Or = omega_r; T->prefactor = prefactor;
+  spl_coef(&c->S, phi_phi, c->cf + 0 * sc, work); spl_coef(&c->S, phi_r, c->cf + 1 * sc, work);
+  spl_coef(&c->S, omega_phi, c->cf + 2 * sc, work); spl_coef(&c->S, omega_r, c->cf + 3 * sc, work);
+  T->cPp = c->cf; T->cPr = c->cf + sc; T->cOp = c->cf + 2 * sc; T->cOr = c->cf + 3 * sc;
+  int iv = 0;
+  for (int j = 0; j < nm; j++) {
+    for (int part = 0; part < (conj_partners ? 2 : 1); part++) {
+      voice_t* v = &c->V[iv];
+      v->l = l[j]; v->m = part ? -m[j] : m[j]; v->n = part ? -n[j] : n[j];
+      double sgn = (l[j] & 1) ? -1.0 : 1.0;
+      double* cre = c->ac + (size_t)iv * 2 * sc; double* cim = cre + sc;
+      for (int k = 0; k < K; k++) y[k] = part ? sgn * amp[((size_t)j * K + k) * 2 + 0] : amp[((size_t)j * K + k) * 2 + 0];
+      spl_coef(&c->S, y, cre, work);
+      for (int k = 0; k < K; k++) y[k] = part ? -sgn * amp[((size_t)j * K + k) * 2 + 1] : amp[((size_t)j * K + k) * 2 + 1];
+      spl_coef(&c->S, y, cim, work);
+      v->are = cre; v->aim = cim;
+      oracle_swsh(-2, v->l, v->m, theta, phi, v->Y);
+      c->vmode[iv] = j; c->vpart[iv] = part;
+      iv++;
+    }
+  }
+  c->P = build_pieces(T, c->V, nv, freqs, nf, &c->np);
+  free(work); free(y);
+  return 0;
+}
+
+/* h+ and hx on the bins, plus counters */
+static void ctx_forward(const ctx_t* c, long long nf, const double* freqs, double* hp, double* hc,
+                        long long* stats, int nthreads) {
+  double* Hpos = (double*)calloc((size_t)(nf > 0 ? nf : 1) * 2, sizeof(double));
+  double* Hneg = (double*)calloc((size_t)(nf > 0 ? nf : 1) * 2, sizeof(double));
+  long long nev = 0, nzero = 0, np = c->np;
+  const piece_t* P = c->P;
+  if (nthreads < 1) nthreads = 1;
+  /* Parallel over contiguous chunks of bins; every bin sums its voices in
+   * ascending voice order, so the result does not depend on nthreads. */
+  long long nchunk = nthreads * 8LL;
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1) reduction(+ : nev, nzero)
+  for (long long ch = 0; ch < nchunk; ch++) {
+    long long b0 = nf * ch / nchunk, b1 = nf * (ch + 1) / nchunk;
+    if (b0 >= b1) continue;
+    for (long long ip = 0; ip < np; ip++) {
+      const piece_t* p = &P[ip];
+      const voice_t* v = &c->V[p->voice];
+      double fc[4];
+      int have_fc = 0;
+      for (int sgn = 0; sgn < 2; sgn++) {
+        long long lo = p->lo[sgn] > b0 ? p->lo[sgn] : b0;
+        long long hi = p->hi[sgn] < b1 ? p->hi[sgn] : b1;
+        if (lo >= hi) continue;
+        if (!have_fc) { voice_fcubic(&c->T, v->m, v->n, p->seg, fc); have_fc = 1; }
+        double* H = sgn ? Hneg : Hpos;
+        for (long long b = lo; b < hi; b++) {
+          double g = sgn ? -freqs[b] : freqs[b];
+          double x = bisect(fc, g, p->ta, p->tb, p->dir);
+          nzero += contrib(&c->T, v, p->seg, fc, g, x, H + 2 * b);
+          nev++;
+        }
+      }
+    }
+  }
+  for (long long b = 0; b < nf; b++) {
+    double pr = Hpos[2 * b], pi = Hpos[2 * b + 1], nr = Hneg[2 * b], ni = -Hneg[2 * b + 1]; /* conj H(-f) */
+    hp[2 * b] = 0.5 * (pr + nr);   hp[2 * b + 1] = 0.5 * (pi + ni);
+    /* hx = i/2 (H(f) - conj H(-f)) */
+    hc[2 * b] = -0.5 * (pi - ni);  hc[2 * b + 1] = 0.5 * (pr - nr);
+  }
+  if (stats) { stats[0] = nev; stats[1] = nzero; stats[2] = np; }
+  free(Hpos); free(Hneg);
+}
+
 /*
  * oracle_sum_modes: one waveform.
  *   K knots t[K]; phi_phi, phi_r, omega_phi, omega_r [K];
@@ -376,79 +489,186 @@ int oracle_sum_modes(int K, const double* t, const double* phi_phi, const double
                      double theta, double phi, double prefactor, int conj_partners,
                      long long nf, const double* freqs, double* hp, double* hc,
                      long long* stats, int nthreads) {
-  if (K < 4 || nm < 0 || nf < 0) return -1;
-  for (int k = 0; k + 1 < K; k++) if (!(t[k + 1] > t[k])) return -2;
-  for (long long i = 0; i < nf; i++) if (!(freqs[i] > 0.0) || (i && !(freqs[i] > freqs[i - 1]))) return -3;
-  for (int j = 0; j < nm; j++) if (l[j] < 2 || abs(m[j]) > l[j] || (conj_partners && m[j] < 0)) return -4;
+  ctx_t c;
+  int rc = ctx_init(&c, K, t, phi_phi, phi_r, omega_phi, omega_r, nm, l, m, n, amp, theta, phi, prefactor,
+                    conj_partners, nf, freqs);
+  if (rc) { ctx_free(&c); return rc; }
+  ctx_forward(&c, nf, freqs, hp, hc, stats, nthreads);
+  ctx_free(&c);
+  return 0;
+}
 
-  spl_sys_t S; if (spl_factor(&S, K, t)) { spl_free(&S); return -5; }
-  double* work = (double*)malloc(sizeof(double) * K);
-  double* y = (double*)malloc(sizeof(double) * K);
-  size_t sc = (size_t)(K - 1) * 4;
-  double* cf = (double*)malloc(sizeof(double) * sc * 4);
-  int nv = conj_partners ? 2 * nm : nm;
-  double* ac = (double*)malloc(sizeof(double) * sc * 2 * (size_t)nv);
-  voice_t* V = (voice_t*)malloc(sizeof(voice_t) * (size_t)(nv > 0 ? nv : 1));
-  traj_t T; T.K = K; T.t = t; T.Op = omega_phi; T.Or = omega_r; T.prefactor = prefactor;
-  spl_coef(&S, phi_phi, cf + 0 * sc, work); spl_coef(&S, phi_r, cf + 1 * sc, work);
-  spl_coef(&S, omega_phi, cf + 2 * sc, work); spl_coef(&S, omega_r, cf + 3 * sc, work);
-  T.cPp = cf; T.cPr = cf + sc; T.cOp = cf + 2 * sc; T.cOr = cf + 3 * sc;
-  int iv = 0;
-  for (int j = 0; j < nm; j++) {
-    for (int part = 0; part < (conj_partners ? 2 : 1); part++) {
-      voice_t* v = &V[iv];
-      v->l = l[j]; v->m = part ? -m[j] : m[j]; v->n = part ? -n[j] : n[j];
-      double sgn = (l[j] & 1) ? -1.0 : 1.0;
-      double* cre = ac + (size_t)iv * 2 * sc; double* cim = cre + sc;
-      for (int k = 0; k < K; k++) y[k] = part ? sgn * amp[((size_t)j * K + k) * 2 + 0] : amp[((size_t)j * K + k) * 2 + 0];
-      spl_coef(&S, y, cre, work);
-      for (int k = 0; k < K; k++) y[k] = part ? -sgn * amp[((size_t)j * K + k) * 2 + 1] : amp[((size_t)j * K + k) * 2 + 1];
-      spl_coef(&S, y, cim, work);
-      v->are = cre; v->aim = cim;
-      oracle_swsh(-2, v->l, v->m, theta, phi, v->Y);
-      iv++;
-    }
+/* ------------------------------------------------------------------ */
+/* Whittle log-likelihood and its gradient                              */
+/* ------------------------------------------------------------------ */
+/*
+ * L = -1/2 sum_alpha <d - h | d - h>_alpha with <a|b> = 4 Re sum_i a* b / S_i df
+ * (Eq. 13-14).  The gradient is the plain chain rule: with
+ * G_alpha = dL/dRe h_alpha + i dL/dIm h_alpha = 4 df (d - h)_alpha / S, a root
+ * contribution C = prefactor A_V(tau) Y_V e^{i psi}/sqrt|Fdot| of voice V at
+ * signed frequency g changes L by Re[W dC], W = (conj G+ + i conj Gx)/2 for
+ * g = f and W = (G+ + i Gx)/2 for g = -f (from h+ = [H(f) + conj H(-f)]/2,
+ * hx = i [H(f) - conj H(-f)]/2).  C depends on the segment's coefficients
+ * directly and through the root tau of F(tau) = g, with
+ * dtau = -(dF/dcoef) / Fdot (implicit differentiation), and through
+ * dC/C = dA_V/A_V - dFdot/(2 Fdot) + i dpsi,
+ * dpsi = (2 pi g - Phi_V'(tau)) dtau - dPhi_V.
+ * Voice-coefficient gradients are mapped to the series (F_V = (m Om_phi +
+ * n Om_r)/2pi, Phi_V = m Phi_phi + n Phi_r, partner amplitude (-1)^l conj A)
+ * and then to knot values through the spline's Jacobian, built column by
+ * column from the same dense solve.
+ */
+static double dd_to_d(dd_t a) { return a.hi + a.lo; }
+
+int oracle_loglike_grad(int K, const double* t, const double* phi_phi, const double* phi_r,
+                        const double* omega_phi, const double* omega_r,
+                        int nm, const int* l, const int* m, const int* n, const double* amp,
+                        double theta, double phi, double prefactor, int conj_partners,
+                        long long nf, const double* freqs, const double* dplus, const double* dcross,
+                        const double* psd, double df, double* loglike,
+                        double* g_phi_phi, double* g_phi_r, double* g_omega_phi, double* g_omega_r,
+                        double* g_amp, int nthreads) {
+  ctx_t c;
+  int rc = ctx_init(&c, K, t, phi_phi, phi_r, omega_phi, omega_r, nm, l, m, n, amp, theta, phi, prefactor,
+                    conj_partners, nf, freqs);
+  if (rc) { ctx_free(&c); return rc; }
+  for (long long i = 0; i < nf; i++) if (!(psd[i] > 0.0)) { ctx_free(&c); return -6; }
+  double* hp = (double*)malloc(sizeof(double) * 2 * (size_t)(nf > 0 ? nf : 1));
+  double* hc = (double*)malloc(sizeof(double) * 2 * (size_t)(nf > 0 ? nf : 1));
+  ctx_forward(&c, nf, freqs, hp, hc, NULL, nthreads);
+  /* likelihood and G = 4 df r / S per channel */
+  double* G = (double*)malloc(sizeof(double) * 4 * (size_t)(nf > 0 ? nf : 1));
+  double L = 0.0;
+  for (long long i = 0; i < nf; i++) {
+    double rpr = dplus[2 * i] - hp[2 * i], rpi = dplus[2 * i + 1] - hp[2 * i + 1];
+    double rcr = dcross[2 * i] - hc[2 * i], rci = dcross[2 * i + 1] - hc[2 * i + 1];
+    L += -2.0 * df * (rpr * rpr + rpi * rpi + rcr * rcr + rci * rci) / psd[i];
+    double s = 4.0 * df / psd[i];
+    G[4 * i + 0] = s * rpr; G[4 * i + 1] = s * rpi; G[4 * i + 2] = s * rcr; G[4 * i + 3] = s * rci;
   }
-  long long np = 0;
-  piece_t* P = build_pieces(&T, V, nv, freqs, nf, &np);
-  double* Hpos = (double*)calloc((size_t)(nf > 0 ? nf : 1) * 2, sizeof(double));
-  double* Hneg = (double*)calloc((size_t)(nf > 0 ? nf : 1) * 2, sizeof(double));
-  long long nev = 0, nzero = 0;
+  *loglike = L;
+  int want = g_phi_phi || g_phi_r || g_omega_phi || g_omega_r || g_amp;
+  if (!want) { free(hp); free(hc); free(G); ctx_free(&c); return 0; }
+
+  const int nseg = K - 1, nv = c.nv;
+  /* per (voice, segment): d/d of F cubic (4), Phi_V cubic (4), A_V cubic Re (4), Im (4) */
+  double* gv = (double*)calloc((size_t)(nv > 0 ? nv : 1) * nseg * 16, sizeof(double));
   if (nthreads < 1) nthreads = 1;
-  /* Parallel over contiguous chunks of bins; every bin sums its voices in
-   * ascending voice order, so the result does not depend on nthreads. */
-  long long nchunk = nthreads * 8LL;
-#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1) reduction(+ : nev, nzero)
-  for (long long ch = 0; ch < nchunk; ch++) {
-    long long b0 = nf * ch / nchunk, b1 = nf * (ch + 1) / nchunk;
-    if (b0 >= b1) continue;
-    for (long long ip = 0; ip < np; ip++) {
+  const piece_t* P = c.P;
+  const traj_t* T = &c.T;
+  /* pieces of one voice are contiguous: parallel over voices, no shared accumulators */
+  long long* vstart = (long long*)malloc(sizeof(long long) * (size_t)(nv + 1));
+  {
+    long long ip = 0;
+    for (int v = 0; v <= nv; v++) { while (ip < c.np && P[ip].voice < v) ip++; vstart[v] = ip; }
+  }
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1)
+  for (int v = 0; v < nv; v++) {
+    const voice_t* V = &c.V[v];
+    for (long long ip = vstart[v]; ip < vstart[v + 1]; ip++) {
       const piece_t* p = &P[ip];
-      const voice_t* v = &V[p->voice];
-      double fc[4];
-      int have_fc = 0;
+      int k = p->seg;
+      double fc[4]; voice_fcubic(T, V->m, V->n, k, fc);
+      const double* cPp = T->cPp + 4 * k; const double* cPr = T->cPr + 4 * k;
+      const double* are = V->are + 4 * k; const double* aim = V->aim + 4 * k;
+      double* acc = gv + ((size_t)v * nseg + k) * 16;
       for (int sgn = 0; sgn < 2; sgn++) {
-        long long lo = p->lo[sgn] > b0 ? p->lo[sgn] : b0;
-        long long hi = p->hi[sgn] < b1 ? p->hi[sgn] : b1;
-        if (lo >= hi) continue;
-        if (!have_fc) { voice_fcubic(&T, v->m, v->n, p->seg, fc); have_fc = 1; }
-        double* H = sgn ? Hneg : Hpos;
-        for (long long b = lo; b < hi; b++) {
+        for (long long b = p->lo[sgn]; b < p->hi[sgn]; b++) {
           double g = sgn ? -freqs[b] : freqs[b];
           double x = bisect(fc, g, p->ta, p->tb, p->dir);
-          nzero += contrib(&T, v, p->seg, fc, g, x, H + 2 * b);
-          nev++;
+          double Fd = dcubic(fc, x);
+          if (Fd == 0.0) continue;
+          double Fdd = 2.0 * fc[2] + 6.0 * fc[3] * x;
+          /* phase, as in contrib() */
+          dd_t tt = two_sum(T->t[k], x);
+          dd_t gt = dd_mul_d(tt, g);
+          dd_t twopi; twopi.hi = OR_TWO_PI_HI; twopi.lo = OR_TWO_PI_LO;
+          dd_t wgt = dd_mul(gt, twopi);
+          dd_t PV = dd_add(dd_mul_d(dd_spline(cPp, x), (double)V->m), dd_mul_d(dd_spline(cPr, x), (double)V->n));
+          dd_t psi = dd_add(wgt, dd_neg(PV));
+          dd_t qpi; qpi.hi = OR_QPI_HI; qpi.lo = OR_QPI_LO;
+          psi = dd_add(psi, Fd > 0.0 ? dd_neg(qpi) : qpi);
+          double kk = nearbyint(psi.hi / OR_TWO_PI_HI);
+          psi = dd_add(psi, dd_neg(dd_mul_d(twopi, kk)));
+          double cs = cos(psi.hi) - psi.lo * sin(psi.hi);
+          double sn = sin(psi.hi) + psi.lo * cos(psi.hi);
+          (void)dd_to_d;
+          /* E = prefactor Y |Fdot|^(-1/2) e^{i psi};  C = A_V E */
+          double w = 1.0 / sqrt(fabs(Fd));
+          double Er = T->prefactor * w * (V->Y[0] * cs - V->Y[1] * sn);
+          double Ei = T->prefactor * w * (V->Y[0] * sn + V->Y[1] * cs);
+          double Ar = cubic(are, x), Ai = cubic(aim, x);
+          double dAr = dcubic(are, x), dAi = dcubic(aim, x);
+          const double* Gb = G + 4 * b;
+          double Wr, Wi;
+          if (!sgn) { Wr = 0.5 * (Gb[0] + Gb[3]); Wi = 0.5 * (-Gb[1] + Gb[2]); }   /* (conj G+ + i conj Gx)/2 */
+          else { Wr = 0.5 * (Gb[0] - Gb[3]); Wi = 0.5 * (Gb[1] + Gb[2]); }         /* (G+ + i Gx)/2 */
+          double WEr = Wr * Er - Wi * Ei, WEi = Wr * Ei + Wi * Er;
+          double Xr = WEr * Ar - WEi * Ai, Xi = WEr * Ai + WEi * Ar;
+          double dPV = (double)V->m * dcubic(cPp, x) + (double)V->n * dcubic(cPr, x);
+          /* coefficient of dtau */
+          double Tdt = (WEr * dAr - WEi * dAi) - 0.5 * Xr * Fdd / Fd - Xi * (OR_TWO_PI_HI * g - dPV);
+          double xp[4] = {1.0, x, x * x, x * x * x};
+          for (int j = 0; j < 4; j++) {
+            double dtau = -xp[j] / Fd;                     /* dtau/dfc_j */
+            double dfdot = (j == 0) ? 0.0 : j * xp[j - 1]; /* dFdot/dfc_j at fixed tau */
+            acc[j] += Tdt * dtau - 0.5 * Xr * dfdot / Fd;   /* F cubic */
+            acc[4 + j] += Xi * xp[j];                       /* Phi_V cubic */
+            acc[8 + j] += WEr * xp[j];                      /* Re A_V */
+            acc[12 + j] += -WEi * xp[j];                    /* Im A_V */
+          }
         }
       }
     }
   }
-  for (long long b = 0; b < nf; b++) {
-    double pr = Hpos[2 * b], pi = Hpos[2 * b + 1], nr = Hneg[2 * b], ni = -Hneg[2 * b + 1]; /* conj H(-f) */
-    hp[2 * b] = 0.5 * (pr + nr);   hp[2 * b + 1] = 0.5 * (pi + ni);
-    /* hx = i/2 (H(f) - conj H(-f)) */
-    hc[2 * b] = -0.5 * (pi - ni);  hc[2 * b + 1] = 0.5 * (pr - nr);
+  /* voice coefficients -> series coefficients */
+  size_t sc = (size_t)nseg * 4;
+  double* gcf = (double*)calloc(sc * 4, sizeof(double));       /* Phi_phi, Phi_r, Om_phi, Om_r */
+  double* gca = (double*)calloc(sc * 2 * (size_t)(nm > 0 ? nm : 1), sizeof(double));  /* per mode Re, Im */
+  for (int v = 0; v < nv; v++) {
+    const voice_t* V = &c.V[v];
+    int j = c.vmode[v], part = c.vpart[v];
+    double sgn = (V->l & 1) ? -1.0 : 1.0;
+    for (int k = 0; k < nseg; k++) {
+      const double* a = gv + ((size_t)v * nseg + k) * 16;
+      for (int q = 0; q < 4; q++) {
+        gcf[0 * sc + 4 * k + q] += (double)V->m * a[4 + q];
+        gcf[1 * sc + 4 * k + q] += (double)V->n * a[4 + q];
+        gcf[2 * sc + 4 * k + q] += (double)V->m / OR_TWO_PI_HI * a[q];
+        gcf[3 * sc + 4 * k + q] += (double)V->n / OR_TWO_PI_HI * a[q];
+        double* ga = gca + (size_t)j * 2 * sc;
+        if (!part) { ga[4 * k + q] += a[8 + q]; ga[sc + 4 * k + q] += a[12 + q]; }
+        else { ga[4 * k + q] += sgn * a[8 + q]; ga[sc + 4 * k + q] += -sgn * a[12 + q]; }
+      }
+    }
   }
-  if (stats) { stats[0] = nev; stats[1] = nzero; stats[2] = np; }
-  free(Hpos); free(Hneg); free(P); free(V); free(ac); free(cf); free(y); free(work); spl_free(&S);
+  /* series coefficients -> knot values through the spline Jacobian J[i] = coef(e_i) */
+  double* J = (double*)malloc(sizeof(double) * sc * (size_t)K);
+  {
+    double* e = (double*)calloc((size_t)K, sizeof(double));
+    double* work = (double*)malloc(sizeof(double) * K);
+    for (int i = 0; i < K; i++) { e[i] = 1.0; spl_coef(&c.S, e, J + (size_t)i * sc, work); e[i] = 0.0; }
+    free(e); free(work);
+  }
+  double* outs[4] = {g_phi_phi, g_phi_r, g_omega_phi, g_omega_r};
+  for (int q = 0; q < 4; q++) {
+    if (!outs[q]) continue;
+    for (int i = 0; i < K; i++) {
+      double s = 0.0;
+      for (size_t r = 0; r < sc; r++) s += J[(size_t)i * sc + r] * gcf[q * sc + r];
+      outs[q][i] = s;
+    }
+  }
+  if (g_amp) {
+    for (int j = 0; j < nm; j++)
+      for (int part = 0; part < 2; part++)
+        for (int i = 0; i < K; i++) {
+          double s = 0.0;
+          const double* ga = gca + (size_t)j * 2 * sc + part * sc;
+          for (size_t r = 0; r < sc; r++) s += J[(size_t)i * sc + r] * ga[r];
+          g_amp[((size_t)j * K + i) * 2 + part] = s;
+        }
+  }
+  free(J); free(gcf); free(gca); free(vstart); free(gv); free(hp); free(hc); free(G); ctx_free(&c);
   return 0;
 }

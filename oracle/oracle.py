@@ -51,6 +51,10 @@ def lib():
                                        C.c_double, C.c_double, C.c_double, C.c_int,
                                        C.c_longlong, dp, dp, dp, C.POINTER(C.c_longlong), C.c_int]
         L.oracle_sum_modes.restype = C.c_int
+        L.oracle_loglike_grad.argtypes = [C.c_int, dp, dp, dp, dp, dp, C.c_int, ip, ip, ip, dp,
+                                          C.c_double, C.c_double, C.c_double, C.c_int,
+                                          C.c_longlong, dp, dp, dp, dp, C.c_double, dp, dp, dp, dp, dp, dp, C.c_int]
+        L.oracle_loglike_grad.restype = C.c_int
         _lib = L
     return _lib
 
@@ -119,6 +123,41 @@ def sum_modes(w, freqs=None, conj_partners=True, nthreads=None, return_stats=Fal
     if return_stats:
         return hpc, hcc_, {"contributions": int(st[0]), "zero_fdot": int(st[1]), "pieces": int(st[2])}
     return hpc, hcc_
+
+
+def loglike_grad(w, dplus, dcross, psd, df, conj_partners=True, nthreads=None, grad=True):
+    """Whittle log-likelihood L = -1/2 sum_alpha <d - h|d - h>_alpha (Eq. 13-14) of
+    the SPA waveform of ``w`` on w.freqs, and (grad=True) its gradient with respect
+    to every knot value: dict with phi_phi, phi_r, omega_phi, omega_r [K] and
+    amp [N_m, K] complex (d/dRe + 1j d/dIm)."""
+    f, fp = _d(w.freqs)
+    t, tp = _d(w.t)
+    a1, p1 = _d(w.phi_phi)
+    a2, p2 = _d(w.phi_r)
+    a3, p3 = _d(w.omega_phi)
+    a4, p4 = _d(w.omega_r)
+    l, lp = _i(w.l)
+    m, mp = _i(w.m)
+    n, np_ = _i(w.n)
+    amp, ap = _d(np.ascontiguousarray(np.asarray(w.amp, np.complex128)).view(np.float64))
+    dp_, dpp = _d(np.ascontiguousarray(np.asarray(dplus, np.complex128)).view(np.float64))
+    dc_, dcp = _d(np.ascontiguousarray(np.asarray(dcross, np.complex128)).view(np.float64))
+    S, Sp = _d(psd)
+    K, nm = t.shape[0], l.shape[0]
+    L = np.zeros(1)
+    Lp = L.ctypes.data_as(C.POINTER(C.c_double))
+    outs = [np.zeros(K) for _ in range(4)] + [np.zeros(2 * nm * K)]
+    ptrs = [o.ctypes.data_as(C.POINTER(C.c_double)) if grad else None for o in outs]
+    rc = lib().oracle_loglike_grad(K, tp, p1, p2, p3, p4, nm, lp, mp, np_, ap, float(w.theta), float(w.phi),
+                                   float(w.prefactor), int(conj_partners), f.shape[0], fp, dpp, dcp, Sp,
+                                   float(df), Lp, *ptrs, int(nthreads or default_threads()))
+    if rc:
+        raise ValueError("oracle_loglike_grad rejected the input: %d" % rc)
+    if not grad:
+        return float(L[0])
+    g = {"phi_phi": outs[0], "phi_r": outs[1], "omega_phi": outs[2], "omega_r": outs[3],
+         "amp": outs[4].view(np.complex128).reshape(nm, K)}
+    return float(L[0]), g
 
 
 # ---------------------------------------------------------------------------
