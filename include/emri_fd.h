@@ -89,7 +89,9 @@ typedef struct {
   long long max_modes_total;/* sum of N_m over a call, >= 1 */
   long long max_bins_total; /* sum of N_f over a call, >= 1 */
   int tile_bins;            /* output bins per work tile: 32, 64 or 128; 0 = default (128) */
-  int reserved[7];          /* must be zero */
+  int likelihood;           /* 1: also allocate the scratch of emri_fd_loglike_and_grad
+                               (FP64 plans only); 0: that call returns EMRI_FD_ERR_ARG */
+  int reserved[6];          /* must be zero */
 } emri_fd_desc;
 
 /*
@@ -127,6 +129,39 @@ emri_fd_status emri_fd_sum_modes(emri_fd_plan_t plan, int n_waveforms,
                                  const int* l, const int* m, const int* n, const double* amp,
                                  const double* theta, const double* phi, const double* prefactor,
                                  const double* freqs, void* h_plus, void* h_cross);
+
+/*
+ * Whittle log-likelihood (Eq. 14 with the inner product of Eq. 13) of
+ * n_waveforms waveforms against data, and its gradient with respect to every
+ * knot value.  Inputs as emri_fd_sum_modes, plus:
+ *   data_plus, data_cross: [sum N_f] complex128 data d+ and dx on the same bins;
+ *   psd:    [sum N_f] one-sided noise PSD S(f) > 0;
+ *   df:     [n_waveforms] frequency spacing of each waveform's grid;
+ * outputs:
+ *   loglike: [n_waveforms] L_w = -1/2 sum_alpha <d - h|d - h>_alpha
+ *            = -2 df sum_i |d_i - h_i|^2 / S_i  (both channels);
+ *   g_phi_phi, g_phi_r, g_omega_phi, g_omega_r: [sum K] dL/d(knot values);
+ *   g_amp:  [sum over waveforms of N_m K] complex128 (dL/dRe, dL/dIm) of the
+ *           amplitude knots.
+ * Any gradient pointer may be NULL (not computed; all NULL = likelihood only).
+ * The gradient is that of L with each bin's branch and segment assignment held
+ * at the input's (L is only piecewise smooth in the frequency knots: a bin
+ * changes segment when a knot frequency crosses it).  Roots t(f) are
+ * recomputed in the adjoint pass, with the same arithmetic as the forward pass.
+ * Needs an FP64 plan created with likelihood = 1 (else EMRI_FD_ERR_ARG).
+ * Pointers may be device or host memory (host: staged, and the call syncs).
+ */
+emri_fd_status emri_fd_loglike_and_grad(emri_fd_plan_t plan, int n_waveforms,
+                                        const long long* knot_off, const long long* mode_off,
+                                        const long long* freq_off,
+                                        const double* t, const double* phi_phi, const double* phi_r,
+                                        const double* omega_phi, const double* omega_r,
+                                        const int* l, const int* m, const int* n, const double* amp,
+                                        const double* theta, const double* phi, const double* prefactor,
+                                        const double* freqs, const double* data_plus, const double* data_cross,
+                                        const double* psd, const double* df, double* loglike,
+                                        double* g_phi_phi, double* g_phi_r, double* g_omega_phi,
+                                        double* g_omega_r, double* g_amp);
 
 /*
  * Wait for the plan's stream and return (and clear) the status latched by the

@@ -18,8 +18,8 @@ EMRI_FD_FP64, EMRI_FD_MIXED = 0, 1
 STATUS = {0: "EMRI_FD_OK", 1: "EMRI_FD_ERR_ARG", 2: "EMRI_FD_ERR_KNOTS", 3: "EMRI_FD_ERR_FREQ",
           4: "EMRI_FD_ERR_MODE", 5: "EMRI_FD_ERR_NONFINITE", 6: "EMRI_FD_ERR_CAPACITY",
           7: "EMRI_FD_ERR_CUDA", 8: "EMRI_FD_ERR_OOM", 9: "EMRI_FD_ERR_TIMEOUT"}
-EXPORTS = ("emri_fd_plan", "emri_fd_sum_modes", "emri_fd_sync", "emri_fd_stats", "emri_fd_profile",
-           "emri_fd_plan_destroy", "emri_fd_strerror", "emri_fd_sum_modes_noalloc")
+EXPORTS = ("emri_fd_plan", "emri_fd_sum_modes", "emri_fd_loglike_and_grad", "emri_fd_sync", "emri_fd_stats",
+           "emri_fd_profile", "emri_fd_plan_destroy", "emri_fd_strerror", "emri_fd_sum_modes_noalloc")
 
 
 class EmriFdError(RuntimeError):
@@ -31,7 +31,8 @@ class EmriFdError(RuntimeError):
 class emri_fd_desc(C.Structure):
     _fields_ = [("precision", C.c_int), ("conj_partners", C.c_int), ("max_waveforms", C.c_int),
                 ("max_knots", C.c_int), ("max_knots_total", C.c_longlong), ("max_modes_total", C.c_longlong),
-                ("max_bins_total", C.c_longlong), ("tile_bins", C.c_int), ("reserved", C.c_int * 7)]
+                ("max_bins_total", C.c_longlong), ("tile_bins", C.c_int), ("likelihood", C.c_int),
+                ("reserved", C.c_int * 6)]
 
 
 _lib = None
@@ -55,6 +56,8 @@ def lib():
         L.emri_fd_plan.restype = C.c_int
         L.emri_fd_sum_modes.argtypes = [vp, C.c_int, vp, vp, vp] + [dp] * 5 + [ip] * 3 + [dp] * 5 + [vp, vp]
         L.emri_fd_sum_modes.restype = C.c_int
+        L.emri_fd_loglike_and_grad.argtypes = [vp, C.c_int, vp, vp, vp] + [dp] * 5 + [ip] * 3 + [dp] * 5 + [dp] * 10
+        L.emri_fd_loglike_and_grad.restype = C.c_int
         L.emri_fd_sync.argtypes = [vp]
         L.emri_fd_sync.restype = C.c_int
         L.emri_fd_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
@@ -97,6 +100,15 @@ def emri_fd_sum_modes(plan, n_waveforms, knot_off, mode_off, freq_off, t, phi_ph
     return lib().emri_fd_sum_modes(C.c_void_p(plan), int(n_waveforms), *[C.c_void_p(int(x)) for x in (
         knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r, l, m, n, amp, theta, phi,
         prefactor, freqs, h_plus, h_cross)])
+
+
+def emri_fd_loglike_and_grad(plan, n_waveforms, knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi,
+                             omega_r, l, m, n, amp, theta, phi, prefactor, freqs, data_plus, data_cross, psd, df,
+                             loglike, g_phi_phi, g_phi_r, g_omega_phi, g_omega_r, g_amp) -> int:
+    """All array arguments are raw addresses (ints, 0 for a skipped gradient); returns the status."""
+    return lib().emri_fd_loglike_and_grad(C.c_void_p(plan), int(n_waveforms), *[C.c_void_p(int(x)) for x in (
+        knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r, l, m, n, amp, theta, phi, prefactor,
+        freqs, data_plus, data_cross, psd, df, loglike, g_phi_phi, g_phi_r, g_omega_phi, g_omega_r, g_amp)])
 
 
 def emri_fd_sum_modes_noalloc(conj_partners, n_knots, n_modes, n_freqs, t, phi_phi, phi_r, omega_phi, omega_r,
@@ -156,7 +168,7 @@ class Plan:
 
     def __init__(self, precision="fp64", conj_partners=True, max_waveforms=1, max_knots=200,
                  max_modes_total=4096, max_bins_total=1 << 22, max_knots_total=0, tile_bins=0,
-                 device=None, stream=None):
+                 likelihood=False, device=None, stream=None):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -170,6 +182,7 @@ class Plan:
         d.max_modes_total = int(max_modes_total)
         d.max_bins_total = int(max_bins_total)
         d.tile_bins = int(tile_bins)
+        d.likelihood = int(bool(likelihood))
         self.desc = d
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -240,6 +253,32 @@ class Plan:
         _check(emri_fd_sync(self.handle), "emri_fd_sum_modes (device checks)")
         return out
 
+    def loglike_and_grad(self, b, data_plus, data_cross, psd, df, grad=True, check=True):
+        """emri_fd_loglike_and_grad on a device batch.  data_*: complex128 device tensors,
+        psd: float64 device tensor, df: float64 tensor [n_wf].  Returns (loglike [n_wf],
+        dict of knot gradients or None)."""
+        T = self.torch
+        n_wf = len(b["knot_off"]) - 1
+        K = int(b["knot_off"][-1])
+        namp = int(np.sum(np.diff(b["mode_off"]) * np.diff(b["knot_off"])))
+        dev = self.device
+        L = T.empty(n_wf, dtype=T.float64, device=dev)
+        g = None
+        if grad:
+            g = {k: T.empty(K, dtype=T.float64, device=dev) for k in ("phi_phi", "phi_r", "omega_phi", "omega_r")}
+            g["amp"] = T.empty(namp, dtype=T.complex128, device=dev)
+        ko, mo, fo = (np.ascontiguousarray(np.asarray(b[k], np.int64)) for k in ("knot_off", "mode_off", "freq_off"))
+        gp = [_addr(g[k]) if g else 0 for k in ("phi_phi", "phi_r", "omega_phi", "omega_r", "amp")]
+        code = emri_fd_loglike_and_grad(self.handle, n_wf, ko.ctypes.data, mo.ctypes.data, fo.ctypes.data,
+                                        *[_addr(b[k]) for k in ("t", "phi_phi", "phi_r", "omega_phi", "omega_r", "l",
+                                                                "m", "n", "amp", "theta", "phi", "prefactor",
+                                                                "freqs")],
+                                        _addr(data_plus), _addr(data_cross), _addr(psd), _addr(df), _addr(L), *gp)
+        _check(code, "emri_fd_loglike_and_grad")
+        if check:
+            _check(emri_fd_sync(self.handle), "emri_fd_loglike_and_grad (device checks)")
+        return L, g
+
     def sync(self):
         _check(emri_fd_sync(self.handle), "emri_fd_sync")
 
@@ -259,3 +298,49 @@ def host_batch(batch):
         out[k] = np.ascontiguousarray(batch[k], np.int32)
     out["amp"] = np.ascontiguousarray(batch["amp"], np.complex128).view(np.float64)
     return out
+
+
+def whittle_loglike(plan, b, data_plus, data_cross, psd, df):
+    """Differentiable Whittle log-likelihood (summed over the batch's waveforms).
+
+    The knot tensors b["phi_phi"], b["phi_r"], b["omega_phi"], b["omega_r"]
+    (float64) and b["amp"] (float64 view of complex128, [sum N_m K * 2]) may
+    require grad.  Forward computes L only; backward calls the C adjoint, which
+    recomputes t(f) instead of storing it."""
+    return WhittleLogLike.apply(plan, b, data_plus, data_cross, psd, df, b["phi_phi"], b["phi_r"],
+                                b["omega_phi"], b["omega_r"], b["amp"])
+
+
+def _autograd_function():
+    import torch
+
+    class _WhittleLogLike(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, plan, b, data_plus, data_cross, psd, df, phi_phi, phi_r, omega_phi, omega_r, amp):
+            bb = dict(b)
+            bb.update(phi_phi=phi_phi.detach(), phi_r=phi_r.detach(), omega_phi=omega_phi.detach(),
+                      omega_r=omega_r.detach(), amp=amp.detach())
+            L, _ = plan.loglike_and_grad(bb, data_plus, data_cross, psd, df, grad=False)
+            ctx.plan, ctx.b, ctx.data = plan, bb, (data_plus, data_cross, psd, df)
+            return L.sum()
+
+        @staticmethod
+        def backward(ctx, gL):
+            _, g = ctx.plan.loglike_and_grad(ctx.b, *ctx.data, grad=True)
+            ga = torch.view_as_real(g["amp"]).reshape(-1)
+            return (None, None, None, None, None, None, gL * g["phi_phi"], gL * g["phi_r"], gL * g["omega_phi"],
+                    gL * g["omega_r"], gL * ga)
+
+    return _WhittleLogLike
+
+
+class _LazyFn:
+    _fn = None
+
+    def apply(self, *a):
+        if _LazyFn._fn is None:
+            _LazyFn._fn = _autograd_function()
+        return _LazyFn._fn.apply(*a)
+
+
+WhittleLogLike = _LazyFn()

@@ -178,6 +178,25 @@ struct DevScratch {
   RunBins* rbins;
   long long run_cap;
   double2* tab;                   // [kTabN] e^{2 pi i k / kTabN}
+  // likelihood / adjoint scratch (plans created with likelihood = 1)
+  double* hbuf;                   // [2][sum N_f] complex128: h+ then hx
+  double* Gbuf;                   // [sum N_f][4] 4 df (d - h)/S, both channels
+  double* Lpart;                  // [max_waveforms][64] partial sums of L
+  int* item_off;                  // [run_cap + 1] adjoint items (run, segment), scanned
+  double* slots;                  // [sum N_m (K-1)][3 sub-pieces][16] per-segment gradients
+  double *agY, *agM;              // [sum N_m K][2] amplitude knot-value / second-derivative gradients
+  double *fgY, *fgM;              // [4][sum K] fundamental series, same
+  double* fseg;                   // [sum K][16] fundamental u-coefficient gradients per segment
+  double *zf, *za;                // transposed-solve work arrays
+};
+
+struct LikeInputs {
+  const double *data_plus, *data_cross;   // [sum N_f] complex128
+  const double* psd;                      // [sum N_f]
+  const double* df;                       // [n_wf]
+  double* loglike;                        // [n_wf]
+  double *g_phi_phi, *g_phi_r, *g_omega_phi, *g_omega_r;   // [sum K] or null
+  double* g_amp;                          // [sum N_m K][2] or null
 };
 
 struct CallShape {
@@ -190,9 +209,14 @@ struct CallShape {
 };
 
 constexpr int kPrepKernels = 12;   // kernels launched by launch_prep (memsets excluded)
+constexpr int kAdjointKernels = 8; // kernels launched by launch_adjoint
 
 void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st);
 void launch_spa(const CallShape& cs, const DevInputs& in, const DevScratch& s, int num_sms, cudaStream_t st);
 void launch_table(double2* tab, cudaStream_t st);
+void launch_scan(int* cnt, long long n, cudaStream_t st);
+void launch_loglike(const CallShape& cs, const LikeInputs& li, const DevScratch& s, cudaStream_t st);
+void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& li, const DevScratch& s, int num_sms,
+                    cudaStream_t st);
 
 }  // namespace emrifd

@@ -19,8 +19,8 @@ struct emri_fd_plan_s {
   cudaEvent_t wf_done = nullptr;     // guards reuse of wf_pinned
   unsigned long long* cnt_pinned = nullptr;
   // staging for host-memory inputs / outputs
-  void* stage[16] = {};
-  size_t stage_sz[16] = {};
+  void* stage[32] = {};
+  size_t stage_sz[32] = {};
   // last call's shape (for stats)
   long long last_tiles = 0, last_nm = 0;
   // optional event timing of the output kernel and of the preparation kernels
@@ -94,7 +94,7 @@ void emri_fd_plan_destroy(emri_fd_plan_t p) {
   if (!p) return;
   cudaStreamSynchronize(p->stream);
   for (void* q : p->allocs) cudaFree(q);
-  for (int i = 0; i < 16; i++) if (p->stage[i]) cudaFree(p->stage[i]);
+  for (int i = 0; i < 32; i++) if (p->stage[i]) cudaFree(p->stage[i]);
   if (p->wf_pinned) cudaFreeHost(p->wf_pinned);
   if (p->cnt_pinned) cudaFreeHost(p->cnt_pinned);
   if (p->wf_done) cudaEventDestroy(p->wf_done);
@@ -111,7 +111,8 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
       d->max_bins_total > 2000000000LL || d->max_knots_total < 0 ||
       !(d->tile_bins == 0 || d->tile_bins == 32 || d->tile_bins == 64 || d->tile_bins == 128))
     return EMRI_FD_ERR_ARG;
-  for (int i = 0; i < 7; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
+  for (int i = 0; i < 6; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
+  if (d->likelihood != 0 && (d->likelihood != 1 || d->precision != EMRI_FD_FP64)) return EMRI_FD_ERR_ARG;
   emri_fd_plan_s* p = new emri_fd_plan_s();
   p->desc = *d;
   if (p->desc.tile_bins == 0) p->desc.tile_bins = 128;
@@ -146,6 +147,20 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
   AL(s.runF, s.run_cap);
   AL(s.rbins, s.run_cap);
   AL(s.tab, kTabN);
+  if (d->likelihood) {
+    AL(s.hbuf, 4 * p->cap_nf);
+    AL(s.Gbuf, 4 * p->cap_nf);
+    AL(s.Lpart, 64 * (long long)d->max_waveforms);
+    AL(s.item_off, s.run_cap + 1);
+    AL(s.slots, 48 * p->cap_seg);
+    AL(s.agY, 2 * p->cap_amp);
+    AL(s.agM, 2 * p->cap_amp);
+    AL(s.za, 2 * p->cap_amp);
+    AL(s.fgY, 4 * p->cap_K);
+    AL(s.fgM, 4 * p->cap_K);
+    AL(s.zf, 4 * p->cap_K);
+    AL(s.fseg, 16 * p->cap_K);
+  }
 #undef AL
   if (st == EMRI_FD_OK && (cudaMallocHost(&p->wf_pinned, sizeof(WfInfo) * d->max_waveforms) != cudaSuccess ||
                            cudaMallocHost(&p->cnt_pinned, sizeof(unsigned long long) * 8) != cudaSuccess ||
@@ -164,19 +179,24 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
   return EMRI_FD_OK;
 }
 
-emri_fd_status emri_fd_sum_modes(emri_fd_plan_t p, int n_wf, const long long* knot_off, const long long* mode_off,
-                                 const long long* freq_off, const double* t, const double* phi_phi,
-                                 const double* phi_r, const double* omega_phi, const double* omega_r, const int* l,
-                                 const int* m, const int* n, const double* amp, const double* theta,
-                                 const double* phi, const double* prefactor, const double* freqs, void* h_plus,
-                                 void* h_cross) {
+}  // extern "C"
+
+namespace {
+
+// host-side shape checks, per-waveform table, input staging (shared by the
+// two computing entry points); on success the waveform table is uploaded
+emri_fd_status prepare_call(emri_fd_plan_s* p, int n_wf, const long long* knot_off, const long long* mode_off,
+                            const long long* freq_off, const double* t, const double* phi_phi, const double* phi_r,
+                            const double* omega_phi, const double* omega_r, const int* l, const int* m, const int* n,
+                            const double* amp, const double* theta, const double* phi, const double* prefactor,
+                            const double* freqs, CallShape& cs, DevInputs& in) {
   if (!p || n_wf < 1 || !knot_off || !mode_off || !freq_off) return EMRI_FD_ERR_ARG;
   if (n_wf > p->desc.max_waveforms) return EMRI_FD_ERR_CAPACITY;
   if (knot_off[0] != 0 || mode_off[0] != 0 || freq_off[0] != 0) return EMRI_FD_ERR_ARG;
   const int TB = p->desc.tile_bins;
-  // host-side shape checks; the pinned table may still be read by the previous call's copy
+  // the pinned table may still be read by the previous call's copy
   if (cudaEventSynchronize(p->wf_done) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_CUDA; }
-  CallShape cs{};
+  cs = CallShape{};
   cs.n_wf = n_wf;
   cs.tile_bins = TB;
   cs.conj = p->desc.conj_partners;
@@ -210,10 +230,9 @@ emri_fd_status emri_fd_sum_modes(emri_fd_plan_t p, int n_wf, const long long* kn
     return EMRI_FD_ERR_CAPACITY;
   if (!t || !phi_phi || !phi_r || !omega_phi || !omega_r || !theta || !phi || !prefactor) return EMRI_FD_ERR_ARG;
   if (cs.nm_total > 0 && (!l || !m || !n || !amp)) return EMRI_FD_ERR_ARG;
-  if (cs.nf_total > 0 && (!freqs || !h_plus || !h_cross)) return EMRI_FD_ERR_ARG;
-  if (cs.nm_total == 0) cs.nm_total = 0;
+  if (cs.nf_total > 0 && !freqs) return EMRI_FD_ERR_ARG;
 
-  DevInputs in{};
+  in = DevInputs{};
   emri_fd_status st = EMRI_FD_OK;
   const size_t kb = sizeof(double) * cs.K_total;
   const void* q;
@@ -237,26 +256,32 @@ emri_fd_status emri_fd_sum_modes(emri_fd_plan_t p, int n_wf, const long long* kn
   STG(12, freqs, sizeof(double) * cs.nf_total, freqs, const double*);
 #undef STG
   if (st != EMRI_FD_OK) return st;
-  const size_t ob = (p->desc.precision == EMRI_FD_FP64 ? 16 : 8) * (size_t)cs.nf_total;
-  const bool host_out = cs.nf_total > 0 && (!is_device_ptr(h_plus) || !is_device_ptr(h_cross));
-  in.h_plus = h_plus;
-  in.h_cross = h_cross;
-  if (host_out) {
-    for (int slot = 13; slot <= 14; slot++) {
-      if (p->stage_sz[slot] < ob) {
-        if (p->stage[slot]) cudaFree(p->stage[slot]);
-        p->stage[slot] = nullptr; p->stage_sz[slot] = 0;
-        if (cudaMalloc(&p->stage[slot], ob) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_OOM; }
-        p->stage_sz[slot] = ob;
-      }
-    }
-    in.h_plus = p->stage[13];
-    in.h_cross = p->stage[14];
-  }
-  cudaStream_t stm = p->stream;
-  if (cudaMemcpyAsync(p->s.wf, p->wf_pinned, sizeof(WfInfo) * n_wf, cudaMemcpyHostToDevice, stm) != cudaSuccess ||
-      cudaEventRecord(p->wf_done, stm) != cudaSuccess)
+  if (cudaMemcpyAsync(p->s.wf, p->wf_pinned, sizeof(WfInfo) * n_wf, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+      cudaEventRecord(p->wf_done, p->stream) != cudaSuccess)
     return EMRI_FD_ERR_CUDA;
+  return EMRI_FD_OK;
+}
+
+// a device buffer for an output of `bytes` at `dst` (host outputs go to staging slot `slot`)
+emri_fd_status stage_out(emri_fd_plan_s* p, int slot, void* dst, size_t bytes, void** out, bool* host) {
+  *host = false;
+  *out = dst;
+  if (!dst || bytes == 0 || is_device_ptr(dst)) return EMRI_FD_OK;
+  if (p->stage_sz[slot] < bytes) {
+    if (p->stage[slot]) cudaFree(p->stage[slot]);
+    p->stage[slot] = nullptr;
+    p->stage_sz[slot] = 0;
+    if (cudaMalloc(&p->stage[slot], bytes) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_OOM; }
+    p->stage_sz[slot] = bytes;
+  }
+  *out = p->stage[slot];
+  *host = true;
+  return EMRI_FD_OK;
+}
+
+// preparation kernels and the output kernel, with optional event timing
+void run_forward(emri_fd_plan_s* p, const CallShape& cs, const DevInputs& in, size_t ob) {
+  cudaStream_t stm = p->stream;
   cudaMemsetAsync(p->s.counters, 0, 8 * sizeof(unsigned long long), stm);
   cudaEvent_t* E = nullptr;
   if (p->profiling && p->ev_used + 3 <= (int)p->ev.size()) {
@@ -288,12 +313,111 @@ emri_fd_status emri_fd_sum_modes(emri_fd_plan_t p, int n_wf, const long long* kn
   }
   p->last_tiles = cs.tiles_total;
   p->last_nm = cs.nm_total;
+}
+
+}  // namespace
+
+extern "C" {
+
+emri_fd_status emri_fd_sum_modes(emri_fd_plan_t p, int n_wf, const long long* knot_off, const long long* mode_off,
+                                 const long long* freq_off, const double* t, const double* phi_phi,
+                                 const double* phi_r, const double* omega_phi, const double* omega_r, const int* l,
+                                 const int* m, const int* n, const double* amp, const double* theta,
+                                 const double* phi, const double* prefactor, const double* freqs, void* h_plus,
+                                 void* h_cross) {
+  CallShape cs;
+  DevInputs in;
+  emri_fd_status st = prepare_call(p, n_wf, knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r, l,
+                                   m, n, amp, theta, phi, prefactor, freqs, cs, in);
+  if (st != EMRI_FD_OK) return st;
+  if (cs.nf_total > 0 && (!h_plus || !h_cross)) return EMRI_FD_ERR_ARG;
+  const size_t ob = (p->desc.precision == EMRI_FD_FP64 ? 16 : 8) * (size_t)cs.nf_total;
+  bool hp_host = false, hc_host = false;
+  if ((st = stage_out(p, 13, h_plus, ob, &in.h_plus, &hp_host)) != EMRI_FD_OK) return st;
+  if ((st = stage_out(p, 14, h_cross, ob, &in.h_cross, &hc_host)) != EMRI_FD_OK) return st;
+  run_forward(p, cs, in, ob);
   if (cudaGetLastError() != cudaSuccess) return EMRI_FD_ERR_CUDA;
-  if (host_out) {
-    if (cudaMemcpyAsync(h_plus, in.h_plus, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess ||
-        cudaMemcpyAsync(h_cross, in.h_cross, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess ||
+  cudaStream_t stm = p->stream;
+  if (hp_host || hc_host) {
+    if ((hp_host && cudaMemcpyAsync(h_plus, in.h_plus, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess) ||
+        (hc_host && cudaMemcpyAsync(h_cross, in.h_cross, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess) ||
         cudaStreamSynchronize(stm) != cudaSuccess)
       return EMRI_FD_ERR_CUDA;
+  }
+  return EMRI_FD_OK;
+}
+
+emri_fd_status emri_fd_loglike_and_grad(emri_fd_plan_t p, int n_wf, const long long* knot_off,
+                                        const long long* mode_off, const long long* freq_off, const double* t,
+                                        const double* phi_phi, const double* phi_r, const double* omega_phi,
+                                        const double* omega_r, const int* l, const int* m, const int* n,
+                                        const double* amp, const double* theta, const double* phi,
+                                        const double* prefactor, const double* freqs, const double* data_plus,
+                                        const double* data_cross, const double* psd, const double* df,
+                                        double* loglike, double* g_phi_phi, double* g_phi_r, double* g_omega_phi,
+                                        double* g_omega_r, double* g_amp) {
+  if (!p) return EMRI_FD_ERR_ARG;
+  if (p->desc.precision != EMRI_FD_FP64 || !p->desc.likelihood) return EMRI_FD_ERR_ARG;
+  CallShape cs;
+  DevInputs in;
+  emri_fd_status st = prepare_call(p, n_wf, knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r, l,
+                                   m, n, amp, theta, phi, prefactor, freqs, cs, in);
+  if (st != EMRI_FD_OK) return st;
+  if (!loglike || !df || (cs.nf_total > 0 && (!data_plus || !data_cross || !psd))) return EMRI_FD_ERR_ARG;
+  LikeInputs li{};
+  const void* q = nullptr;
+  if ((st = stage_in(p, 15, data_plus, 16 * (size_t)cs.nf_total, &q)) != EMRI_FD_OK) return st;
+  li.data_plus = static_cast<const double*>(q);
+  if ((st = stage_in(p, 16, data_cross, 16 * (size_t)cs.nf_total, &q)) != EMRI_FD_OK) return st;
+  li.data_cross = static_cast<const double*>(q);
+  if ((st = stage_in(p, 17, psd, 8 * (size_t)cs.nf_total, &q)) != EMRI_FD_OK) return st;
+  li.psd = static_cast<const double*>(q);
+  if ((st = stage_in(p, 18, df, 8 * (size_t)n_wf, &q)) != EMRI_FD_OK) return st;
+  li.df = static_cast<const double*>(q);
+  bool host[6] = {false, false, false, false, false, false};
+  void* o = nullptr;
+  const size_t kb = 8 * (size_t)cs.K_total;
+  if ((st = stage_out(p, 19, loglike, 8 * (size_t)n_wf, &o, &host[0])) != EMRI_FD_OK) return st;
+  li.loglike = static_cast<double*>(o);
+  double* gin[5] = {g_phi_phi, g_phi_r, g_omega_phi, g_omega_r, g_amp};
+  double* gdev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  for (int k = 0; k < 5; k++) {
+    const size_t bytes = k < 4 ? kb : 16 * (size_t)cs.amp_total;
+    if ((st = stage_out(p, 20 + k, gin[k], bytes, &o, &host[1 + k])) != EMRI_FD_OK) return st;
+    gdev[k] = static_cast<double*>(o);
+  }
+  li.g_phi_phi = gdev[0]; li.g_phi_r = gdev[1]; li.g_omega_phi = gdev[2]; li.g_omega_r = gdev[3]; li.g_amp = gdev[4];
+  // forward into the plan's h buffers, then the residual and L
+  in.h_plus = p->s.hbuf;
+  in.h_cross = p->s.hbuf + 2 * cs.nf_total;
+  run_forward(p, cs, in, 16 * (size_t)cs.nf_total);
+  cudaStream_t stm = p->stream;
+  if (cs.nf_total > 0) {
+    launch_loglike(cs, li, p->s, stm);
+    p->launches += 2;
+  } else {
+    cudaMemsetAsync(li.loglike, 0, 8 * (size_t)n_wf, stm);
+  }
+  const bool want = g_phi_phi || g_phi_r || g_omega_phi || g_omega_r || g_amp;
+  if (want) {
+    for (int k = 0; k < 5; k++)
+      if (gdev[k]) cudaMemsetAsync(gdev[k], 0, k < 4 ? kb : 16 * (size_t)cs.amp_total, stm);
+    if (cs.nm_total > 0 && cs.nf_total > 0) {
+      launch_adjoint(cs, in, li, p->s, p->num_sms, stm);
+      p->launches += kAdjointKernels;
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) return EMRI_FD_ERR_CUDA;
+  bool any_host = false;
+  for (int k = 0; k < 6; k++) any_host = any_host || host[k];
+  if (any_host) {
+    if (host[0] && cudaMemcpyAsync(loglike, li.loglike, 8 * (size_t)n_wf, cudaMemcpyDeviceToHost, stm) != cudaSuccess)
+      return EMRI_FD_ERR_CUDA;
+    for (int k = 0; k < 5; k++)
+      if (host[1 + k] && cudaMemcpyAsync(gin[k], gdev[k], k < 4 ? kb : 16 * (size_t)cs.amp_total,
+                                         cudaMemcpyDeviceToHost, stm) != cudaSuccess)
+        return EMRI_FD_ERR_CUDA;
+    if (cudaStreamSynchronize(stm) != cudaSuccess) return EMRI_FD_ERR_CUDA;
   }
   return EMRI_FD_OK;
 }

@@ -544,6 +544,8 @@ __global__ void k_table(double2* tab) {
 
 void launch_table(double2* tab, cudaStream_t st) { k_table<<<(kTabN + 255) / 256, 256, 0, st>>>(tab); }
 
+void launch_scan(int* cnt, long long n, cudaStream_t st) { k_scan<<<1, 1024, 0, st>>>(cnt, n); }
+
 void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st) {
   dim3 gk(8, cs.n_wf);
   k_validate_knots<<<gk, 256, 0, st>>>(s.wf, in, s.status);

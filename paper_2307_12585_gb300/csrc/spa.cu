@@ -20,7 +20,7 @@
 // in ascending run order; warp w handles entries w, w+8, ... for all bins of
 // the tile (BPL per lane) and the 8 warp partials are summed in warp order,
 // so every bin's sum has a fixed order (no atomics on the outputs).
-#include "common.cuh"
+#include "spa_math.cuh"
 
 namespace emrifd {
 namespace {
@@ -44,9 +44,6 @@ struct SpaParams {
   long long tiles_total;
 };
 
-constexpr double kTwoPiOver2p64 = 3.4061215800865545e-19;   // 2 pi / 2^64 (exact scaling of 2 pi)
-constexpr double kMagic = 6755399441055744.0;               // 1.5 * 2^52
-
 template <int BPL, int PREC>
 struct Smem {
   double2 tab[PREC == 0 ? kTabN : 1];
@@ -55,30 +52,6 @@ struct Smem {
   long long tile;
   double red[kWarps][32 * BPL][4];
 };
-
-// root of b u + c u^2 + d u^3 = delta on [ulo, uhi] (monotone, direction dir)
-// FP32 safeguarded Newton (regula-falsi start); returns u and dF/du at u (FP32)
-__device__ __forceinline__ float root_f32(float bf, float cf, float df, float dl, float lo, float hi, int dir,
-                                          float& Dout) {
-  float flo = ((df * lo + cf) * lo + bf) * lo - dl;
-  float fhi = ((df * hi + cf) * hi + bf) * hi - dl;
-  float u = lo + (hi - lo) * __fdividef(flo, flo - fhi);
-  if (!(u >= lo && u <= hi)) u = 0.5f * (lo + hi);
-  float D = 0.f;
-#pragma unroll 1
-  for (int it = 0; it < 6; it++) {
-    float fu = ((df * u + cf) * u + bf) * u - dl;
-    D = (3.f * df * u + 2.f * cf) * u + bf;
-    if (fu == 0.f) break;
-    if ((fu > 0.f) == (dir > 0)) hi = u; else lo = u;
-    float un = u - __fdividef(fu, D);
-    if (!(un >= lo && un <= hi)) un = 0.5f * (lo + hi);
-    u = un;
-  }
-  D = (3.f * df * u + 2.f * cf) * u + bf;
-  Dout = D;
-  return u;
-}
 
 template <int BPL, int PREC>
 __global__ void __launch_bounds__(kThreads, 2) k_spa(SpaParams P) {
@@ -171,71 +144,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_spa(SpaParams P) {
           if (bin < b0 || bin >= b1) continue;
           const double g = neg ? -fq[q] : fq[q];
           const long long key = neg ? kn[q] : kp[q];
-          // a5: segment = s0 + number of run knots already passed by g
-          int a = R.s0 + 1, bb = R.s1 + 1;
-          while (a < bb) {
-            int c = (a + bb) >> 1;
-            long long kk = P.keyF[M.key_base + c];
-            bool passed = R.dir > 0 ? (kk <= key) : (kk >= key);
-            if (passed) a = c + 1; else bb = c;
-          }
-          const int s = a - 1;
+          // a5: segment holding the root
+          const int s = run_segment(R, P.keyF, M.key_base, key);
           const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
           const SegCore C = P.core[M.seg_base + s];
           // a6: root
           const double delta = g - C.A;
-          float Df;
-          float uf = root_f32(C.bf, C.cf, C.df, d2f_bits(delta), d2f_bits(ulo), d2f_bits(uhi), R.dir, Df);
-          double u = f2d_bits(uf);
-          {
-            double res = fma(u, fma(u, fma(u, C.d, C.c), C.b), -delta);
-            float rcf = __fdividef(1.f, Df);
-            u = fma(-res, f2d_bits(rcf), u);
-            // predicted error of that step; near a turnover (small dF/du) iterate
-            float stp = fabsf(d2f_bits(res) * rcf);
-            float kap = fabsf(__fdividef(C.cf + 3.f * C.df * uf, Df));
-            float err = stp * (kap * stp + 4.8e-7f);
-#pragma unroll 1
-            for (int it = 0; it < 4 && err > 1e-13f; it++) {
-              float ufc = d2f_bits(u);
-              float Dc = (3.f * C.df * ufc + 2.f * C.cf) * ufc + C.bf;
-              res = fma(u, fma(u, fma(u, C.d, C.c), C.b), -delta);
-              float rc2 = __fdividef(1.f, Dc);
-              u = fma(-res, f2d_bits(rc2), u);
-              stp = fabsf(d2f_bits(res) * rc2);
-              kap = fabsf(__fdividef(C.cf + 3.f * C.df * ufc, Dc));
-              err = stp * (kap * stp + 4.8e-7f);
-            }
-            // clamp into the piece (u >= 0, so integer order of the bits is numeric order)
-            long long ub_ = __double_as_longlong(u);
-            if (ub_ < __double_as_longlong(ulo)) u = ulo;
-            else if (ub_ > __double_as_longlong(uhi)) u = uhi;
-          }
+          float uf, Df;
+          const double u = solve_root(C, delta, ulo, uhi, R.dir, uf, Df);
           // a8: dF/du and the weight sqrt(h)/sqrt|dF/du| (sqrt(h) is in the amplitude)
           const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
           const long long Dbits = __double_as_longlong(Dd);
           if ((Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0) continue;   // Fdot == 0: no contribution
           const bool pos_slope = Dbits >= 0;
           // a7: phase in Q0.64 turns
-          const double inner = fma(u, fma(u, C.P3, C.P2), C.Q1);
-          const double inseg = u * (delta * C.h - inner);
-          unsigned long long Th = q64_mul(g, C.ts) - C.theta0 + q64_of(inseg);
-          Th += pos_slope ? (0ull - (1ull << 61)) : (1ull << 61);
+          const unsigned long long Th = phase_q64(C, g, delta, u, pos_slope);
           if (PREC == 0) {
-            const double Dabs = fabs(Dd);
-            const double y0 = f2d_bits(rsqrtf(d2f_bits(Dabs)));
-            const double ee = (Dabs * y0) * y0;
-            const double wgt = fma(y0, fma(ee, -0.5, 0.5), y0);
-            // e^{2 pi i Th/2^64}: table entry times a short Taylor series
-            const unsigned long long kq = (Th + (1ull << (63 - kTabBits))) >> (64 - kTabBits);
-            const long long rr = (long long)(Th - (kq << (64 - kTabBits)));
-            const double x = (__longlong_as_double(0x4338000000000000LL + rr) - kMagic) * kTwoPiOver2p64;
-            const double x2 = x * x;
-            const double cx = fma(x2, -0.5, 1.0);
-            const double sx = x * fma(x2, -1.0 / 6.0, 1.0);
-            const double2 T = S.tab[kq & (kTabN - 1)];
-            const double er = fma(T.x, cx, -T.y * sx);
-            const double ei = fma(T.y, cx, T.x * sx);
+            const double wgt = rsqrt_abs(Dd);
+            double er, ei;
+            cis_q64(Th, S.tab, er, ei);
             // a9-a10
             const SegAmp64 Am = P.amp64[M.seg_base + s];
             double are = fma(u, fma(u, fma(u, Am.re[3], Am.re[2]), Am.re[1]), Am.re[0]);

@@ -1,0 +1,113 @@
+// Per-(branch, bin) arithmetic of the SPA sum shared by the output kernel and
+// the adjoint kernel, so that both evaluate exactly the same quantities.
+// (arXiv 2307.12585, Sec. 2.2, Eq. 6: root of the segment cubic; Eq. 3-4, 10:
+// phase 2 pi f t - Phi_V(t) - sgn(Fdot) pi/4 and weight 1/sqrt|Fdot|.)
+#pragma once
+#include "common.cuh"
+
+namespace emrifd {
+
+constexpr double kTwoPiOver2p64 = 3.4061215800865545e-19;   // 2 pi / 2^64 (exact scaling of 2 pi)
+constexpr double kMagic = 6755399441055744.0;               // 1.5 * 2^52
+
+// root of b u + c u^2 + d u^3 = delta on [ulo, uhi] (monotone, direction dir):
+// FP32 safeguarded Newton from a regula-falsi start; returns u and dF/du (FP32)
+__device__ __forceinline__ float root_f32(float bf, float cf, float df, float dl, float lo, float hi, int dir,
+                                          float& Dout) {
+  float flo = ((df * lo + cf) * lo + bf) * lo - dl;
+  float fhi = ((df * hi + cf) * hi + bf) * hi - dl;
+  float u = lo + (hi - lo) * __fdividef(flo, flo - fhi);
+  if (!(u >= lo && u <= hi)) u = 0.5f * (lo + hi);
+  float D = 0.f;
+#pragma unroll 1
+  for (int it = 0; it < 6; it++) {
+    float fu = ((df * u + cf) * u + bf) * u - dl;
+    D = (3.f * df * u + 2.f * cf) * u + bf;
+    if (fu == 0.f) break;
+    if ((fu > 0.f) == (dir > 0)) hi = u; else lo = u;
+    float un = u - __fdividef(fu, D);
+    if (!(un >= lo && un <= hi)) un = 0.5f * (lo + hi);
+    u = un;
+  }
+  D = (3.f * df * u + 2.f * cf) * u + bf;
+  Dout = D;
+  return u;
+}
+
+// a5: segment of the run holding the root for key(g): s0 + knots already passed
+__device__ __forceinline__ int run_segment(const Run& R, const long long* keyF, long long key_base, long long key) {
+  int a = R.s0 + 1, bb = R.s1 + 1;
+  while (a < bb) {
+    int c = (a + bb) >> 1;
+    long long kk = keyF[key_base + c];
+    bool passed = R.dir > 0 ? (kk <= key) : (kk >= key);
+    if (passed) a = c + 1; else bb = c;
+  }
+  return a - 1;
+}
+
+// a6: FP32 start value, FP64 Newton polish (iterated where the predicted error of
+// one step exceeds 1e-13, i.e. near turnovers), clamped into [ulo, uhi]
+__device__ __forceinline__ double solve_root(const SegCore& C, double delta, double ulo, double uhi, int dir,
+                                             float& uf_out, float& Df_out) {
+  float Df;
+  float uf = root_f32(C.bf, C.cf, C.df, d2f_bits(delta), d2f_bits(ulo), d2f_bits(uhi), dir, Df);
+  double u = f2d_bits(uf);
+  double res = fma(u, fma(u, fma(u, C.d, C.c), C.b), -delta);
+  float rcf = __fdividef(1.f, Df);
+  u = fma(-res, f2d_bits(rcf), u);
+  float stp = fabsf(d2f_bits(res) * rcf);
+  float kap = fabsf(__fdividef(C.cf + 3.f * C.df * uf, Df));
+  float err = stp * (kap * stp + 4.8e-7f);
+#pragma unroll 1
+  for (int it = 0; it < 4 && err > 1e-13f; it++) {
+    float ufc = d2f_bits(u);
+    float Dc = (3.f * C.df * ufc + 2.f * C.cf) * ufc + C.bf;
+    res = fma(u, fma(u, fma(u, C.d, C.c), C.b), -delta);
+    float rc2 = __fdividef(1.f, Dc);
+    u = fma(-res, f2d_bits(rc2), u);
+    stp = fabsf(d2f_bits(res) * rc2);
+    kap = fabsf(__fdividef(C.cf + 3.f * C.df * ufc, Dc));
+    err = stp * (kap * stp + 4.8e-7f);
+  }
+  // clamp into the piece (u >= 0, so integer order of the bits is numeric order)
+  long long ub_ = __double_as_longlong(u);
+  if (ub_ < __double_as_longlong(ulo)) u = ulo;
+  else if (ub_ > __double_as_longlong(uhi)) u = uhi;
+  uf_out = uf;
+  Df_out = Df;
+  return u;
+}
+
+// a7: Q0.64 phase (turns) of 2 pi g t - Phi_V(t) + m phi - sgn(Fdot) pi/4
+__device__ __forceinline__ unsigned long long phase_q64(const SegCore& C, double g, double delta, double u,
+                                                        bool pos_slope) {
+  const double inner = fma(u, fma(u, C.P3, C.P2), C.Q1);
+  const double inseg = u * (delta * C.h - inner);
+  unsigned long long Th = q64_mul(g, C.ts) - C.theta0 + q64_of(inseg);
+  Th += pos_slope ? (0ull - (1ull << 61)) : (1ull << 61);
+  return Th;
+}
+
+// e^{2 pi i Th/2^64}: 4096-entry table times 1 + i x - x^2/2 - i x^3/6, |x| <= pi/4096
+__device__ __forceinline__ void cis_q64(unsigned long long Th, const double2* tab, double& er, double& ei) {
+  const unsigned long long kq = (Th + (1ull << (63 - kTabBits))) >> (64 - kTabBits);
+  const long long rr = (long long)(Th - (kq << (64 - kTabBits)));
+  const double x = (__longlong_as_double(0x4338000000000000LL + rr) - kMagic) * kTwoPiOver2p64;
+  const double x2 = x * x;
+  const double cx = fma(x2, -0.5, 1.0);
+  const double sx = x * fma(x2, -1.0 / 6.0, 1.0);
+  const double2 T = tab[kq & (kTabN - 1)];
+  er = fma(T.x, cx, -T.y * sx);
+  ei = fma(T.y, cx, T.x * sx);
+}
+
+// a8: 1/sqrt|D| from an FP32 seed and one FP64 Newton step
+__device__ __forceinline__ double rsqrt_abs(double Dd) {
+  const double Dabs = fabs(Dd);
+  const double y0 = f2d_bits(rsqrtf(d2f_bits(Dabs)));
+  const double ee = (Dabs * y0) * y0;
+  return fma(y0, fma(ee, -0.5, 0.5), y0);
+}
+
+}  // namespace emrifd
