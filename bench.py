@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--waveforms", type=int, default=8)
     ap.add_argument("--tile-bins", type=int, default=128)
+    ap.add_argument("--config", default="paper", choices=["paper", "batch", "mixed-batch", "likelihood"])
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--check-waveforms", type=int, default=8)
     return ap.parse_args()
 
 
@@ -107,29 +111,42 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def oracle_setup_s(w, threads):
+    """time of the oracle's per-waveform set-up (splines, voices, monotone pieces):
+    one call on a single bin"""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    O.sum_modes(w, freqs=w.freqs[len(w.freqs) // 2:len(w.freqs) // 2 + 1], nthreads=threads)
+    return time.perf_counter() - t0
+
+
 def cpu_oracle_rate(w, budget_s=15.0):
-    """The CPU oracle on a strided sample of the waveform's bins (bins are
-    independent, so the sample extrapolates); returns waveforms/s, threads, sample text."""
+    """The CPU oracle on a strided sample of the waveform's bins.  Bins are
+    independent, so the per-bin part extrapolates; the per-waveform set-up is
+    timed on its own and counted once.  Returns waveforms/s, threads, sample text."""
     from oracle import oracle as O
     O.build()
     threads = O.default_threads()
+    setup = oracle_setup_s(w, threads)
     stride = 256
     sel = w.freqs[::stride]
     t0 = time.perf_counter()
     O.sum_modes(w, freqs=sel, nthreads=threads)
     dt = time.perf_counter() - t0
-    # size the timed sample to about budget_s
-    stride = int(min(64, max(1, stride * dt / budget_s)))
+    stride = int(min(64, max(1, stride * max(dt - setup, 1e-3) / budget_s)))
     sel = w.freqs[::stride]
     t0 = time.perf_counter()
     O.sum_modes(w, freqs=sel, nthreads=threads)
     dt = time.perf_counter() - t0
-    per_wave = dt * (w.n_freqs / sel.shape[0])
-    return 1.0 / per_wave, threads, "every %d-th bin (%d of %d bins), %.1f s" % (stride, sel.shape[0], w.n_freqs, dt)
+    per_wave = setup + max(dt - setup, 0.0) * (w.n_freqs / sel.shape[0])
+    return 1.0 / per_wave, threads, ("every %d-th bin (%d of %d bins) in %.1f s, per-waveform set-up %.2f s counted "
+                                     "once, per-bin part extrapolated" % (stride, sel.shape[0], w.n_freqs, dt, setup))
 
 
 def reference_arm(args, rank, world):
-    """CPU oracle timed as the reference implementation (rank 0 only)."""
+    """CPU oracle timed as the reference implementation (rank 0 only): each step
+    evaluates every 16th bin of the workload; the per-waveform set-up is timed
+    separately and counted once per extrapolated waveform."""
     if rank != 0:
         return
     from paper_2307_12585_gb300 import synth
@@ -137,40 +154,66 @@ def reference_arm(args, rank, world):
     O.build()
     w = synth.paper_config(1)
     threads = O.default_threads()
-    stride = 400
+    stride = 16
     sel = w.freqs[::stride]
+    setup = oracle_setup_s(w, threads)
     for _ in range(args.warmup):
         O.sum_modes(w, freqs=sel, nthreads=threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         O.sum_modes(w, freqs=sel, nthreads=threads)
     dt = (time.perf_counter() - t0) / args.steps
-    val = 1.0 / (dt * w.n_freqs / sel.shape[0])
+    per_wave = setup + max(dt - setup, 0.0) * w.n_freqs / sel.shape[0]
+    val = 1.0 / per_wave
     line = {"impl": "reference", "metric": "waveforms/s", "value": val, "unit": "waveforms/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "reference": "CPU FP64 oracle (oracle/oracle.c)"},
             "cpu_baseline": {"value": val, "unit": "waveforms/s", "cores": threads, "kind": "oracle",
-                             "sample": "every %d-th bin per step (%d of %d bins), extrapolated" % (
-                                 stride, sel.shape[0], w.n_freqs)},
+                             "sample": "every %d-th bin per step (%d of %d bins); set-up %.2f s counted once, "
+                                       "per-bin part extrapolated" % (stride, sel.shape[0], w.n_freqs, setup)},
             "e2e": {"value": val, "unit": "waveforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse()
-    rank, world, local = dist_setup(args)
-    if args.impl == "reference":
-        reference_arm(args, rank, world)
-        return
+def event_time(stream, fn, steps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        fn(i)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def max_over_ranks(ms, world):
     import torch
     import torch.distributed as dist
-    from paper_2307_12585_gb300 import api, build, synth
-
-    torch.cuda.set_device(local)
     if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    build.build()
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def base_line(args, world, metric, value, unit, ms, workload, extra=None):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+            "config": {"workload": workload, "precision": args.precision,
+                       "parallelism": "independent waveforms per GPU (replicas)"}}
+    if extra:
+        line.update(extra)
+    return line
+
+
+def run_paper(args, rank, world, local):
+    """Default: the paper-shaped single FP64 waveform (2 yr, 2000 modes, 3,155,760 bins)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2307_12585_gb300 import api, synth
+
     nw = args.waveforms
     seeds = [1 + rank * nw + i for i in range(nw)]
     wfs = [synth.paper_config(s) for s in seeds]
@@ -180,9 +223,8 @@ def main():
     nf = wfs[0].n_freqs
     outs = [(torch.empty(nf, dtype=plan.out_dtype, device="cuda"), torch.empty(nf, dtype=plan.out_dtype, device="cuda"))
             for _ in range(2)]
-    # per-waveform mode-bin counts (exact, from the plan)
     mode_bins = []
-    for i, b in enumerate(dev):
+    for b in dev:
         plan.sum_modes(b, out=outs[0])
         mode_bins.append(plan.stats()["mode_bins"])
     for i in range(args.warmup):
@@ -194,25 +236,15 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
-    stream = plan.stream
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    mb = 0
-    for i in range(args.steps):
-        plan.sum_modes(dev[i % nw], out=outs[i % 2], check=False)
-        mb += mode_bins[i % nw]
-    e1.record(stream)
+    ms = event_time(plan.stream, lambda i: plan.sum_modes(dev[i % nw], out=outs[i % 2], check=False), args.steps)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
     plan.sync()
     st = plan.stats()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
+    mb = sum(mode_bins[i % nw] for i in range(args.steps))
     sec = ms * 1e-3
     value = world * args.steps / sec
     spa_s = st["spa_ns"] * 1e-9 / max(1, st["timed_calls"])
@@ -222,6 +254,27 @@ def main():
     peak_tflops = FP64_PER_CLK_PER_SM * 2 * n_sms * clk_hz / 1e12
     achieved = FP64_FLOPS_PER_MODE_BIN * mb_per_launch / spa_s / 1e12
     issue = FP64_OPS_PER_MODE_BIN * mb_per_launch / spa_s / (FP64_PER_CLK_PER_SM * n_sms * clk_hz)
+
+    mixed = None
+    if args.precision == "fp64" and not args.no_mixed:
+        # the mixed form on the same waveforms and bins, for the speed-up the metric quotes
+        mplan = api.Plan("mixed", conj_partners=True, max_waveforms=1, max_knots=200, max_modes_total=2000,
+                         max_bins_total=nf, tile_bins=args.tile_bins)
+        mout = (torch.empty(nf, dtype=torch.complex64, device="cuda"), torch.empty(nf, dtype=torch.complex64, device="cuda"))
+        for i in range(args.warmup):
+            mplan.sum_modes(dev[i % nw], out=mout, check=False)
+        mplan.sync()
+        mms = event_time(mplan.stream, lambda i: mplan.sum_modes(dev[i % nw], out=mout, check=False), args.steps)
+        mplan.sync()
+        # accuracy of the mixed form against this run's FP64 output of the same waveform
+        plan.sum_modes(dev[0], out=outs[0])
+        mplan.sum_modes(dev[0], out=mout)
+        num = (torch.linalg.vector_norm(mout[0].to(torch.complex128) - outs[0][0]) ** 2 +
+               torch.linalg.vector_norm(mout[1].to(torch.complex128) - outs[0][1]) ** 2)
+        den = torch.linalg.vector_norm(outs[0][0]) ** 2 + torch.linalg.vector_norm(outs[0][1]) ** 2
+        mixed = {"value": world * args.steps / (mms * 1e-3), "unit": "waveforms/s", "ms_per_step": mms / args.steps,
+                 "speedup_vs_fp64": ms / mms, "rel_l2_vs_fp64": float(torch.sqrt(num / den))}
+        mplan.close()
 
     e2e = None
     if not args.no_e2e:
@@ -242,7 +295,7 @@ def main():
             plan.sum_modes_host(hb[i % 2], out=hout[i % 2])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        esteps = max(3, args.steps // 2)
+        esteps = max(3, args.steps // 4)
         for i in range(esteps):
             plan.sum_modes_host(hb[i % 2], out=hout[i % 2])
         torch.cuda.synchronize()
@@ -256,14 +309,7 @@ def main():
         cpu = {"value": v, "unit": "waveforms/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
-        line = {
-            "metric": "waveforms/s", "value": value, "unit": "waveforms/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "waveforms_resident": nw,
-                       "l2": "inputs larger than L2: %d resident waveforms rotated, ~200 MB touched per step" % nw,
-                       "parallelism": "independent waveforms per GPU"},
+        line = base_line(args, world, "waveforms/s", value, "waveforms/s", ms, WORKLOAD, {
             "mode_bin_evals_per_s": world * mb / sec,
             "mode_bins_per_waveform": mb_per_launch,
             "spa_kernel_ms": spa_s * 1e3, "prep_ms": st["prep_ns"] * 1e-6 / max(1, st["timed_calls"]),
@@ -272,10 +318,158 @@ def main():
                          "issue_frac": issue,
                          "note": "FP64 pipe: %d FP64 flops (%d FP64 instructions) per mode-bin; peak = %d FP64 FMA/clk/SM x 2 x SMs x median SM clock" % (
                              FP64_FLOPS_PER_MODE_BIN, FP64_OPS_PER_MODE_BIN, FP64_PER_CLK_PER_SM)},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"], "clocks": clocks,
-        }
+            "mixed_form": mixed, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"], "clocks": clocks})
+        line["config"].update({"waveforms_resident": nw, "tile_bins": args.tile_bins,
+                               "l2": "inputs larger than L2: %d resident waveforms rotated, ~200 MB touched per step" % nw})
         print(json.dumps(line), flush=True)
     plan.close()
+
+
+def run_batched(args, rank, world, local, mixed):
+    """Batched workloads in one graph-captured call: 256 waveforms (N_m ~ U{50..3000},
+    T ~ U(0.5, 4) yr, N_f log-uniform in [1e4, 6e6], uniform or log grids) in FP64, or
+    64 paper-shaped 2 yr waveforms in the mixed form."""
+    import torch
+    from paper_2307_12585_gb300 import api, autotune, synth
+
+    if mixed:
+        nb = args.batch or 64
+        wfs = [synth.paper_config(1 + rank * nb + i) for i in range(nb)]
+        prec = "mixed"
+        workload = "%d paper-shaped 2 yr waveforms (2000 modes, 3,155,760 bins each), mixed precision" % nb
+    else:
+        nb = args.batch or 256
+        wfs = synth.batch_config(nb, seed0=100 + rank * nb)
+        prec = args.precision
+        workload = ("%d waveforms in one call: N_m ~ U{50..3000}, T ~ U(0.5,4) yr, N_f log-uniform [1e4, 6e6], "
+                    "uniform or log grids, K=200" % nb)
+    b = synth.concat(wfs)
+    plan = api.Plan(prec, conj_partners=True, max_waveforms=nb, max_knots=200,
+                    max_knots_total=int(b["knot_off"][-1]), max_modes_total=int(b["mode_off"][-1]),
+                    max_bins_total=int(b["freq_off"][-1]))
+    db = plan.upload(b)
+    nf = int(b["freq_off"][-1])
+    out = (torch.empty(nf, dtype=plan.out_dtype, device="cuda"), torch.empty(nf, dtype=plan.out_dtype, device="cuda"))
+    tune = autotune.tune(plan, db, out)
+    plan.sum_modes(db, out=out)
+    mb = plan.stats()["mode_bins"]
+    g = plan.capture(db, out)
+    for _ in range(args.warmup):
+        g.replay()
+    plan.sync()
+    plan.profile(True)        # resets the launch counter
+    clk = ClockSampler(local)
+    torch.cuda.synchronize()
+    clk.start()
+    ms = event_time(plan.stream, lambda i: g.replay(), args.steps)
+    clocks = clk.stop()
+    plan.sync()
+    ms = max_over_ranks(ms, world)
+    sec = ms * 1e-3
+    extra = {"mode_bin_evals_per_s": world * mb * args.steps / sec, "mode_bins_per_batch": mb,
+             "waveforms_per_step": nb, "bins_per_batch": nf, "autotune": tune, "cuda_graph": True,
+             "gpu_launches": plan.stats()["launches"], "clocks": clocks}
+    if mixed:
+        # speed-up over the FP64 single-waveform form on the same GPU and waveform shape
+        p64 = api.Plan("fp64", max_waveforms=1, max_knots=200, max_modes_total=2000, max_bins_total=wfs[0].n_freqs)
+        d0 = p64.upload(synth.concat([wfs[0]]))
+        o64 = p64.sum_modes(d0)
+        t64 = event_time(p64.stream, lambda i: p64.sum_modes(d0, out=o64, check=False), 10) / 10
+        extra["fp64_single_ms"] = t64
+        extra["speedup_vs_fp64_single"] = (t64 * 1e-3) / (sec / args.steps / nb)
+        # accuracy of every waveform against the FP64 form (device), on all bins
+        hm = (out[0].to(torch.complex128), out[1].to(torch.complex128))
+        errs = []
+        for i, w in enumerate(wfs[: args.check_waveforms]):
+            lo, hi = int(b["freq_off"][i]), int(b["freq_off"][i + 1])
+            di = p64.upload(synth.concat([w]))
+            ref = p64.sum_modes(di)
+            num = sum(torch.linalg.vector_norm(hm[c][lo:hi] - ref[c]) ** 2 for c in range(2))
+            den = sum(torch.linalg.vector_norm(ref[c]) ** 2 for c in range(2))
+            ov = sum(torch.real(torch.vdot(ref[c], hm[c][lo:hi])) / torch.sqrt(
+                torch.linalg.vector_norm(ref[c]) ** 2 * torch.linalg.vector_norm(hm[c][lo:hi]) ** 2) for c in range(2)) / 2
+            errs.append((float(torch.sqrt(num / den)), float(1 - ov)))
+        extra["rel_l2_vs_fp64"] = {"max": max(e[0] for e in errs), "median": float(np.median([e[0] for e in errs])),
+                                   "waveforms_checked": len(errs)}
+        extra["mismatch_vs_fp64"] = {"max": max(e[1] for e in errs), "median": float(np.median([e[1] for e in errs]))}
+        p64.close()
+    if rank == 0:
+        line = base_line(args, world, "waveforms/s", world * nb * args.steps / sec, "waveforms/s", ms, workload, extra)
+        line["dtype"] = "f64" if prec == "fp64" else "f64+f32"
+        line["config"]["precision"] = prec
+        print(json.dumps(line), flush=True)
+    g.close()
+    plan.close()
+
+
+def run_likelihood(args, rank, world, local):
+    """Whittle log-likelihood + gradient of every knot value: T = 1 yr, 500 modes,
+    150 knots, 1,577,880 bins at df = 1/T, PSD 1e-40((1e-3/f)^4 + 1 + (f/2e-2)^2),
+    data = waveform at offset parameters + Gaussian noise, SNR 78."""
+    import torch
+    from paper_2307_12585_gb300 import api, synth
+
+    w = synth.likelihood_config(3 + rank)
+    T = w.meta["T"]
+    df = 1.0 / T
+    plan = api.Plan("fp64", max_waveforms=1, max_knots=w.K, max_modes_total=w.n_modes, max_bins_total=w.n_freqs,
+                    likelihood=True)
+    b = plan.upload(synth.concat([w]))
+    hp, hc = plan.sum_modes(b)
+    S = torch.as_tensor(synth.psd(w.freqs)).cuda()
+    rho = torch.sqrt(4 * df * torch.sum((hp.abs() ** 2 + hc.abs() ** 2) / S))
+    scale = 78.0 / float(rho)
+    b["prefactor"] = b["prefactor"] * scale
+    rng = np.random.default_rng(7)
+    dp = hp * scale * (1 + 0.01j) + torch.as_tensor(synth.noise(rng, w.freqs, df)).cuda()
+    dc = hc * scale * (1 + 0.01j) + torch.as_tensor(synth.noise(rng, w.freqs, df)).cuda()
+    dfs = torch.tensor([df], dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        plan.loglike_and_grad(b, dp, dc, S, dfs, grad=True, check=False)
+    plan.sync()
+    clk = ClockSampler(local)
+    torch.cuda.synchronize()
+    clk.start()
+    ms = event_time(plan.stream, lambda i: plan.loglike_and_grad(b, dp, dc, S, dfs, grad=True, check=False),
+                    args.steps)
+    clocks = clk.stop()
+    plan.sync()
+    lms = event_time(plan.stream, lambda i: plan.loglike_and_grad(b, dp, dc, S, dfs, grad=False, check=False),
+                     args.steps)
+    plan.sync()
+    ms = max_over_ranks(ms, world)
+    if rank == 0:
+        line = base_line(args, world, "likelihood+gradient evaluations/s", world * args.steps / (ms * 1e-3),
+                         "evaluations/s", ms,
+                         "Whittle likelihood + knot gradient: T=1 yr, 500 modes, K=150, 1,577,880 bins, SNR 78",
+                         {"loglike_only_per_s": world * args.steps / (lms * 1e-3),
+                          "n_gradients": 4 * w.K + 2 * w.n_modes * w.K, "clocks": clocks})
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2307_12585_gb300 import build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    if args.config == "paper":
+        run_paper(args, rank, world, local)
+    elif args.config == "batch":
+        run_batched(args, rank, world, local, mixed=False)
+    elif args.config == "mixed-batch":
+        run_batched(args, rank, world, local, mixed=True)
+    elif args.config == "likelihood":
+        run_likelihood(args, rank, world, local)
     if world > 1:
         dist.destroy_process_group()
 

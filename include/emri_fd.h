@@ -196,7 +196,7 @@ emri_fd_status emri_fd_profile(emri_fd_plan_t plan, int enable);
  * latency-critical code that cannot afford cudaMalloc/cudaFree (which may
  * synchronise the device), and plug-ins or callbacks that must not call the
  * allocator.  It calls no cudaMalloc, cudaFree or other allocating routine:
- * all scratch lives in one file-scope __device__ array of 6,505,984 bytes
+ * all scratch lives in one file-scope __device__ array of 6,510,592 bytes
  * (6.2 MiB), which every GPU that loads the library holds until the process
  * exits.
  *   Limits: n_knots in [4, EMRI_FD_NOALLOC_MAX_KNOTS], n_modes in
@@ -223,6 +223,35 @@ emri_fd_status emri_fd_sum_modes_noalloc(int conj_partners, long long n_knots, l
                                          const int* l, const int* m, const int* n, const double* amp,
                                          double theta, double phi, double prefactor, const double* freqs,
                                          void* h_plus, void* h_cross, void* stream);
+
+/*
+ * Change the output-tile width of a plan (32, 64 or 128 bins) for later calls.
+ * Results may change in the last bits (the in-tile summation grouping changes).
+ */
+emri_fd_status emri_fd_set_tile(emri_fd_plan_t plan, int tile_bins);
+
+/*
+ * CUDA-graph capture of one emri_fd_sum_modes call (batches included): the
+ * whole launch sequence (checks, preparation and output kernels) is recorded
+ * once on the plan's stream and replayed with emri_fd_replay.  All data
+ * pointers must be device memory; the graph reads them at every replay (the
+ * caller may change their contents, not their sizes or addresses).  The graph
+ * owns a copy of the batch's slice table; the plan's scratch is shared, so
+ * replays and other calls of the plan must stay ordered on its stream.
+ * Errors: as emri_fd_sum_modes, EMRI_FD_ERR_ARG for host pointers.
+ */
+typedef struct emri_fd_graph_s* emri_fd_graph_t;
+emri_fd_status emri_fd_capture(emri_fd_plan_t plan, int n_waveforms,
+                               const long long* knot_off, const long long* mode_off, const long long* freq_off,
+                               const double* t, const double* phi_phi, const double* phi_r,
+                               const double* omega_phi, const double* omega_r,
+                               const int* l, const int* m, const int* n, const double* amp,
+                               const double* theta, const double* phi, const double* prefactor,
+                               const double* freqs, void* h_plus, void* h_cross, emri_fd_graph_t* graph);
+/* Launch a captured call on its plan's stream (asynchronous). */
+emri_fd_status emri_fd_replay(emri_fd_graph_t graph);
+/* Release a captured call (synchronises its plan's stream first). */
+void emri_fd_graph_destroy(emri_fd_graph_t graph);
 
 /* Release the plan and its device memory (synchronises its stream first). */
 void emri_fd_plan_destroy(emri_fd_plan_t plan);

@@ -19,7 +19,8 @@ STATUS = {0: "EMRI_FD_OK", 1: "EMRI_FD_ERR_ARG", 2: "EMRI_FD_ERR_KNOTS", 3: "EMR
           4: "EMRI_FD_ERR_MODE", 5: "EMRI_FD_ERR_NONFINITE", 6: "EMRI_FD_ERR_CAPACITY",
           7: "EMRI_FD_ERR_CUDA", 8: "EMRI_FD_ERR_OOM", 9: "EMRI_FD_ERR_TIMEOUT"}
 EXPORTS = ("emri_fd_plan", "emri_fd_sum_modes", "emri_fd_loglike_and_grad", "emri_fd_sync", "emri_fd_stats",
-           "emri_fd_profile", "emri_fd_plan_destroy", "emri_fd_strerror", "emri_fd_sum_modes_noalloc")
+           "emri_fd_profile", "emri_fd_plan_destroy", "emri_fd_strerror", "emri_fd_sum_modes_noalloc",
+           "emri_fd_set_tile", "emri_fd_capture", "emri_fd_replay", "emri_fd_graph_destroy")
 
 
 class EmriFdError(RuntimeError):
@@ -58,6 +59,15 @@ def lib():
         L.emri_fd_sum_modes.restype = C.c_int
         L.emri_fd_loglike_and_grad.argtypes = [vp, C.c_int, vp, vp, vp] + [dp] * 5 + [ip] * 3 + [dp] * 5 + [dp] * 10
         L.emri_fd_loglike_and_grad.restype = C.c_int
+        L.emri_fd_set_tile.argtypes = [vp, C.c_int]
+        L.emri_fd_set_tile.restype = C.c_int
+        L.emri_fd_capture.argtypes = [vp, C.c_int, vp, vp, vp] + [dp] * 5 + [ip] * 3 + [dp] * 5 + [vp, vp,
+                                                                                          C.POINTER(C.c_void_p)]
+        L.emri_fd_capture.restype = C.c_int
+        L.emri_fd_replay.argtypes = [vp]
+        L.emri_fd_replay.restype = C.c_int
+        L.emri_fd_graph_destroy.argtypes = [vp]
+        L.emri_fd_graph_destroy.restype = None
         L.emri_fd_sync.argtypes = [vp]
         L.emri_fd_sync.restype = C.c_int
         L.emri_fd_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
@@ -122,6 +132,28 @@ def emri_fd_sum_modes_noalloc(conj_partners, n_knots, n_modes, n_freqs, t, phi_p
                                                                           l, m, n, amp)],
                                            float(theta), float(phi), float(prefactor), C.c_void_p(int(freqs)),
                                            C.c_void_p(int(h_plus)), C.c_void_p(int(h_cross)), C.c_void_p(int(stream)))
+
+
+def emri_fd_set_tile(plan, tile_bins) -> int:
+    return lib().emri_fd_set_tile(C.c_void_p(plan), int(tile_bins))
+
+
+def emri_fd_capture(plan, n_waveforms, knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r,
+                    l, m, n, amp, theta, phi, prefactor, freqs, h_plus, h_cross):
+    """Returns (status, graph handle)."""
+    g = C.c_void_p()
+    code = lib().emri_fd_capture(C.c_void_p(plan), int(n_waveforms), *[C.c_void_p(int(x)) for x in (
+        knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r, l, m, n, amp, theta, phi, prefactor,
+        freqs, h_plus, h_cross)], C.byref(g))
+    return code, g.value
+
+
+def emri_fd_replay(graph) -> int:
+    return lib().emri_fd_replay(C.c_void_p(graph))
+
+
+def emri_fd_graph_destroy(graph) -> None:
+    lib().emri_fd_graph_destroy(C.c_void_p(graph))
 
 
 def emri_fd_sync(plan) -> int:
@@ -279,6 +311,19 @@ class Plan:
             _check(emri_fd_sync(self.handle), "emri_fd_loglike_and_grad (device checks)")
         return L, g
 
+    def set_tile(self, tile_bins):
+        _check(emri_fd_set_tile(self.handle, tile_bins), "emri_fd_set_tile")
+
+    def capture(self, b, out):
+        """Capture emri_fd_sum_modes(b) -> out into a CUDA graph; returns a Graph."""
+        ko, mo, fo = (np.ascontiguousarray(np.asarray(b[k], np.int64)) for k in ("knot_off", "mode_off", "freq_off"))
+        code, g = emri_fd_capture(self.handle, len(ko) - 1, ko.ctypes.data, mo.ctypes.data, fo.ctypes.data,
+                                  *[_addr(b[k]) for k in ("t", "phi_phi", "phi_r", "omega_phi", "omega_r", "l", "m",
+                                                          "n", "amp", "theta", "phi", "prefactor", "freqs")],
+                                  _addr(out[0]), _addr(out[1]))
+        _check(code, "emri_fd_capture")
+        return Graph(g, self)
+
     def sync(self):
         _check(emri_fd_sync(self.handle), "emri_fd_sync")
 
@@ -287,6 +332,27 @@ class Plan:
 
     def profile(self, enable=True):
         emri_fd_profile(self.handle, enable)
+
+
+class Graph:
+    """A captured emri_fd_sum_modes call (emri_fd_replay / emri_fd_graph_destroy)."""
+
+    def __init__(self, handle, plan):
+        self.handle, self.plan = handle, plan
+
+    def replay(self):
+        _check(emri_fd_replay(self.handle), "emri_fd_replay")
+
+    def close(self):
+        if self.handle:
+            emri_fd_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def host_batch(batch):

@@ -1,0 +1,85 @@
+"""Tile-shape autotuner for the SPA output kernel.
+
+For a batch already resident on the device, times emri_fd_sum_modes with each
+output-tile width (32, 64, 128 bins) using CUDA events on the plan's stream,
+keeps the fastest, and caches the choice in a JSON file keyed by the device
+name, precision and a coarse signature of the batch (waveform count and the
+powers of two of the total modes and bins).  Cache file:
+$EMRI_FD_AUTOTUNE_CACHE, else ~/.cache/emri_fd/autotune.json.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+CANDIDATES = (32, 64, 128)
+
+
+def cache_path() -> str:
+    p = os.environ.get("EMRI_FD_AUTOTUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "emri_fd", "autotune.json")
+
+
+def signature(plan, b) -> str:
+    import torch
+    n_wf = len(b["knot_off"]) - 1
+    nm = int(b["mode_off"][-1])
+    nf = int(b["freq_off"][-1])
+    name = torch.cuda.get_device_name(plan.device)
+    return "%s|p%d|w%d|m2^%d|f2^%d" % (name, plan.precision, n_wf, int(math.log2(max(nm, 1))),
+                                       int(math.log2(max(nf, 1))))
+
+
+def _load(path):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(path, data):
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(data, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def tune(plan, b, out, reps: int = 3, use_cache: bool = True, candidates=CANDIDATES) -> dict:
+    """Set the plan's tile width to the fastest candidate for batch b; returns
+    {"tile_bins": T, "ms": {T: ms...}, "cached": bool}."""
+    import torch
+    path = cache_path()
+    key = signature(plan, b)
+    data = _load(path) if use_cache else {}
+    if key in data:
+        plan.set_tile(int(data[key]["tile_bins"]))
+        return {"tile_bins": int(data[key]["tile_bins"]), "ms": data[key].get("ms", {}), "cached": True}
+    times = {}
+    stream = plan.stream
+    for tb in candidates:
+        plan.set_tile(tb)
+        plan.sum_modes(b, out=out, check=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            plan.sum_modes(b, out=out, check=False)
+        e1.record(stream)
+        e1.synchronize()
+        times[tb] = e0.elapsed_time(e1) / reps
+    plan.sync()
+    best = min(times, key=times.get)
+    plan.set_tile(best)
+    if use_cache:
+        data[key] = {"tile_bins": int(best), "ms": {str(k): v for k, v in times.items()}}
+        _save(path, data)
+    return {"tile_bins": int(best), "ms": times, "cached": False}

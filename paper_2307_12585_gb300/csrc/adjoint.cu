@@ -31,7 +31,7 @@ constexpr double kInv2Pi = 0.15915494309189535;
 
 // ------------------------------------------------------------ residual and L
 __global__ void k_residual(const WfInfo* wf, const double2* hp, const double2* hc, const double2* dp,
-                           const double2* dc, const double* psd, const double* dfs, double4* G, double* Lpart,
+                           const double2* dc, const double* psd, const double* dfs, dbl4* G, double* Lpart,
                            int* status) {
   __shared__ double red[256];
   const WfInfo W = wf[blockIdx.y];
@@ -47,7 +47,7 @@ __global__ void k_residual(const WfInfo* wf, const double2* hp, const double2* h
     const double rpr = x.x - a.x, rpi = x.y - a.y, rcr = y.x - c.x, rci = y.y - c.y;
     const double w = 4.0 * df / S;
     acc += (rpr * rpr + rpi * rpi + rcr * rcr + rci * rci) * (-0.5 * w);
-    G[b] = make_double4(w * rpr, w * rpi, w * rcr, w * rci);
+    G[b] = mk_dbl4(w * rpr, w * rpi, w * rcr, w * rci);
   }
   if (bad) atomicOr(status, bad);
   red[threadIdx.x] = acc;
@@ -101,7 +101,7 @@ struct AdjParams {
   const Run* runs;
   const RunBins* rb;
   const double* freqs;
-  const double4* G;
+  const dbl4* G;
   const int* item_off;     // exclusive scan of items per run, total at [run_cap]
   long long run_cap;
   const double2* tab;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjParams P) {
         const double Ai = fma(u, fma(u, fma(u, Am.im[3], Am.im[2]), Am.im[1]), Am.im[0]);
         const double dAr = fma(u, fma(u, 3.0 * Am.re[3], 2.0 * Am.re[2]), Am.re[1]);
         const double dAi = fma(u, fma(u, 3.0 * Am.im[3], 2.0 * Am.im[2]), Am.im[1]);
-        const double4 Gb = P.G[b];
+        const dbl4 Gb = P.G[b];
         double Qr, Qi;
         if (!neg) { Qr = M.alpha * Gb.x + M.beta * Gb.w; Qi = -M.alpha * Gb.y + M.beta * Gb.z; }
         else { Qr = M.alpha * Gb.x - M.beta * Gb.w; Qi = M.alpha * Gb.y + M.beta * Gb.z; }
@@ -337,7 +337,7 @@ __device__ __forceinline__ void tri_row_t(const double* t, int K, int i, double&
 }
 
 __device__ void spline_adjoint(const double* t, int K, const double* gY, long long ys, const double* gM0, long long ms,
-                               const double* cp, const double* im, double* out, long long os, double* z) {
+                               const dbl4* fac, double* out, long long os, double* z) {
   // z holds K doubles of scratch with stride os (written into out first)
   for (int i = 0; i < K; i++) z[i * os] = gM0[i * ms];
   {
@@ -350,18 +350,16 @@ __device__ void spline_adjoint(const double* t, int K, const double* gY, long lo
   }
   // Tri = L U with L lower bidiagonal (diag m_i, sub a_i), U unit upper (super c'_i):
   // Tri^T lam = g  <=>  U^T w = g (forward), L^T lam = w (backward)
-  for (int i = 2; i <= K - 2; i++) z[i * os] -= cp[i - 1] * z[(i - 1) * os];
+  for (int i = 2; i <= K - 2; i++) z[i * os] -= fac[i - 1].x * z[(i - 1) * os];
   {
     double a, b, c, s;
-    z[(K - 2) * os] *= im[K - 2];
+    z[(K - 2) * os] *= fac[K - 2].y;
     for (int i = K - 3; i >= 1; i--) {
       tri_row_t(t, K, i + 1, a, b, c, s);
-      z[i * os] = (z[i * os] - a * z[(i + 1) * os]) * im[i];
+      z[i * os] = (z[i * os] - a * z[(i + 1) * os]) * fac[i].y;
     }
   }
   // lam -> y through rhs_i = s_i * 6 [(y_{i+1} - y_i)/h_i - (y_i - y_{i-1})/h_{i-1}]
-  double gy_prev = 0.0;  // not used; gradients assembled below
-  (void)gy_prev;
   for (int i = 0; i < K; i++) out[i * os] = gY[i * ys];
   for (int i = 1; i <= K - 2; i++) {
     double a, b, c, s;
@@ -375,7 +373,7 @@ __device__ void spline_adjoint(const double* t, int K, const double* gY, long lo
 }
 
 __global__ void k_spline_adj(int n_wf, const WfInfo* wf, const ModeInfo* modes, long long nm_total, const double* t,
-                             const double* cp, const double* im, const double* fgY, const double* fgM,
+                             const dbl4* fac, const double* fgY, const double* fgM,
                              long long K_total, const double* agY, const double* agM, double* zf, double* za,
                              double* g_pp, double* g_pr, double* g_op, double* g_or, double* g_amp) {
   long long sid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -385,8 +383,8 @@ __global__ void k_spline_adj(int n_wf, const WfInfo* wf, const ModeInfo* modes, 
     const WfInfo W = wf[w];
     double* outp = q == 0 ? g_pp : q == 1 ? g_pr : q == 2 ? g_op : g_or;
     if (!outp) return;
-    spline_adjoint(t + W.ko, (int)W.K, fgY + q * K_total + W.ko, 1, fgM + q * K_total + W.ko, 1, cp + W.ko,
-                   im + W.ko, outp + W.ko, 1, zf + q * K_total + W.ko);
+    spline_adjoint(t + W.ko, (int)W.K, fgY + q * K_total + W.ko, 1, fgM + q * K_total + W.ko, 1, fac + W.ko,
+                   outp + W.ko, 1, zf + q * K_total + W.ko);
     return;
   }
   sid -= nfund;
@@ -395,8 +393,8 @@ __global__ void k_spline_adj(int n_wf, const WfInfo* wf, const ModeInfo* modes, 
   int part = (int)(sid & 1);
   const ModeInfo M = modes[j];
   const WfInfo W = wf[M.wf];
-  spline_adjoint(t + W.ko, (int)W.K, agY + 2 * M.key_base + part, 2, agM + 2 * M.key_base + part, 2, cp + W.ko,
-                 im + W.ko, g_amp + 2 * M.key_base + part, 2, za + 2 * M.key_base + part);
+  spline_adjoint(t + W.ko, (int)W.K, agY + 2 * M.key_base + part, 2, agM + 2 * M.key_base + part, 2, fac + W.ko,
+                 g_amp + 2 * M.key_base + part, 2, za + 2 * M.key_base + part);
 }
 
 }  // namespace
@@ -407,7 +405,7 @@ void launch_loglike(const CallShape& cs, const LikeInputs& li, const DevScratch&
                                 reinterpret_cast<const double2*>(s.hbuf) + cs.nf_total,
                                 reinterpret_cast<const double2*>(li.data_plus),
                                 reinterpret_cast<const double2*>(li.data_cross), li.psd, li.df,
-                                reinterpret_cast<double4*>(s.Gbuf), s.Lpart, s.status);
+                                reinterpret_cast<dbl4*>(s.Gbuf), s.Lpart, s.status);
   k_loglike_final<<<(cs.n_wf + 63) / 64, 64, 0, st>>>(cs.n_wf, s.Lpart, li.loglike);
 }
 
@@ -419,7 +417,7 @@ void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& 
   cudaMemsetAsync(s.slots, 0, sizeof(double) * 48 * (size_t)cs.seg_total, st);
   AdjParams p;
   p.wf = s.wf; p.modes = s.modes; p.core = s.core; p.amp64 = s.amp64; p.crit = s.crit; p.keyF = s.keyF;
-  p.runs = s.runs; p.rb = s.rbins; p.freqs = in.freqs; p.G = reinterpret_cast<const double4*>(s.Gbuf);
+  p.runs = s.runs; p.rb = s.rbins; p.freqs = in.freqs; p.G = reinterpret_cast<const dbl4*>(s.Gbuf);
   p.item_off = s.item_off; p.run_cap = s.run_cap; p.tab = s.tab; p.slots = s.slots; p.status = s.status;
   const size_t sm = sizeof(double2) * kTabN;
   cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -434,7 +432,7 @@ void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& 
   k_fund_knot<<<gk, 128, 0, st>>>(cs.n_wf, s.wf, in.t, s.fseg, cs.K_total, s.fgY, s.fgM);
   long long nser = 4LL * cs.n_wf + 2 * cs.nm_total;
   k_spline_adj<<<(unsigned)((nser + 127) / 128), 128, 0, st>>>(
-      cs.n_wf, s.wf, s.modes, cs.nm_total, in.t, s.spl_cp, s.spl_im, s.fgY, s.fgM, cs.K_total, s.agY, s.agM, s.zf,
+      cs.n_wf, s.wf, s.modes, cs.nm_total, in.t, s.spl_fac, s.fgY, s.fgM, cs.K_total, s.agY, s.agM, s.zf,
       s.za, li.g_phi_phi, li.g_phi_r, li.g_omega_phi, li.g_omega_r, li.g_amp);
 }
 

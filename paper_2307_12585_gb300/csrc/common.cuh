@@ -3,7 +3,7 @@
 // Data layout in HBM, per call (all plan-owned scratch, sized at plan creation):
 //   WfInfo[n_wf]             per-waveform slice offsets and derived bases
 //   ModeInfo[sum N_m]        per-mode numbers, waveform id, polarisation weights
-//   spl_cprime/spl_invm      per-knot factors of each waveform's not-a-knot system
+//   spl_fac, spl_ih          per-knot factors of each waveform's not-a-knot system
 //   fundM[4][sum K]          knot second derivatives of Phi_phi, Phi_r, Om_phi, Om_r
 //   ampM[sum N_m K][2]       knot second derivatives of Re A, Im A
 //   SegCore[sum N_m (K-1)]   per (mode, segment): frequency cubic, phase polynomial,
@@ -64,6 +64,11 @@ struct __align__(16) SegCore {
   float bf, cf, df, pad;   // FP32 copies of b, c, d for the root's initial guess
 };
 static_assert(sizeof(SegCore) == 112, "SegCore layout");
+
+struct __align__(32) dbl4 { double x, y, z, w; };
+__host__ __device__ __forceinline__ dbl4 mk_dbl4(double x, double y, double z, double w) {
+  dbl4 r; r.x = x; r.y = y; r.z = z; r.w = w; return r;
+}
 
 struct __align__(16) SegAmp64 { double re[4], im[4]; };   // prefactor sqrt(h) A(u), cubic in u
 struct __align__(16) SegAmp32 { float re[4], im[4]; };
@@ -164,7 +169,8 @@ struct DevScratch {
   unsigned long long* counters;   // [0] tile queue, [1] mode-bins, [2] runs total, [3] busy tiles
   WfInfo* wf;
   ModeInfo* modes;
-  double *spl_cp, *spl_im;        // [sum K] Thomas factors per waveform knot
+  dbl4* spl_fac;               // [sum K] {c'_i, 1/m_i, s_i/m_i, a_i/m_i} of each waveform's not-a-knot sweep
+  double* spl_ih;                 // [sum K] 1/h_k
   double* fundM;                  // [4][sum K]
   double* ampM;                   // [sum N_m K][2]
   SegCore* core;

@@ -134,8 +134,8 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
   AL(s.counters, 8);
   AL(s.wf, d->max_waveforms);
   AL(s.modes, p->cap_nm);
-  AL(s.spl_cp, p->cap_K);
-  AL(s.spl_im, p->cap_K);
+  AL(s.spl_fac, p->cap_K);
+  AL(s.spl_ih, p->cap_K);
   AL(s.fundM, 4 * p->cap_K);
   AL(s.ampM, 2 * p->cap_amp);
   AL(s.core, p->cap_seg);
@@ -476,4 +476,98 @@ emri_fd_status emri_fd_profile(emri_fd_plan_t p, int enable) {
   return EMRI_FD_OK;
 }
 
+struct emri_fd_graph_s {
+  cudaGraphExec_t exec = nullptr;
+  WfInfo* wf = nullptr;       // the graph's own waveform table
+  emri_fd_plan_s* plan = nullptr;
+};
+
+emri_fd_status emri_fd_set_tile(emri_fd_plan_t p, int tile_bins) {
+  if (!p || !(tile_bins == 32 || tile_bins == 64 || tile_bins == 128)) return EMRI_FD_ERR_ARG;
+  p->desc.tile_bins = tile_bins;
+  return EMRI_FD_OK;
+}
+
+emri_fd_status emri_fd_capture(emri_fd_plan_t p, int n_wf, const long long* knot_off, const long long* mode_off,
+                               const long long* freq_off, const double* t, const double* phi_phi,
+                               const double* phi_r, const double* omega_phi, const double* omega_r, const int* l,
+                               const int* m, const int* n, const double* amp, const double* theta,
+                               const double* phi, const double* prefactor, const double* freqs, void* h_plus,
+                               void* h_cross, emri_fd_graph_t* graph) {
+  if (!p || !graph) return EMRI_FD_ERR_ARG;
+  *graph = nullptr;
+  const void* dptrs[] = {t, phi_phi, phi_r, omega_phi, omega_r, l, m, n, amp, theta, phi, prefactor, freqs,
+                         h_plus, h_cross};
+  for (const void* q : dptrs)
+    if (q && !is_device_ptr(q)) return EMRI_FD_ERR_ARG;   // a graph cannot capture host staging
+  CallShape cs;
+  DevInputs in;
+  emri_fd_status st = prepare_call(p, n_wf, knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r, l,
+                                   m, n, amp, theta, phi, prefactor, freqs, cs, in);
+  if (st != EMRI_FD_OK) return st;
+  if (cs.nf_total > 0 && (!h_plus || !h_cross)) return EMRI_FD_ERR_ARG;
+  in.h_plus = h_plus;
+  in.h_cross = h_cross;
+  emri_fd_graph_s* G = new emri_fd_graph_s();
+  G->plan = p;
+  if (cudaMalloc(&G->wf, sizeof(WfInfo) * n_wf) != cudaSuccess) { cudaGetLastError(); delete G; return EMRI_FD_ERR_OOM; }
+  if (cudaMemcpyAsync(G->wf, p->wf_pinned, sizeof(WfInfo) * n_wf, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError(); cudaFree(G->wf); delete G; return EMRI_FD_ERR_CUDA;
+  }
+  // the captured launches read the graph's own waveform table; they are recorded on
+  // a private non-blocking stream (the plan's stream may be the legacy default
+  // stream, which cannot be captured); replays run on the plan's stream
+  cudaStream_t cap = nullptr;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError(); cudaFree(G->wf); delete G; return EMRI_FD_ERR_CUDA;
+  }
+  WfInfo* saved = p->s.wf;
+  cudaStream_t saved_stream = p->stream;
+  p->s.wf = G->wf;
+  p->stream = cap;
+  const bool prof = p->profiling;
+  const long long launches = p->launches;
+  p->profiling = false;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    run_forward(p, cs, in, (p->desc.precision == EMRI_FD_FP64 ? 16 : 8) * (size_t)cs.nf_total);
+    e = cudaStreamEndCapture(cap, &g);
+  }
+  p->s.wf = saved;
+  p->stream = saved_stream;
+  p->profiling = prof;
+  p->launches = launches;
+  cudaStreamDestroy(cap);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    cudaFree(G->wf);
+    delete G;
+    return EMRI_FD_ERR_CUDA;
+  }
+  *graph = G;
+  return EMRI_FD_OK;
+}
+
+emri_fd_status emri_fd_replay(emri_fd_graph_t G) {
+  if (!G || !G->exec) return EMRI_FD_ERR_ARG;
+  if (cudaGraphLaunch(G->exec, G->plan->stream) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_CUDA; }
+  G->plan->launches += kPrepKernels + 1;
+  return EMRI_FD_OK;
+}
+
+void emri_fd_graph_destroy(emri_fd_graph_t G) {
+  if (!G) return;
+  cudaStreamSynchronize(G->plan->stream);
+  if (G->exec) cudaGraphExecDestroy(G->exec);
+  if (G->wf) cudaFree(G->wf);
+  cudaGetLastError();
+  delete G;
+}
+
 }  // extern "C"
+

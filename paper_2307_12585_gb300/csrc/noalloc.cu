@@ -35,9 +35,9 @@ constexpr size_t kOffCounters = kOffStatus + al256(sizeof(int));
 constexpr size_t kOffWf = kOffCounters + al256(8 * sizeof(unsigned long long));
 constexpr size_t kOffAngles = kOffWf + al256(sizeof(WfInfo));
 constexpr size_t kOffModes = kOffAngles + al256(3 * sizeof(double));
-constexpr size_t kOffCp = kOffModes + al256(kNaMaxModes * sizeof(ModeInfo));
-constexpr size_t kOffIm = kOffCp + al256(kNaMaxK * sizeof(double));
-constexpr size_t kOffFundM = kOffIm + al256(kNaMaxK * sizeof(double));
+constexpr size_t kOffFac = kOffModes + al256(kNaMaxModes * sizeof(ModeInfo));
+constexpr size_t kOffIh = kOffFac + al256(kNaMaxK * sizeof(dbl4));
+constexpr size_t kOffFundM = kOffIh + al256(kNaMaxK * sizeof(double));
 constexpr size_t kOffAmpM = kOffFundM + al256(4 * kNaMaxK * sizeof(double));
 constexpr size_t kOffCore = kOffAmpM + al256(2 * kNaMaxAmp * sizeof(double));
 constexpr size_t kOffAmp64 = kOffCore + al256(kNaMaxSeg * sizeof(SegCore));
@@ -49,7 +49,7 @@ constexpr size_t kOffRunF = kOffRuns + al256(kNaRunCap * sizeof(Run));
 constexpr size_t kOffRbins = kOffRunF + al256(kNaRunCap * sizeof(double2));
 constexpr size_t kOffTab = kOffRbins + al256(kNaRunCap * sizeof(RunBins));
 constexpr size_t kNaBytes = kOffTab + al256(kTabN * sizeof(double2));
-static_assert(kNaBytes == 6505984, "the size stated in include/emri_fd.h");
+static_assert(kNaBytes == 6510592, "the size stated in include/emri_fd.h");
 
 // The scratch.  In host code this name is only a stand-in for the device
 // symbol; its device address comes from cudaGetSymbolAddress below.
@@ -119,8 +119,8 @@ extern "C" emri_fd_status emri_fd_sum_modes_noalloc(int conj_partners, long long
   s.counters = reinterpret_cast<unsigned long long*>(base + kOffCounters);
   s.wf = reinterpret_cast<WfInfo*>(base + kOffWf);
   s.modes = reinterpret_cast<ModeInfo*>(base + kOffModes);
-  s.spl_cp = reinterpret_cast<double*>(base + kOffCp);
-  s.spl_im = reinterpret_cast<double*>(base + kOffIm);
+  s.spl_fac = reinterpret_cast<dbl4*>(base + kOffFac);
+  s.spl_ih = reinterpret_cast<double*>(base + kOffIh);
   s.fundM = reinterpret_cast<double*>(base + kOffFundM);
   s.ampM = reinterpret_cast<double*>(base + kOffAmpM);
   s.core = reinterpret_cast<SegCore*>(base + kOffCore);

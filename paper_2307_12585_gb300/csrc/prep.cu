@@ -20,27 +20,34 @@ constexpr double kInv2PiLo = -9.839338337591243e-18;
 // ------------------------------------------------------------------ checks
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double_as_longlong(x) & 0x7FF0000000000000LL) != 0x7FF0000000000000LL;
+}
+
 __global__ void k_validate_knots(const WfInfo* wf, DevInputs in, int* status) {
   const WfInfo W = wf[blockIdx.y];
   int bad = 0;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < W.K; k += (long long)gridDim.x * blockDim.x) {
     long long i = W.ko + k;
     double t = in.t[i];
-    if (!(finite(t) && finite(in.phi_phi[i]) && finite(in.phi_r[i]) && finite(in.omega_phi[i]) && finite(in.omega_r[i])))
+    if (!(finite_bits(t) && finite_bits(in.phi_phi[i]) && finite_bits(in.phi_r[i]) && finite_bits(in.omega_phi[i]) &&
+          finite_bits(in.omega_r[i])))
       bad |= ST_NONFINITE;
-    if (k + 1 < W.K && !(in.t[i + 1] > t)) bad |= ST_KNOTS;
+    if (k + 1 < W.K && !(ordkey(in.t[i + 1]) > ordkey(t))) bad |= ST_KNOTS;
   }
   if (bad) atomicOr(status, bad);
 }
 
+// frequencies: positive, finite and strictly increasing, checked on the bit
+// patterns (for positive doubles integer order is numeric order)
 __global__ void k_validate_freqs(const WfInfo* wf, DevInputs in, int* status) {
   const WfInfo W = wf[blockIdx.y];
   int bad = 0;
+  const long long* fb = reinterpret_cast<const long long*>(in.freqs) + W.fo;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < W.nf; k += (long long)gridDim.x * blockDim.x) {
-    long long i = W.fo + k;
-    double f = in.freqs[i];
-    if (!(f > 0.0) || !finite(f)) bad |= ST_FREQ;
-    if (k + 1 < W.nf && !(in.freqs[i + 1] > f)) bad |= ST_FREQ;
+    const long long u = fb[k];
+    if (!(u > 0 && u < 0x7FF0000000000000LL)) bad |= ST_FREQ;
+    if (k + 1 < W.nf && !(fb[k + 1] > u)) bad |= ST_FREQ;
   }
   if (bad) atomicOr(status, bad);
 }
@@ -48,27 +55,32 @@ __global__ void k_validate_freqs(const WfInfo* wf, DevInputs in, int* status) {
 __global__ void k_validate_amp(long long n2, const double* amp, int* status) {
   int bad = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
-    if (!finite(amp[i])) bad = ST_NONFINITE;
+    if (!finite_bits(amp[i])) bad = ST_NONFINITE;
   if (bad) atomicOr(status, bad);
 }
 
 // ---------------------------------------------------- spin-weighted harmonic
 // -2Y_lm(theta, phi) = S_lm(theta) e^{i m phi} with
 // S_lm = (-1)^s sqrt((2l+1)/4pi) d^l_{m,-s}(theta), s = -2, and the Wigner
-// small-d sum  d^l_{a,b}(x) = sum_k (-1)^{a-b+k} sqrt((l+a)!(l-a)!(l+b)!(l-b)!)
+// small-d sum (1/k! from a table of exact-as-possible constants, k <= 40)  d^l_{a,b}(x) = sum_k (-1)^{a-b+k} sqrt((l+a)!(l-a)!(l+b)!(l-b)!)
 //   / ((l+b-k)! k! (a-b+k)! (l-a-k)!) cos^{2l+b-a-2k}(x/2) sin^{a-b+2k}(x/2).
-__device__ double fact_d(int n) { double f = 1.0; for (int i = 2; i <= n; i++) f *= (double)i; return f; }
-__device__ double ipow(double x, int n) { double r = 1.0; for (int i = 0; i < n; i++) r *= x; return r; }
+__constant__ double c_invfact[41] = {1.0, 1.0, 0.5, 0.16666666666666666, 0.041666666666666664, 0.008333333333333333, 0.001388888888888889, 0.0001984126984126984, 2.48015873015873e-05, 2.7557319223985893e-06, 2.755731922398589e-07, 2.505210838544172e-08, 2.08767569878681e-09, 1.6059043836821613e-10, 1.1470745597729725e-11, 7.647163731819816e-13, 4.779477332387385e-14, 2.8114572543455206e-15, 1.5619206968586225e-16, 8.22063524662433e-18, 4.110317623312165e-19, 1.9572941063391263e-20, 8.896791392450574e-22, 3.8681701706306835e-23, 1.6117375710961184e-24, 6.446950284384474e-26, 2.4795962632247972e-27, 9.183689863795546e-29, 3.279889237069838e-30, 1.1309962886447718e-31, 3.7699876288159054e-33, 1.2161250415535181e-34, 3.800390754854744e-36, 1.151633562077195e-37, 3.387157535521162e-39, 9.67759295863189e-41, 2.688220266286636e-42, 7.265460179153071e-44, 1.911963205040282e-45, 4.902469756513544e-47, 1.225617439128386e-48};
 
-__device__ double swsh_theta(int l, int m, double theta) {
+__device__ __forceinline__ double ipow(double x, int n) {
+  double r = 1.0;
+  while (n) { if (n & 1) r *= x; x *= x; n >>= 1; }
+  return r;
+}
+
+__device__ double swsh_theta(int l, int m, double ch, double sh) {
   const int a = m, b = 2;
-  double ch = cos(0.5 * theta), sh = sin(0.5 * theta);
-  double root = sqrt(fact_d(l + a) * fact_d(l - a) * fact_d(l + b) * fact_d(l - b));
+  // sqrt((l+a)!(l-a)!(l+b)!(l-b)!) = 1/sqrt(product of inverse factorials)
+  double root = rsqrt(c_invfact[l + a] * c_invfact[l - a] * c_invfact[l + b] * c_invfact[l - b]);
   double sum = 0.0;
   for (int k = 0; k <= 2 * l; k++) {
     int f0 = l + b - k, f1 = k, f2 = a - b + k, f3 = l - a - k;
     if (f0 < 0 || f2 < 0 || f3 < 0) continue;
-    double term = root / (fact_d(f0) * fact_d(f1) * fact_d(f2) * fact_d(f3));
+    double term = root * (c_invfact[f0] * c_invfact[f1]) * (c_invfact[f2] * c_invfact[f3]);
     term *= ipow(ch, 2 * l + b - a - 2 * k) * ipow(sh, a - b + 2 * k);
     sum += ((a - b + k) & 1) ? -term : term;
   }
@@ -96,9 +108,11 @@ __global__ void k_modes(int n_wf, const WfInfo* wf, DevInputs in, int conj, Mode
     atomicOr(status, ST_MODE);
   } else {
     // c+ = alpha e^{i m phi}, cx = i beta e^{i m phi} (the e^{i m phi} goes into the phase)
-    double S = swsh_theta(l, m, th);
+    double sh, ch;
+    sincos(0.5 * th, &sh, &ch);
+    double S = swsh_theta(l, m, ch, sh);
     if (conj) {
-      double Sp = swsh_theta(l, -m, th) * ((l & 1) ? -1.0 : 1.0);
+      double Sp = swsh_theta(l, -m, ch, sh) * ((l & 1) ? -1.0 : 1.0);
       M.alpha = 0.5 * (S + Sp);
       M.beta = 0.5 * (S - Sp);
     } else {
@@ -131,59 +145,79 @@ __device__ __forceinline__ void tri_row(const double* t, int K, int i, double& a
   } else { a = h0; b = 2.0 * (h0 + h1); c = h1; }
 }
 
-__global__ void k_spline_factor(int n_wf, const WfInfo* wf, const double* tall, double* cp, double* im) {
+// reciprocal of a normal double from an FP32 seed and two FP64 Newton steps
+__device__ __forceinline__ double rcp_d(double x) {
+  const float xf = d2f_bits(x);
+  const float yf = __fdividef(1.f, xf);
+  if (!(fabsf(yf) > 0.f && fabsf(yf) < 3.0e38f)) return 1.0 / x;
+  double y = f2d_bits(yf);
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
+// per waveform: the forward-sweep factors {c'_i, 1/m_i, s_i/m_i, a_i/m_i} of the
+// reduced system, and 1/h_k (one thread per waveform: the sweep is sequential)
+__global__ void k_spline_factor(int n_wf, const WfInfo* wf, const double* tall, dbl4* fac, double* ih) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= n_wf) return;
   const WfInfo W = wf[w];
   const double* t = tall + W.ko;
   int K = (int)W.K;
+  for (int k = 0; k + 1 < K; k++) ih[W.ko + k] = rcp_d(t[k + 1] - t[k]);
+  ih[W.ko + K - 1] = 0.0;
   double cprev = 0.0;
+  fac[W.ko] = mk_dbl4(0.0, 0.0, 0.0, 0.0);
+  fac[W.ko + K - 1] = mk_dbl4(0.0, 0.0, 0.0, 0.0);
   for (int i = 1; i <= K - 2; i++) {
-    double a, b, c, s;
-    tri_row(t, K, i, a, b, c, s);
-    if (i == 1 && K == 4) { /* row 1 is also followed by the last row: keep c */ }
-    double mm = b - a * cprev;
-    double inv = 1.0 / mm;
+    double a, b, c, sc;
+    tri_row(t, K, i, a, b, c, sc);
+    double inv = rcp_d(b - a * cprev);
     double cc = (i == K - 2) ? 0.0 : c * inv;
-    cp[W.ko + i] = cc;
-    im[W.ko + i] = inv;
+    fac[W.ko + i] = mk_dbl4(cc, inv, sc * inv, a * inv);
     cprev = cc;
   }
 }
 
 // one thread per series; y has stride ys, M is written with stride ms
-__device__ void spline_solve(const double* t, int K, const double* y, long long ys, double* M, long long ms,
-                             const double* cp, const double* im) {
+__device__ void spline_solve(int K, const double* y, long long ys, double* M, long long ms, const dbl4* fac,
+                             const double* ih) {
   double rp = 0.0;
+  double y0 = y[0], y1 = y[ys];
+  double d0 = (y1 - y0) * ih[0];
   for (int i = 1; i <= K - 2; i++) {
-    double h0 = t[i] - t[i - 1], h1 = t[i + 1] - t[i];
-    double r = 6.0 * ((y[(i + 1) * ys] - y[i * ys]) / h1 - (y[i * ys] - y[(i - 1) * ys]) / h0);
-    double a, b, c, s;
-    tri_row(t, K, i, a, b, c, s);
-    rp = (r * s - a * rp) * im[i];
-    M[i * ms] = rp;      // forward-swept right-hand side, overwritten below
+    const double y2 = y[(i + 1) * ys];
+    const double d1 = (y2 - y1) * ih[i];
+    const double r = 6.0 * (d1 - d0);
+    const dbl4 F = fac[i];
+    rp = fma(r, F.z, -rp * F.w);        // (r s - a rp)/m
+    M[i * ms] = rp;                     // forward-swept right-hand side, overwritten below
+    d0 = d1;
+    y1 = y2;
   }
   double next = M[(K - 2) * ms];
   for (int i = K - 3; i >= 1; i--) {
-    double v = M[i * ms] - cp[i] * next;
+    double v = M[i * ms] - fac[i].x * next;
     M[i * ms] = v;
     next = v;
   }
-  double h0 = t[1] - t[0], h1 = t[2] - t[1];
-  M[0] = ((h0 + h1) * M[ms] - h0 * M[2 * ms]) / h1;
-  double ha = t[K - 2] - t[K - 3], hb = t[K - 1] - t[K - 2];
-  M[(K - 1) * ms] = ((ha + hb) * M[(K - 2) * ms] - hb * M[(K - 3) * ms]) / ha;
+  // M_0 = ((h0+h1) M_1 - h0 M_2)/h1 ;  M_{K-1} = ((ha+hb) M_{K-2} - hb M_{K-3})/ha
+  const double r01 = ih[1] / ih[0];                      // h0 / h1
+  M[0] = (1.0 + r01) * M[ms] - r01 * M[2 * ms];
+  const double rba = ih[K - 3] / ih[K - 2];              // hb / ha
+  M[(K - 1) * ms] = (1.0 + rba) * M[(K - 2) * ms] - rba * M[(K - 3) * ms];
 }
 
 __global__ void k_spline_solve(int n_wf, const WfInfo* wf, const ModeInfo* modes, long long nm_total, DevInputs in,
-                               const double* cp, const double* im, double* fundM, long long K_total, double* ampM) {
+                               const dbl4* fac, const double* ih, double* fundM, long long K_total, double* ampM) {
   long long sid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long nfund = 4LL * n_wf;
   if (sid < nfund) {
     int w = (int)(sid >> 2), which = (int)(sid & 3);
     const WfInfo W = wf[w];
     const double* y = which == 0 ? in.phi_phi : which == 1 ? in.phi_r : which == 2 ? in.omega_phi : in.omega_r;
-    spline_solve(in.t + W.ko, (int)W.K, y + W.ko, 1, fundM + which * K_total + W.ko, 1, cp + W.ko, im + W.ko);
+    spline_solve((int)W.K, y + W.ko, 1, fundM + which * K_total + W.ko, 1, fac + W.ko, ih + W.ko);
     return;
   }
   sid -= nfund;
@@ -192,8 +226,7 @@ __global__ void k_spline_solve(int n_wf, const WfInfo* wf, const ModeInfo* modes
   int part = (int)(sid & 1);
   const ModeInfo Mi = modes[j];
   const WfInfo W = wf[Mi.wf];
-  spline_solve(in.t + W.ko, (int)W.K, in.amp + 2 * Mi.key_base + part, 2, ampM + 2 * Mi.key_base + part, 2,
-               cp + W.ko, im + W.ko);
+  spline_solve((int)W.K, in.amp + 2 * Mi.key_base + part, 2, ampM + 2 * Mi.key_base + part, 2, fac + W.ko, ih + W.ko);
 }
 
 // ------------------------------------------------ per (mode, segment) records
@@ -290,7 +323,27 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
   // turnovers: roots of dF/du = b + 2c u + 3d u^2 in (0, 1)
   SegCrit X;
   X.n = 0; X.u[0] = X.u[1] = 0.0; X.F[0] = X.F[1] = 0.0; X.pad[0] = X.pad[1] = X.pad[2] = 0;
+  // FP32 pre-check: dF/du = b + c2 u + d3 u^2 keeps one sign on [0, 1] when its end
+  // values agree in sign and its vertex is outside [0, 1] or has that sign too
+  // (margins of 1e-3 relative cover the FP32 rounding); otherwise solve exactly
+  bool maybe = true;
   {
+    const float fb = (float)C.b, fc2 = (float)C.c2, fd3 = (float)C.d3;
+    const float D0 = fb, D1 = fb + fc2 + fd3;
+    const float scl = fabsf(fb) + fabsf(fc2) + fabsf(fd3);
+    if (D0 * D1 > 1e-3f * scl * scl) {
+      if (fd3 == 0.f) maybe = false;
+      else {
+        const float uv = -fc2 / (2.f * fd3);
+        if (uv < -1e-3f || uv > 1.001f) maybe = false;
+        else {
+          const float Dv = fb + uv * (fc2 + fd3 * uv);
+          if (Dv * D0 > 1e-3f * scl * scl) maybe = false;
+        }
+      }
+    }
+  }
+  if (maybe) {
     double qa = C.d3, qb = C.c2, qc = C.b;
     double rt[2]; int nr = 0;
     if (qa == 0.0) {
@@ -474,25 +527,45 @@ __global__ void k_wf_runs(int n_wf, WfInfo* wf, const int* run_off, long long ru
   wf[w].nruns = b - a;
 }
 
-// lower_bound / upper_bound on the ascending bins of one waveform
-__device__ __forceinline__ long long lbound(const double* f, long long n, double x) {
-  long long a = 0, b = n;
-  while (a < b) { long long c = (a + b) >> 1; if (f[c] < x) a = c + 1; else b = c; }
-  return a;
-}
-__device__ __forceinline__ long long ubound(const double* f, long long n, double x) {
-  long long a = 0, b = n;
-  while (a < b) { long long c = (a + b) >> 1; if (f[c] <= x) a = c + 1; else b = c; }
-  return a;
-}
-
 // Output-bin ranges of each run.  Increasing runs own [F_start, F_end),
 // decreasing runs own (F_end, F_start]; the negative-frequency part serves
 // bins f with -f in that range (they enter through conj H(-f)).
+// One warp per run: four groups of 8 lanes find the four bounds at once, each
+// with an 8-way search (8 probes per step, integer keys of the doubles).
+// bound of group g: first i in [0, n) with key(f[i]) >= x (strict: > x)
+__device__ __forceinline__ long long group_bound(const long long* fk, long long n, long long x, bool strict, int j,
+                                                 unsigned gmask) {
+  long long lo = 0, hi = n;   // answer in [lo, hi]
+  while (hi - lo > 8) {
+    const long long span = hi - lo;
+    const long long p = lo + (span * (j + 1)) / 9;
+    const long long v = fk[p];
+    const bool pr = strict ? (v > x) : (v >= x);
+    const unsigned bal = __ballot_sync(gmask, pr) & gmask;
+    // probes of this group sit at bit offsets (lane & ~7) .. +7
+    const unsigned mine = bal >> (threadIdx.x & 24);
+    const int first = mine ? __ffs(mine) - 1 : 8;
+    const long long pl = first > 0 ? lo + (span * first) / 9 : lo - 1;        // probe before the first true
+    const long long ph = first < 8 ? lo + (span * (first + 1)) / 9 : hi;       // first true probe
+    lo = (first > 0) ? pl + 1 : lo;
+    hi = ph;
+  }
+  // at most 8 candidates left: lo .. hi-1, answer = first true or hi
+  const long long p = lo + j;
+  bool pr = false;
+  if (p < hi) {
+    const long long v = fk[p];
+    pr = strict ? (v > x) : (v >= x);
+  }
+  const unsigned bal = (__ballot_sync(gmask, pr) & gmask) >> (threadIdx.x & 24);
+  return bal ? lo + (__ffs(bal) - 1) : hi;
+}
+
 __global__ void k_run_bins(const WfInfo* wf, const ModeInfo* modes, long long nm_total, const int* run_total,
                            const Run* runs, const double2* runF, long long run_cap, const double* freqs, RunBins* rb,
                            unsigned long long* counters, int* status) {
-  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, grp = lane >> 3, j = lane & 7;
   long long nr = *run_total;
   if (nr > run_cap) nr = run_cap;
   if (r >= nr) return;
@@ -501,35 +574,46 @@ __global__ void k_run_bins(const WfInfo* wf, const ModeInfo* modes, long long nm
   // a run whose fields were not all written (cannot happen when the count and
   // fill passes agree) is made empty, so that no later kernel indexes with it
   if (R.mode < 0 || R.mode >= nm_total) {
-    B.b0p = B.b1p = B.b0n = B.b1n = 0;
-    rb[r] = B;
-    atomicOr(status, ST_CAPACITY);
+    if (lane == 0) {
+      B.b0p = B.b1p = B.b0n = B.b1n = 0;
+      rb[r] = B;
+      atomicOr(status, ST_CAPACITY);
+    }
     return;
   }
   const WfInfo W = wf[modes[R.mode].wf];
   if (R.s0 < 0 || R.s1 < R.s0 || R.s1 >= W.K - 1 || R.dir == 0) {
-    B.b0p = B.b1p = B.b0n = B.b1n = (int)W.fo;
-    rb[r] = B;
-    atomicOr(status, ST_CAPACITY);
+    if (lane == 0) {
+      B.b0p = B.b1p = B.b0n = B.b1n = (int)W.fo;
+      rb[r] = B;
+      atomicOr(status, ST_CAPACITY);
+    }
     return;
   }
-  const double* f = freqs + W.fo;
-  double Fs = runF[r].x, Fe = runF[r].y;
-  long long b0p, b1p, b0n, b1n;
+  const long long* fk = reinterpret_cast<const long long*>(freqs) + W.fo;   // positive: bits are ordered keys
+  const double Fs = runF[r].x, Fe = runF[r].y;
+  // group 0..3: (b0p, b1p, b0n, b1n); lower bound = first f >= x, upper = first f > x
+  double x;
+  bool strict;
   if (R.dir > 0) {
-    b0p = lbound(f, W.nf, Fs); b1p = lbound(f, W.nf, Fe);
-    b0n = ubound(f, W.nf, -Fe); b1n = ubound(f, W.nf, -Fs);
+    x = grp == 0 ? Fs : grp == 1 ? Fe : grp == 2 ? -Fe : -Fs;
+    strict = grp >= 2;
   } else {
-    b0p = ubound(f, W.nf, Fe); b1p = ubound(f, W.nf, Fs);
-    b0n = lbound(f, W.nf, -Fs); b1n = lbound(f, W.nf, -Fe);
+    x = grp == 0 ? Fe : grp == 1 ? Fs : grp == 2 ? -Fs : -Fe;
+    strict = grp <= 1;
   }
-  if (b1p < b0p) b1p = b0p;
-  if (b1n < b0n) b1n = b0n;
-  B.b0p = (int)(W.fo + b0p); B.b1p = (int)(W.fo + b1p);
-  B.b0n = (int)(W.fo + b0n); B.b1n = (int)(W.fo + b1n);
-  rb[r] = B;
-  unsigned long long cnt = (unsigned long long)((b1p - b0p) + (b1n - b0n));
-  if (cnt) atomicAdd(&counters[1], cnt);
+  const unsigned gmask = 0xFFu << (grp * 8);
+  const long long v = group_bound(fk, W.nf, ordkey(x), strict, j, gmask);
+  const long long b0p = __shfl_sync(0xffffffffu, v, 0), b1p = __shfl_sync(0xffffffffu, v, 8);
+  const long long b0n = __shfl_sync(0xffffffffu, v, 16), b1n = __shfl_sync(0xffffffffu, v, 24);
+  if (lane == 0) {
+    const long long e1p = b1p < b0p ? b0p : b1p, e1n = b1n < b0n ? b0n : b1n;
+    B.b0p = (int)(W.fo + b0p); B.b1p = (int)(W.fo + e1p);
+    B.b0n = (int)(W.fo + b0n); B.b1n = (int)(W.fo + e1n);
+    rb[r] = B;
+    unsigned long long cnt = (unsigned long long)((e1p - b0p) + (e1n - b0n));
+    if (cnt) atomicAdd(&counters[1], cnt);
+  }
 }
 
 __global__ void k_table(double2* tab) {
@@ -549,15 +633,15 @@ void launch_scan(int* cnt, long long n, cudaStream_t st) { k_scan<<<1, 1024, 0, 
 void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st) {
   dim3 gk(8, cs.n_wf);
   k_validate_knots<<<gk, 256, 0, st>>>(s.wf, in, s.status);
-  dim3 gf(64, cs.n_wf);
+  dim3 gf(256, cs.n_wf);
   k_validate_freqs<<<gf, 256, 0, st>>>(s.wf, in, s.status);
   k_validate_amp<<<256, 256, 0, st>>>(2 * cs.amp_total, in.amp, s.status);
   k_modes<<<(unsigned)((cs.nm_total + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes, cs.nm_total,
                                                                   s.status);
-  k_spline_factor<<<(cs.n_wf + 63) / 64, 64, 0, st>>>(cs.n_wf, s.wf, in.t, s.spl_cp, s.spl_im);
+  k_spline_factor<<<(cs.n_wf + 63) / 64, 64, 0, st>>>(cs.n_wf, s.wf, in.t, s.spl_fac, s.spl_ih);
   long long nser = 4LL * cs.n_wf + 2 * cs.nm_total;
-  k_spline_solve<<<(unsigned)((nser + 127) / 128), 128, 0, st>>>(cs.n_wf, s.wf, s.modes, cs.nm_total, in, s.spl_cp,
-                                                                 s.spl_im, s.fundM, cs.K_total, s.ampM);
+  k_spline_solve<<<(unsigned)((nser + 127) / 128), 128, 0, st>>>(cs.n_wf, s.wf, s.modes, cs.nm_total, in, s.spl_fac,
+                                                                 s.spl_ih, s.fundM, cs.K_total, s.ampM);
   k_seg_prep<<<(unsigned)((cs.seg_total + 127) / 128), 128, 0, st>>>(
       cs.n_wf, s.wf, s.modes, in, s.fundM, cs.K_total, s.ampM, cs.seg_total, s.core,
       cs.precision == 0 ? s.amp64 : nullptr, cs.precision == 1 ? s.amp32 : nullptr, s.crit, s.keyF);
@@ -569,7 +653,7 @@ void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, 
   cudaMemsetAsync(s.runs, 0xFF, sizeof(Run) * (size_t)s.run_cap, st);
   k_runs<true><<<wblocks, 256, 0, st>>>(s.wf, s.modes, cs.nm_total, s.core, s.crit, s.keyF, s.run_cnt, s.runs,
                                         s.runF, s.run_cap, nullptr, s.status);
-  k_run_bins<<<(unsigned)((s.run_cap + 255) / 256), 256, 0, st>>>(s.wf, s.modes, cs.nm_total, s.run_cnt + cs.nm_total,
+  k_run_bins<<<(unsigned)((s.run_cap * 32 + 255) / 256), 256, 0, st>>>(s.wf, s.modes, cs.nm_total, s.run_cnt + cs.nm_total,
                                                                   s.runs, s.runF, s.run_cap, in.freqs, s.rbins,
                                                                   s.counters, s.status);
 }

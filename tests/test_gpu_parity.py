@@ -164,3 +164,41 @@ def test_mixed_precision_paper_sampled(oracle):
     rp, rc = oracle.sum_modes(w, freqs=w.freqs[sel])
     for g, r in zip((hp[sel], hc[sel]), (rp, rc)):
         assert rel_l2(g, r) <= TOL32
+
+
+def test_graph_replay_equals_direct_call():
+    from tests.gpu_util import plan_for
+    wfs = [synth.small_config(0, n_bins=3001), synth.paper_config(3, n_modes=150, T_years=0.5, grid="sparse", n_sparse=2000)]
+    plan = plan_for(wfs)
+    b = plan.upload(synth.concat(wfs))
+    direct = [x.clone() for x in plan.sum_modes(b)]
+    out = (torch.zeros_like(direct[0]), torch.zeros_like(direct[1]))
+    g = plan.capture(b, out)
+    for _ in range(2):
+        out[0].zero_()
+        out[1].zero_()
+        g.replay()
+        plan.sync()
+        assert torch.equal(out[0], direct[0]) and torch.equal(out[1], direct[1])
+    # the graph reads the input buffers at every replay
+    b["amp"].mul_(2.0)
+    g.replay()
+    plan.sync()
+    assert torch.allclose(out[0], 2 * direct[0], rtol=1e-13, atol=0)
+    g.close()
+    plan.close()
+
+
+def test_autotuner(tmp_path, monkeypatch):
+    from paper_2307_12585_gb300 import autotune
+    from tests.gpu_util import plan_for
+    monkeypatch.setenv("EMRI_FD_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    w = synth.small_config(0, n_bins=20000)
+    plan = plan_for([w])
+    b = plan.upload(synth.concat([w]))
+    out = plan.sum_modes(b)
+    r1 = autotune.tune(plan, b, out)
+    assert r1["tile_bins"] in (32, 64, 128) and not r1["cached"]
+    r2 = autotune.tune(plan, b, out)
+    assert r2["cached"] and r2["tile_bins"] == r1["tile_bins"]
+    plan.close()
