@@ -73,7 +73,7 @@ typedef enum {
   EMRI_FD_ERR_TIMEOUT = 9     /* a bounded device wait ran out */
 } emri_fd_status;
 
-enum { EMRI_FD_FP64 = 0, EMRI_FD_MIXED = 1 };
+enum { EMRI_FD_FP64 = 0, EMRI_FD_MIXED = 1, EMRI_FD_FP64X = 2 };
 
 #define EMRI_FD_MAX_L 20
 
@@ -81,7 +81,10 @@ typedef struct {
   int precision;            /* EMRI_FD_FP64: FP64 throughout, complex128 outputs.
                                EMRI_FD_MIXED: FP64 root and phase, FP32 amplitude,
                                weight, sincos and compensated accumulation;
-                               complex64 outputs. */
+                               complex64 outputs.
+                               EMRI_FD_FP64X: the FP64 form's accuracy from FP32-pair
+                               ("double-float", ~48-bit) and integer arithmetic, no
+                               FP64 instruction per evaluation; complex128 outputs. */
   int conj_partners;        /* 0 or 1, see above */
   int max_waveforms;        /* 1 .. 65535 */
   int max_knots;            /* per waveform, >= 4 */
@@ -196,7 +199,7 @@ emri_fd_status emri_fd_profile(emri_fd_plan_t plan, int enable);
  * latency-critical code that cannot afford cudaMalloc/cudaFree (which may
  * synchronise the device), and plug-ins or callbacks that must not call the
  * allocator.  It calls no cudaMalloc, cudaFree or other allocating routine:
- * all scratch lives in one file-scope __device__ array of 6,510,592 bytes
+ * all scratch lives in one file-scope __device__ array of 6,538,240 bytes
  * (6.2 MiB), which every GPU that loads the library holds until the process
  * exits.
  *   Limits: n_knots in [4, EMRI_FD_NOALLOC_MAX_KNOTS], n_modes in

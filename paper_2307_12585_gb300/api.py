@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-EMRI_FD_FP64, EMRI_FD_MIXED = 0, 1
+EMRI_FD_FP64, EMRI_FD_MIXED, EMRI_FD_FP64X = 0, 1, 2
 STATUS = {0: "EMRI_FD_OK", 1: "EMRI_FD_ERR_ARG", 2: "EMRI_FD_ERR_KNOTS", 3: "EMRI_FD_ERR_FREQ",
           4: "EMRI_FD_ERR_MODE", 5: "EMRI_FD_ERR_NONFINITE", 6: "EMRI_FD_ERR_CAPACITY",
           7: "EMRI_FD_ERR_CUDA", 8: "EMRI_FD_ERR_OOM", 9: "EMRI_FD_ERR_TIMEOUT"}
@@ -204,7 +204,8 @@ class Plan:
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
-        self.precision = EMRI_FD_FP64 if precision in ("fp64", 0) else EMRI_FD_MIXED
+        self.precision = {"fp64": EMRI_FD_FP64, 0: EMRI_FD_FP64, "mixed": EMRI_FD_MIXED, 1: EMRI_FD_MIXED,
+                          "fp64x": EMRI_FD_FP64X, 2: EMRI_FD_FP64X}[precision]
         d = emri_fd_desc()
         d.precision = self.precision
         d.conj_partners = int(bool(conj_partners))
@@ -233,7 +234,7 @@ class Plan:
 
     @property
     def out_dtype(self):
-        return self.torch.complex128 if self.precision == EMRI_FD_FP64 else self.torch.complex64
+        return self.torch.complex64 if self.precision == EMRI_FD_MIXED else self.torch.complex128
 
     def upload(self, batch, non_blocking=False):
         """numpy batch -> dict of device tensors (offsets stay on the host)."""
@@ -273,7 +274,7 @@ class Plan:
         library stages inputs and outputs itself and synchronises before returning."""
         n_wf = len(b["knot_off"]) - 1
         nf = int(b["freq_off"][-1])
-        cdt = np.complex128 if self.precision == EMRI_FD_FP64 else np.complex64
+        cdt = np.complex64 if self.precision == EMRI_FD_MIXED else np.complex128
         if out is None:
             out = (np.empty(nf, cdt), np.empty(nf, cdt))
         ko, mo, fo = (np.ascontiguousarray(np.asarray(b[k], np.int64)) for k in ("knot_off", "mode_off", "freq_off"))

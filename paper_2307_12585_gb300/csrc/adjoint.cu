@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjParams P) {
         const double g = neg ? -P.freqs[b] : P.freqs[b];
         const double delta = g - C.A;
         float uf, Df;
-        const double u = solve_root(C, delta, ulo, uhi, R.dir, uf, Df);
+        const double u = solve_root<6>(C, delta, ulo, uhi, R.dir, uf, Df);
         const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
         const long long Dbits = __double_as_longlong(Dd);
         if ((Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0) continue;

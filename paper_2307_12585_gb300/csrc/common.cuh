@@ -49,6 +49,7 @@ struct ModeInfo {
   long long seg_base;      // first record of this mode
   long long key_base;      // first knot key / amplitude knot of this mode
   double alpha, beta;      // h+ += alpha Z, hx += i beta Z (positive branch), see spa.cu
+  float af[2], bf[2];      // alpha, beta as FP32 pairs (hi, lo)
 };
 
 struct __align__(16) SegCore {
@@ -74,9 +75,20 @@ struct __align__(16) SegAmp64 { double re[4], im[4]; };   // prefactor sqrt(h) A
 struct __align__(16) SegAmp32 { float re[4], im[4]; };
 struct __align__(16) SegCrit { double u[2]; double F[2]; int n; int pad[3]; };  // 48 B
 
+// FP64X records: the SegCore polynomials as FP32 pairs (hi, lo), and the
+// amplitude cubic times sqrt(h) (no prefactor, applied at the store)
+struct __align__(16) SegFF {
+  float A[2], b[2], c[2], d[2];      // frequency cubic [Hz]
+  float c2[2], d3[2];                // 2c, 3d
+  float Q1[2], P2[2], P3[2], h[2];   // in-segment phase [turns], segment length [s]
+  float are[4][2], aim[4][2];        // sqrt(h) A(u)
+};
+static_assert(sizeof(SegFF) == 144, "SegFF layout");
+
 struct __align__(16) Run {
   int mode, dir, s0, s1;   // global mode index; +1/-1; first/last segment (local)
   double u0, u1;           // start u in s0, end u in s1
+  float u0f[2], u1f[2];    // the same as FP32 pairs (hi, lo)
 };
 struct __align__(16) RunBins { int b0p, b1p, b0n, b1n; };  // global output bins, [b0, b1)
 
@@ -129,6 +141,12 @@ __device__ __forceinline__ unsigned long long q64_of(double x) {
   return (u >> 63) ? (0ull - r) : r;
 }
 
+// exact float of a small integer (|v| < 2^22) without a conversion instruction:
+// 1.5 * 2^23 + v has v in its low mantissa bits
+__device__ __forceinline__ float small_int_to_float(int v) {
+  return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f);
+}
+
 // frac(a * b) in Q0.64 turns, from the exact 106-bit product of the mantissas
 __device__ __forceinline__ unsigned long long q64_mul(double a, double b) {
   unsigned long long ua = (unsigned long long)__double_as_longlong(a);
@@ -176,6 +194,7 @@ struct DevScratch {
   SegCore* core;
   SegAmp64* amp64;
   SegAmp32* amp32;
+  SegFF* segff;                   // FP64X plans
   SegCrit* crit;
   long long* keyF;                // [sum N_m K]
   int* run_cnt;                   // [sum N_m + 1], exclusive-scanned in place
@@ -184,6 +203,7 @@ struct DevScratch {
   RunBins* rbins;
   long long run_cap;
   double2* tab;                   // [kTabN] e^{2 pi i k / kTabN}
+  float4* tabf;                   // [kTabN] the same as FP32 pairs (cos hi, cos lo, sin hi, sin lo), FP64X plans
   // likelihood / adjoint scratch (plans created with likelihood = 1)
   double* hbuf;                   // [2][sum N_f] complex128: h+ then hx
   double* Gbuf;                   // [sum N_f][4] 4 df (d - h)/S, both channels
@@ -220,6 +240,7 @@ constexpr int kAdjointKernels = 8; // kernels launched by launch_adjoint
 void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st);
 void launch_spa(const CallShape& cs, const DevInputs& in, const DevScratch& s, int num_sms, cudaStream_t st);
 void launch_table(double2* tab, cudaStream_t st);
+void launch_table_ff(const double2* tab, float4* tabf, cudaStream_t st);
 void launch_scan(int* cnt, long long n, cudaStream_t st);
 void launch_loglike(const CallShape& cs, const LikeInputs& li, const DevScratch& s, cudaStream_t st);
 void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& li, const DevScratch& s, int num_sms,

@@ -106,7 +106,7 @@ void emri_fd_plan_destroy(emri_fd_plan_t p) {
 emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* stream) {
   if (!out || !d) return EMRI_FD_ERR_ARG;
   *out = nullptr;
-  if ((d->precision != EMRI_FD_FP64 && d->precision != EMRI_FD_MIXED) || (d->conj_partners != 0 && d->conj_partners != 1) ||
+  if ((d->precision != EMRI_FD_FP64 && d->precision != EMRI_FD_MIXED && d->precision != EMRI_FD_FP64X) || (d->conj_partners != 0 && d->conj_partners != 1) ||
       d->max_waveforms < 1 || d->max_waveforms > 65535 || d->max_knots < 4 || d->max_modes_total < 1 || d->max_bins_total < 1 ||
       d->max_bins_total > 2000000000LL || d->max_knots_total < 0 ||
       !(d->tile_bins == 0 || d->tile_bins == 32 || d->tile_bins == 64 || d->tile_bins == 128))
@@ -139,7 +139,9 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
   AL(s.fundM, 4 * p->cap_K);
   AL(s.ampM, 2 * p->cap_amp);
   AL(s.core, p->cap_seg);
-  if (d->precision == EMRI_FD_FP64) { AL(s.amp64, p->cap_seg); } else { AL(s.amp32, p->cap_seg); }
+  if (d->precision == EMRI_FD_FP64) { AL(s.amp64, p->cap_seg); }
+  else if (d->precision == EMRI_FD_MIXED) { AL(s.amp32, p->cap_seg); }
+  else { AL(s.segff, p->cap_seg); AL(s.tabf, kTabN); }
   AL(s.crit, p->cap_seg);
   AL(s.keyF, p->cap_amp);
   AL(s.run_cnt, p->cap_nm + 1);
@@ -172,6 +174,7 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
     cudaMemsetAsync(s.status, 0, sizeof(int), p->stream);
     cudaMemsetAsync(s.counters, 0, 8 * sizeof(unsigned long long), p->stream);
     launch_table(s.tab, p->stream);
+    if (s.tabf) launch_table_ff(s.tab, s.tabf, p->stream);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(p->stream) != cudaSuccess) st = EMRI_FD_ERR_CUDA;
   }
   if (st != EMRI_FD_OK) { emri_fd_plan_destroy(p); return st; }
@@ -331,7 +334,7 @@ emri_fd_status emri_fd_sum_modes(emri_fd_plan_t p, int n_wf, const long long* kn
                                    m, n, amp, theta, phi, prefactor, freqs, cs, in);
   if (st != EMRI_FD_OK) return st;
   if (cs.nf_total > 0 && (!h_plus || !h_cross)) return EMRI_FD_ERR_ARG;
-  const size_t ob = (p->desc.precision == EMRI_FD_FP64 ? 16 : 8) * (size_t)cs.nf_total;
+  const size_t ob = (p->desc.precision == EMRI_FD_MIXED ? 8 : 16) * (size_t)cs.nf_total;
   bool hp_host = false, hc_host = false;
   if ((st = stage_out(p, 13, h_plus, ob, &in.h_plus, &hp_host)) != EMRI_FD_OK) return st;
   if ((st = stage_out(p, 14, h_cross, ob, &in.h_cross, &hc_host)) != EMRI_FD_OK) return st;
@@ -532,7 +535,7 @@ emri_fd_status emri_fd_capture(emri_fd_plan_t p, int n_wf, const long long* knot
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    run_forward(p, cs, in, (p->desc.precision == EMRI_FD_FP64 ? 16 : 8) * (size_t)cs.nf_total);
+    run_forward(p, cs, in, (p->desc.precision == EMRI_FD_MIXED ? 8 : 16) * (size_t)cs.nf_total);
     e = cudaStreamEndCapture(cap, &g);
   }
   p->s.wf = saved;

@@ -49,7 +49,7 @@ constexpr size_t kOffRunF = kOffRuns + al256(kNaRunCap * sizeof(Run));
 constexpr size_t kOffRbins = kOffRunF + al256(kNaRunCap * sizeof(double2));
 constexpr size_t kOffTab = kOffRbins + al256(kNaRunCap * sizeof(RunBins));
 constexpr size_t kNaBytes = kOffTab + al256(kTabN * sizeof(double2));
-static_assert(kNaBytes == 6510592, "the size stated in include/emri_fd.h");
+static_assert(kNaBytes == 6538240, "the size stated in include/emri_fd.h");
 
 // The scratch.  In host code this name is only a stand-in for the device
 // symbol; its device address comes from cudaGetSymbolAddress below.

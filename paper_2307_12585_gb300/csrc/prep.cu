@@ -8,6 +8,7 @@
 // by the mode numbers; turnovers where dF/dt = 0, at most one per segment in
 // practice; the segment of each frequency is determined before the summation).
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace emrifd {
 
@@ -119,6 +120,10 @@ __global__ void k_modes(int n_wf, const WfInfo* wf, DevInputs in, int conj, Mode
       M.alpha = 0.5 * S;
       M.beta = 0.5 * S;
     }
+  }
+  {
+    const ff a = ff_from_double(M.alpha), b = ff_from_double(M.beta);
+    M.af[0] = a.hi; M.af[1] = a.lo; M.bf[0] = b.hi; M.bf[1] = b.lo;
   }
   modes[j] = M;
 }
@@ -257,9 +262,15 @@ __device__ __forceinline__ void ucoef(double y0, double y1, double M0, double M1
   c[3] = h2 * (M1 - M0) * (1.0 / 6.0);
 }
 
+__device__ __forceinline__ void put_ff(float* dst, double x) {
+  const ff v = ff_from_double(x);
+  dst[0] = v.hi;
+  dst[1] = v.lo;
+}
+
 __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, DevInputs in, const double* fundM,
                            long long K_total, const double* ampM, long long seg_total, SegCore* core,
-                           SegAmp64* amp64, SegAmp32* amp32, SegCrit* crit, long long* keyF) {
+                           SegAmp64* amp64, SegAmp32* amp32, SegFF* segff, SegCrit* crit, long long* keyF) {
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= seg_total) return;
   int lo = 0, hi = n_wf - 1;
@@ -318,6 +329,15 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
     SegAmp32 A;
     for (int q = 0; q < 4; q++) { A.re[q] = (float)(sc * cre[q]); A.im[q] = (float)(sc * cim[q]); }
     amp32[r] = A;
+  }
+  if (segff) {
+    SegFF X;
+    put_ff(X.A, C.A); put_ff(X.b, C.b); put_ff(X.c, C.c); put_ff(X.d, C.d);
+    put_ff(X.c2, C.c2); put_ff(X.d3, C.d3);
+    put_ff(X.Q1, C.Q1); put_ff(X.P2, C.P2); put_ff(X.P3, C.P3); put_ff(X.h, h);
+    const double sh = sqrt(h);
+    for (int q = 0; q < 4; q++) { put_ff(X.are[q], sh * cre[q]); put_ff(X.aim[q], sh * cim[q]); }
+    segff[r] = X;
   }
 
   // turnovers: roots of dF/du = b + 2c u + 3d u^2 in (0, 1)
@@ -453,6 +473,9 @@ __global__ void k_runs(const WfInfo* wf, const ModeInfo* modes, long long nm_tot
             runs[rid].dir = d;
             runs[rid].s0 = s;
             runs[rid].u0 = P.ua[i];
+            const ff uu = ff_from_double(P.ua[i]);
+            runs[rid].u0f[0] = uu.hi;
+            runs[rid].u0f[1] = uu.lo;
             runF[rid].x = P.Fa[i];
           }
           idx++;
@@ -479,6 +502,9 @@ __global__ void k_runs(const WfInfo* wf, const ModeInfo* modes, long long nm_tot
           if (rid < run_cap) {
             runs[rid].s1 = s;
             runs[rid].u1 = P.ub[i];
+            const ff uu = ff_from_double(P.ub[i]);
+            runs[rid].u1f[0] = uu.hi;
+            runs[rid].u1f[1] = uu.lo;
             runF[rid].y = P.Fb[i];
           }
         }
@@ -628,6 +654,19 @@ __global__ void k_table(double2* tab) {
 
 void launch_table(double2* tab, cudaStream_t st) { k_table<<<(kTabN + 255) / 256, 256, 0, st>>>(tab); }
 
+namespace {
+__global__ void k_table_ff(const double2* tab, float4* tabf) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kTabN) return;
+  const ff c = ff_from_double(tab[k].x), s = ff_from_double(tab[k].y);
+  tabf[k] = make_float4(c.hi, c.lo, s.hi, s.lo);
+}
+}  // namespace
+
+void launch_table_ff(const double2* tab, float4* tabf, cudaStream_t st) {
+  k_table_ff<<<(kTabN + 255) / 256, 256, 0, st>>>(tab, tabf);
+}
+
 void launch_scan(int* cnt, long long n, cudaStream_t st) { k_scan<<<1, 1024, 0, st>>>(cnt, n); }
 
 void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st) {
@@ -644,7 +683,8 @@ void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, 
                                                                  s.spl_ih, s.fundM, cs.K_total, s.ampM);
   k_seg_prep<<<(unsigned)((cs.seg_total + 127) / 128), 128, 0, st>>>(
       cs.n_wf, s.wf, s.modes, in, s.fundM, cs.K_total, s.ampM, cs.seg_total, s.core,
-      cs.precision == 0 ? s.amp64 : nullptr, cs.precision == 1 ? s.amp32 : nullptr, s.crit, s.keyF);
+      cs.precision == 0 ? s.amp64 : nullptr, cs.precision == 1 ? s.amp32 : nullptr,
+      cs.precision == 2 ? s.segff : nullptr, s.crit, s.keyF);
   unsigned wblocks = (unsigned)((cs.nm_total * 32 + 255) / 256);
   k_runs<false><<<wblocks, 256, 0, st>>>(s.wf, s.modes, cs.nm_total, s.core, s.crit, s.keyF, nullptr, nullptr,
                                          nullptr, s.run_cap, s.run_cnt, s.status);

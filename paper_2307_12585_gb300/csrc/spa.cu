@@ -21,6 +21,7 @@
 // the tile (BPL per lane) and the 8 warp partials are summed in warp order,
 // so every bin's sum has a fixed order (no atomics on the outputs).
 #include "spa_math.cuh"
+#include "ff.cuh"
 
 namespace emrifd {
 namespace {
@@ -32,6 +33,7 @@ struct SpaParams {
   const SegCore* core;
   const SegAmp64* amp64;
   const SegAmp32* amp32;
+  const SegFF* segff;
   const long long* keyF;
   const Run* runs;
   const RunBins* rb;
@@ -39,6 +41,8 @@ struct SpaParams {
   void* hp;
   void* hc;
   const double2* tab;
+  const float4* tabf;
+  const double* prefactor;
   unsigned long long* counters;
   const int* status;
   long long tiles_total;
@@ -47,14 +51,126 @@ struct SpaParams {
 template <int BPL, int PREC>
 struct Smem {
   double2 tab[PREC == 0 ? kTabN : 1];
+
   int list[kListCap];
   int wsum[kWarps + 1];
   long long tile;
   double red[kWarps][32 * BPL][4];
 };
 
+// FP64X per-(branch, bin) body: returns the four increments (h+ re, h+ im,
+// hx re, hx im) as FP32 pairs in v[0..7]; false if the root has Fdot == 0
+__device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, double f, ff fx, bool neg, ff ulo, ff uhi,
+                                           int dir, ff fa, ff fb, const float4* tabf, float* v) {
+  const ff Ax = ff_make(X.A[0], X.A[1]), bx = ff_make(X.b[0], X.b[1]), cx_ = ff_make(X.c[0], X.c[1]),
+           dx = ff_make(X.d[0], X.d[1]);
+  const ff gx = neg ? ff_neg(fx) : fx;
+  const ff dl = ff_sub(gx, Ax);
+  // a6: FP32 start, then Newton with the residual in FP32 pairs
+  float Df;
+  const float uf = root_f32<4>(C.bf, C.cf, C.df, dl.hi, ulo.hi, uhi.hi, dir, Df);
+  ff t = ff_add(ff_mul_f(dx, uf), cx_);
+  t = ff_add(ff_mul_f(t, uf), bx);
+  ff res = ff_sub(ff_mul_f(t, uf), dl);
+  const float rcf = __fdividef(1.f, Df);
+  float stepf = -res.hi * rcf;
+  ff u = two_sum(uf, stepf);
+  float stp = fabsf(stepf);
+  float kap = fabsf(__fdividef(C.cf + 3.f * C.df * uf, Df));
+  float err = stp * (kap * stp + 4.8e-7f);
+#pragma unroll 1
+  for (int it = 0; it < 4 && err > 1e-13f; it++) {
+    const float ufc = u.hi;
+    const float Dc = (3.f * C.df * ufc + 2.f * C.cf) * ufc + C.bf;
+    t = ff_add(ff_mul(dx, u), cx_);
+    t = ff_add(ff_mul(t, u), bx);
+    res = ff_sub(ff_mul(t, u), dl);
+    const float rc2 = __fdividef(1.f, Dc);
+    stepf = -res.hi * rc2;
+    u = ff_add_f(u, stepf);
+    stp = fabsf(stepf);
+    kap = fabsf(__fdividef(C.cf + 3.f * C.df * ufc, Dc));
+    err = stp * (kap * stp + 4.8e-7f);
+  }
+  if (ff_lt(u, ulo)) u = ulo;
+  else if (ff_lt(uhi, u)) u = uhi;
+  // a8: dF/du and 1/sqrt|dF/du| (rsqrtf seed, one Newton step in pairs)
+  const ff D = ff_add(ff_mul(ff_add(ff_mul(ff_make(X.d3[0], X.d3[1]), u), ff_make(X.c2[0], X.c2[1])), u), bx);
+  if (D.hi == 0.f) return false;
+  const bool pos = D.hi > 0.f;
+  const ff Da = pos ? D : ff_neg(D);
+  const float y0 = rsqrtf(Da.hi);
+  const ff ee = ff_mul_f(ff_mul_f(Da, y0), y0);
+  const ff wgt = ff_mul_f(ff_add_f(ff_mul_f(ee, -0.5f), 1.5f), y0);
+  // a7: phase, Q0.64 turns
+  const ff dh = ff_mul(dl, ff_make(X.h[0], X.h[1]));
+  const ff inner = ff_add(ff_mul(ff_add(ff_mul(ff_make(X.P3[0], X.P3[1]), u), ff_make(X.P2[0], X.P2[1])), u),
+                          ff_make(X.Q1[0], X.Q1[1]));
+  const ff inseg = ff_mul(ff_sub(dh, inner), u);
+  const unsigned long long ft = q64_mul(f, C.ts);           // f t_s; the branch sign is applied here
+  unsigned long long Th = (neg ? 0ull - ft : ft) - C.theta0 + q64_of_float(inseg.hi) + q64_of_float(inseg.lo);
+  Th += pos ? (0ull - (1ull << 61)) : (1ull << 61);
+  // e^{2 pi i Th/2^64}: table entry times (1 - x^2/2) + i (x - x^3/6), |x| <= pi/4096
+  const unsigned long long kq = (Th + (1ull << (63 - kTabBits))) >> (64 - kTabBits);
+  const long long rr = (long long)(Th - (kq << (64 - kTabBits))) >> 8;   // units of 2^-56 turn
+  const ff xt = two_sum(small_int_to_float((int)(rr >> 22)) * 5.820766091346741e-11f,        // 2^-34
+                        small_int_to_float((int)(rr & 0x3FFFFF)) * 1.3877787807814457e-17f);  // 2^-56
+  const ff xr = ff_mul(xt, ff_make(6.2831854820251465f, -1.7484555314695172e-07f));
+  const float qx = 0.5f * xr.hi * xr.hi;
+  const ff sx = ff_add_f(xr, -xr.hi * xr.hi * xr.hi * (1.f / 6.f));
+  const float4 T = __ldg(tabf + (kq & (kTabN - 1)));
+  const ff Tc = ff_make(T.x, T.y), Ts = ff_make(T.z, T.w);
+  const ff er = ff_add_f(ff_sub(Tc, ff_mul(Ts, sx)), -T.x * qx);
+  const ff ei = ff_add_f(ff_add(Ts, ff_mul(Tc, sx)), -T.z * qx);
+  // a9-a10
+  ff ar = ff_make(X.are[3][0], X.are[3][1]), ai = ff_make(X.aim[3][0], X.aim[3][1]);
+#pragma unroll
+  for (int k = 2; k >= 0; k--) {
+    ar = ff_add(ff_mul(ar, u), ff_make(X.are[k][0], X.are[k][1]));
+    ai = ff_add(ff_mul(ai, u), ff_make(X.aim[k][0], X.aim[k][1]));
+  }
+  ar = ff_mul(ar, wgt);
+  ai = ff_mul(ai, wgt);
+  const ff zr = ff_sub(ff_mul(ar, er), ff_mul(ai, ei));
+  const ff zi = ff_add(ff_mul(ar, ei), ff_mul(ai, er));
+  // a11: h+ += alpha Z (conj Z for F < 0), hx += i beta Z (-i beta conj Z)
+  const ff o0 = ff_mul(fa, zr), o1 = ff_mul(neg ? ff_neg(fa) : fa, zi);
+  const ff o2 = ff_mul(ff_neg(fb), zi), o3 = ff_mul(neg ? ff_neg(fb) : fb, zr);
+  v[0] = o0.hi; v[1] = o0.lo; v[2] = o1.hi; v[3] = o1.lo; v[4] = o2.hi; v[5] = o2.lo; v[6] = o3.hi; v[7] = o3.lo;
+  return true;
+}
+
+// mixed per-(branch, bin) body: FP64 root polish and in-segment phase, FP32
+// weight, sincos, amplitude and products; increments in v[0..3]
+__device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am, double f, bool neg, double ulo,
+                                           double uhi, int dir, float fa, float fb, float* v) {
+  const double g = neg ? -f : f;
+  const double delta = g - C.A;
+  float uf, Df;
+  const double u = solve_root<4>(C, delta, ulo, uhi, dir, uf, Df);
+  const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
+  const long long Dbits = __double_as_longlong(Dd);
+  if ((Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0) return false;
+  const unsigned long long Th = phase_q64(C, g, delta, u, Dbits >= 0);
+  const float wgt = rsqrtf(fabsf(Df));
+  // half-turns in [-1, 1) from the top 46 bits of Th, without conversion instructions
+  const long long ts_ = (long long)Th;
+  const float th = small_int_to_float((int)(ts_ >> 42)) * 4.76837158203125e-07f +              // 2^-21
+                   small_int_to_float((int)((ts_ >> 20) & 0x3FFFFF)) * 1.1368683772161603e-13f;  // 2^-43
+  float sn, cs;
+  sincospif(th, &sn, &cs);
+  float are = ((Am.re[3] * uf + Am.re[2]) * uf + Am.re[1]) * uf + Am.re[0];
+  float aim = ((Am.im[3] * uf + Am.im[2]) * uf + Am.im[1]) * uf + Am.im[0];
+  are *= wgt;
+  aim *= wgt;
+  const float zr = are * cs - aim * sn;
+  const float zi = are * sn + aim * cs;
+  v[0] = fa * zr; v[1] = (neg ? -fa : fa) * zi; v[2] = -fb * zi; v[3] = (neg ? -fb : fb) * zr;
+  return true;
+}
+
 template <int BPL, int PREC>
-__global__ void __launch_bounds__(kThreads, 2) k_spa(SpaParams P) {
+__global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : 4) k_spa(SpaParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<BPL, PREC>& S = *reinterpret_cast<Smem<BPL, PREC>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -62,6 +178,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_spa(SpaParams P) {
   if (*P.status != 0) return;
   if (PREC == 0)
     for (int i = tid; i < kTabN; i += kThreads) S.tab[i] = P.tab[i];
+
   __syncthreads();
 
   for (;;) {
@@ -86,6 +203,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_spa(SpaParams P) {
     }
     double acc[BPL][4];
     float accf[BPL][4], cmp[BPL][4];
+    ff fqf[BPL], accx[BPL][4];
+#pragma unroll
+    for (int q = 0; q < BPL; q++) {
+      fqf[q] = PREC == 2 ? ff_from_double(fq[q]) : ff_make(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < 4; c++) accx[q][c] = ff_make(0.f, 0.f);
+    }
 #pragma unroll
     for (int q = 0; q < BPL; q++)
 #pragma unroll
@@ -137,29 +261,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_spa(SpaParams P) {
         const RunBins B = P.rb[r];
         const int b0 = neg ? B.b0n : B.b0p, b1 = neg ? B.b1n : B.b1p;
         const ModeInfo M = P.modes[R.mode];
-        const double sa = M.alpha, sb = neg ? -M.beta : M.beta;   // h+ += alpha Z~, hx += i sb Z~
+        if constexpr (PREC == 0) {
+          const double sa = M.alpha, sb = neg ? -M.beta : M.beta;   // h+ += alpha Z~, hx += i sb Z~
 #pragma unroll
-        for (int q = 0; q < BPL; q++) {
-          const long long bin = bin0 + lane + 32 * q;
-          if (bin < b0 || bin >= b1) continue;
-          const double g = neg ? -fq[q] : fq[q];
-          const long long key = neg ? kn[q] : kp[q];
-          // a5: segment holding the root
-          const int s = run_segment(R, P.keyF, M.key_base, key);
-          const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
-          const SegCore C = P.core[M.seg_base + s];
-          // a6: root
-          const double delta = g - C.A;
-          float uf, Df;
-          const double u = solve_root(C, delta, ulo, uhi, R.dir, uf, Df);
-          // a8: dF/du and the weight sqrt(h)/sqrt|dF/du| (sqrt(h) is in the amplitude)
-          const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
-          const long long Dbits = __double_as_longlong(Dd);
-          if ((Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0) continue;   // Fdot == 0: no contribution
-          const bool pos_slope = Dbits >= 0;
-          // a7: phase in Q0.64 turns
-          const unsigned long long Th = phase_q64(C, g, delta, u, pos_slope);
-          if (PREC == 0) {
+          for (int q = 0; q < BPL; q++) {
+            const long long bin = bin0 + lane + 32 * q;
+            if (bin < b0 || bin >= b1) continue;
+            const double g = neg ? -fq[q] : fq[q];
+            const long long key = neg ? kn[q] : kp[q];
+            // a5: segment holding the root
+            const int s = run_segment(R, P.keyF, M.key_base, key);
+            const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
+            const SegCore C = P.core[M.seg_base + s];
+            // a6: root
+            const double delta = g - C.A;
+            float uf, Df;
+            const double u = solve_root<6>(C, delta, ulo, uhi, R.dir, uf, Df);
+            // a8: dF/du and the weight sqrt(h)/sqrt|dF/du| (sqrt(h) is in the amplitude)
+            const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
+            const long long Dbits = __double_as_longlong(Dd);
+            if ((Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0) continue;   // Fdot == 0: no contribution
+            const bool pos_slope = Dbits >= 0;
+            // a7: phase in Q0.64 turns
+            const unsigned long long Th = phase_q64(C, g, delta, u, pos_slope);
             const double wgt = rsqrt_abs(Dd);
             double er, ei;
             cis_q64(Th, S.tab, er, ei);
@@ -177,26 +301,50 @@ __global__ void __launch_bounds__(kThreads, 2) k_spa(SpaParams P) {
             acc[q][1] = fma(neg ? -sa : sa, zi, acc[q][1]);
             acc[q][2] = fma(-M.beta, zi, acc[q][2]);
             acc[q][3] = fma(sb, zr, acc[q][3]);
-          } else {
-            const float wgt = rsqrtf(fabsf(Df));
-            const float th = (float)(int)(Th >> 32) * 4.656612873077393e-10f;   // half-turns in [-1, 1)
-            float sn, cs;
-            sincospif(th, &sn, &cs);
-            const SegAmp32 Am = P.amp32[M.seg_base + s];
-            float are = ((Am.re[3] * uf + Am.re[2]) * uf + Am.re[1]) * uf + Am.re[0];
-            float aim = ((Am.im[3] * uf + Am.im[2]) * uf + Am.im[1]) * uf + Am.im[0];
-            are *= wgt;
-            aim *= wgt;
-            const float zr = are * cs - aim * sn;
-            const float zi = are * sn + aim * cs;
-            const float fa = (float)sa, fb = (float)M.beta;
-            float v[4] = {fa * zr, (neg ? -fa : fa) * zi, -fb * zi, (neg ? -fb : fb) * zr};
+          }
+        } else {
+          // FP64X and mixed: one copy of the per-bin body (rolled loop over the
+          // lane's bins); per-lane values and accumulators are selected with
+          // predicated moves so they stay in registers
+          const ff fa = ff_make(M.af[0], M.af[1]), fb = ff_make(M.bf[0], M.bf[1]);
+          const ff u0x = ff_make(R.u0f[0], R.u0f[1]), u1x = ff_make(R.u1f[0], R.u1f[1]);
+#pragma unroll 1
+          for (int q = 0; q < BPL; q++) {
+            const long long bin = bin0 + lane + 32 * q;
+            if (bin < b0 || bin >= b1) continue;
+            double fqq = fq[0];
+            long long kq_ = neg ? kn[0] : kp[0];
+            ff fx = fqf[0];
 #pragma unroll
-            for (int c = 0; c < 4; c++) {   // Kahan-compensated accumulation
-              float y = v[c] - cmp[q][c];
-              float t2 = accf[q][c] + y;
-              cmp[q][c] = (t2 - accf[q][c]) - y;
-              accf[q][c] = t2;
+            for (int qq = 1; qq < BPL; qq++)
+              if (qq == q) { fqq = fq[qq]; kq_ = neg ? kn[qq] : kp[qq]; fx = fqf[qq]; }
+            const int s = run_segment(R, P.keyF, M.key_base, kq_);
+            const SegCore C = P.core[M.seg_base + s];
+            float v[8];
+            bool ok;
+            if constexpr (PREC == 2) {
+              ok = body_fp64x(C, P.segff[M.seg_base + s], fqq, fx, neg, s == R.s0 ? u0x : ff_make(0.f, 0.f),
+                              s == R.s1 ? u1x : ff_make(1.f, 0.f), R.dir, fa, fb, P.tabf, v);
+            } else {
+              const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
+              ok = body_mixed(C, P.amp32[M.seg_base + s], fqq, neg, ulo, uhi, R.dir, M.af[0], M.bf[0], v);
+            }
+            if (!ok) continue;
+#pragma unroll
+            for (int qq = 0; qq < BPL; qq++) {
+              if (qq != q) continue;
+              if constexpr (PREC == 2) {
+#pragma unroll
+                for (int c = 0; c < 4; c++) accx[qq][c] = ff_add(accx[qq][c], ff_make(v[2 * c], v[2 * c + 1]));
+              } else {
+#pragma unroll
+                for (int c = 0; c < 4; c++) {   // Kahan-compensated accumulation
+                  float y = v[c] - cmp[qq][c];
+                  float t2 = accf[qq][c] + y;
+                  cmp[qq][c] = (t2 - accf[qq][c]) - y;
+                  accf[qq][c] = t2;
+                }
+              }
             }
           }
         }
@@ -210,7 +358,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_spa(SpaParams P) {
     for (int q = 0; q < BPL; q++)
 #pragma unroll
       for (int c = 0; c < 4; c++)
-        S.red[warp][lane + 32 * q][c] = PREC == 0 ? acc[q][c] : ((double)accf[q][c] - (double)cmp[q][c]);
+        S.red[warp][lane + 32 * q][c] = PREC == 0 ? acc[q][c]
+                                        : PREC == 2 ? ((double)accx[q][c].hi + (double)accx[q][c].lo)
+                                                    : ((double)accf[q][c] - (double)cmp[q][c]);
     __syncthreads();
     for (int i = tid; i < TB; i += kThreads) {
       const long long bin = bin0 + i;
@@ -222,6 +372,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_spa(SpaParams P) {
         if (PREC == 0) {
           reinterpret_cast<double2*>(P.hp)[bin] = make_double2(v[0], v[1]);
           reinterpret_cast<double2*>(P.hc)[bin] = make_double2(v[2], v[3]);
+        } else if (PREC == 2) {
+          const double pf = P.prefactor[lo];
+          reinterpret_cast<double2*>(P.hp)[bin] = make_double2(pf * v[0], pf * v[1]);
+          reinterpret_cast<double2*>(P.hc)[bin] = make_double2(pf * v[2], pf * v[3]);
         } else {
           reinterpret_cast<float2*>(P.hp)[bin] = make_float2((float)v[0], (float)v[1]);
           reinterpret_cast<float2*>(P.hc)[bin] = make_float2((float)v[2], (float)v[3]);
@@ -251,12 +405,17 @@ void launch_spa(const CallShape& cs, const DevInputs& in, const DevScratch& s, i
   p.wf = s.wf; p.n_wf = cs.n_wf; p.modes = s.modes; p.core = s.core; p.amp64 = s.amp64; p.amp32 = s.amp32;
   p.keyF = s.keyF; p.runs = s.runs; p.rb = s.rbins; p.freqs = in.freqs; p.hp = in.h_plus; p.hc = in.h_cross;
   p.tab = s.tab; p.counters = s.counters; p.status = s.status; p.tiles_total = cs.tiles_total;
+  p.segff = s.segff; p.tabf = s.tabf; p.prefactor = in.prefactor;
   cudaMemsetAsync(s.counters, 0, sizeof(unsigned long long), st);
   const int bpl = cs.tile_bins / 32;
   if (cs.precision == 0) {
     if (bpl == 1) launch_one<1, 0>(p, num_sms, st);
     else if (bpl == 4) launch_one<4, 0>(p, num_sms, st);
     else launch_one<2, 0>(p, num_sms, st);
+  } else if (cs.precision == 2) {
+    if (bpl == 1) launch_one<1, 2>(p, num_sms, st);
+    else if (bpl == 4) launch_one<4, 2>(p, num_sms, st);
+    else launch_one<2, 2>(p, num_sms, st);
   } else {
     if (bpl == 1) launch_one<1, 1>(p, num_sms, st);
     else if (bpl == 4) launch_one<4, 1>(p, num_sms, st);

@@ -12,6 +12,7 @@ constexpr double kMagic = 6755399441055744.0;               // 1.5 * 2^52
 
 // root of b u + c u^2 + d u^3 = delta on [ulo, uhi] (monotone, direction dir):
 // FP32 safeguarded Newton from a regula-falsi start; returns u and dF/du (FP32)
+template <int NIT>
 __device__ __forceinline__ float root_f32(float bf, float cf, float df, float dl, float lo, float hi, int dir,
                                           float& Dout) {
   float flo = ((df * lo + cf) * lo + bf) * lo - dl;
@@ -20,7 +21,7 @@ __device__ __forceinline__ float root_f32(float bf, float cf, float df, float dl
   if (!(u >= lo && u <= hi)) u = 0.5f * (lo + hi);
   float D = 0.f;
 #pragma unroll 1
-  for (int it = 0; it < 6; it++) {
+  for (int it = 0; it < NIT; it++) {
     float fu = ((df * u + cf) * u + bf) * u - dl;
     D = (3.f * df * u + 2.f * cf) * u + bf;
     if (fu == 0.f) break;
@@ -48,10 +49,11 @@ __device__ __forceinline__ int run_segment(const Run& R, const long long* keyF, 
 
 // a6: FP32 start value, FP64 Newton polish (iterated where the predicted error of
 // one step exceeds 1e-13, i.e. near turnovers), clamped into [ulo, uhi]
+template <int NIT>
 __device__ __forceinline__ double solve_root(const SegCore& C, double delta, double ulo, double uhi, int dir,
                                              float& uf_out, float& Df_out) {
   float Df;
-  float uf = root_f32(C.bf, C.cf, C.df, d2f_bits(delta), d2f_bits(ulo), d2f_bits(uhi), dir, Df);
+  float uf = root_f32<NIT>(C.bf, C.cf, C.df, d2f_bits(delta), d2f_bits(ulo), d2f_bits(uhi), dir, Df);
   double u = f2d_bits(uf);
   double res = fma(u, fma(u, fma(u, C.d, C.c), C.b), -delta);
   float rcf = __fdividef(1.f, Df);

@@ -33,10 +33,14 @@ def _cmp(got, ref, tol):
         assert np.array_equal(np.abs(g) > 0, np.abs(r) > 0)
 
 
+PRECS = ["fp64", "fp64x"]   # both must meet the FP64 tolerance
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("n_bins", [2 ** 15, 2 ** 15 - 13, 1000, 77])
-def test_small_config(oracle, n_bins):
+def test_small_config(oracle, n_bins, prec):
     w = synth.small_config(0, n_bins=n_bins)
-    _cmp(run(w), oracle.sum_modes(w), TOL64)
+    _cmp(run(w, precision=prec), oracle.sum_modes(w), TOL64)
 
 
 @pytest.mark.parametrize("tb", [32, 64, 128])
@@ -62,26 +66,29 @@ def test_mode_bin_count_matches_oracle(oracle):
     assert 2 * st["mode_bins"] == ost["contributions"]
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("K", [50, 100, 400])
-def test_power_law_chirp(oracle, K):
+def test_power_law_chirp(oracle, K, prec):
     w, p = synth.chirp_config(K=K, n_bins=2 ** 13)
-    _cmp(run(w, conj=False), oracle.sum_modes(w, conj_partners=False), TOL64)
+    _cmp(run(w, conj=False, precision=prec), oracle.sum_modes(w, conj_partners=False), TOL64)
 
 
-def test_linear_chirp_closed_form(oracle):
+@pytest.mark.parametrize("prec", PRECS)
+def test_linear_chirp_closed_form(oracle, prec):
     w, p = AN.linear_chirp()
-    hp, hc = run(w, conj=False)
+    hp, hc = run(w, conj=False, precision=prec)
     ref = oracle.sum_modes(w, conj_partners=False)
     _cmp((hp, hc), ref, TOL64)
     Y = oracle.swsh_closed(2, 1, w.theta, w.phi)
     got = (hp - 1j * hc) / (Y * w.amp[0, 0])
     exp = AN.linear_chirp_expected(w, p, w.freqs)
-    assert np.max(np.abs(got - exp)) / np.max(np.abs(exp)) < 1e-11
+    assert np.max(np.abs(got - exp)) / np.max(np.abs(exp)) < (1e-11 if prec == "fp64" else 5e-11)
 
 
-def test_quadratic_turnover(oracle):
+@pytest.mark.parametrize("prec", PRECS)
+def test_quadratic_turnover(oracle, prec):
     w, p = AN.quadratic_voice()
-    got = run(w, conj=False)
+    got = run(w, conj=False, precision=prec)
     ref = oracle.sum_modes(w, conj_partners=False)
     # bins within 1e-6 of the turnover frequency are ill-conditioned (|H| ~ |f - F*|^(-1/4))
     far = np.abs(w.freqs - p["Fs"]) > 1e-6 * p["Fs"]
@@ -90,17 +97,19 @@ def test_quadratic_turnover(oracle):
     assert np.array_equal(np.abs(got[0]) > 0, np.abs(ref[0]) > 0)
 
 
-def test_sparse_paper_grid(oracle):
+@pytest.mark.parametrize("prec", PRECS)
+def test_sparse_paper_grid(oracle, prec):
     w = synth.paper_config(1, grid="sparse")
-    _cmp(run(w), oracle.sum_modes(w), TOL64)
+    _cmp(run(w, precision=prec), oracle.sum_modes(w), TOL64)
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("seed", [1, 2])
-def test_paper_config_sampled(oracle, seed):
+def test_paper_config_sampled(oracle, seed, prec):
     """Full-size 2 yr waveform (2000 modes, 3,155,760 bins) in the bench's launch
     configuration; the oracle evaluates ~4000 sampled bins (bins are independent)."""
     w = synth.paper_config(seed)
-    hp, hc = run(w)
+    hp, hc = run(w, precision=prec)
     rng = np.random.default_rng(seed)
     occupied = np.nonzero(np.abs(hp) > 0)[0]
     sel = np.unique(np.concatenate([rng.choice(w.n_freqs, 1000, replace=False),
@@ -109,13 +118,14 @@ def test_paper_config_sampled(oracle, seed):
     _cmp((hp[sel], hc[sel]), (rp, rc), TOL64)
 
 
-def test_batch_equals_singles_bitwise():
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_equals_singles_bitwise(prec):
     wfs = [synth.small_config(0, n_bins=3001), synth.paper_config(3, n_modes=300, T_years=0.5, grid="sparse", n_sparse=4000),
            synth.chirp_config(K=60, n_bins=999)[0]]
-    bh, bc = run(wfs)
+    bh, bc = run(wfs, precision=prec)
     off = 0
     for w in wfs:
-        sh, sc = run(w)
+        sh, sc = run(w, precision=prec)
         assert np.array_equal(bh[off:off + w.n_freqs], sh) and np.array_equal(bc[off:off + w.n_freqs], sc)
         off += w.n_freqs
 
