@@ -182,6 +182,15 @@ struct DevInputs {
   void *h_plus, *h_cross;
 };
 
+// per knot segment of a waveform: the u-coefficients (c1, c2, c3, 0) of the four
+// fundamental series (Phi_phi, Phi_r, Omega_phi, Omega_r) and, as Q0.64 turns,
+// frac(Phi_phi_s / 2 pi), frac(Phi_r_s / 2 pi) and frac(phi / 2 pi)
+struct FundSeg {
+  dbl4 P[4];
+  unsigned long long q[4];
+};
+static_assert(sizeof(FundSeg) == 160, "FundSeg layout");
+
 struct DevScratch {
   int* status;
   unsigned long long* counters;   // [0] tile queue, [1] mode-bins, [2] runs total, [3] busy tiles
@@ -190,6 +199,7 @@ struct DevScratch {
   dbl4* spl_fac;               // [sum K] {c'_i, 1/m_i, s_i/m_i, a_i/m_i} of each waveform's not-a-knot sweep
   double* spl_ih;                 // [sum K] 1/h_k
   double* fundM;                  // [4][sum K]
+  FundSeg* fund;                  // [sum K]
   double* ampM;                   // [sum N_m K][2]
   SegCore* core;
   SegAmp64* amp64;

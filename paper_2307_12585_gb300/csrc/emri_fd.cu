@@ -137,6 +137,7 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
   AL(s.spl_fac, p->cap_K);
   AL(s.spl_ih, p->cap_K);
   AL(s.fundM, 4 * p->cap_K);
+  AL(s.fund, p->cap_K);
   AL(s.ampM, 2 * p->cap_amp);
   AL(s.core, p->cap_seg);
   if (d->precision == EMRI_FD_FP64) { AL(s.amp64, p->cap_seg); }

@@ -38,7 +38,8 @@ constexpr size_t kOffModes = kOffAngles + al256(3 * sizeof(double));
 constexpr size_t kOffFac = kOffModes + al256(kNaMaxModes * sizeof(ModeInfo));
 constexpr size_t kOffIh = kOffFac + al256(kNaMaxK * sizeof(dbl4));
 constexpr size_t kOffFundM = kOffIh + al256(kNaMaxK * sizeof(double));
-constexpr size_t kOffAmpM = kOffFundM + al256(4 * kNaMaxK * sizeof(double));
+constexpr size_t kOffFund = kOffFundM + al256(4 * kNaMaxK * sizeof(double));
+constexpr size_t kOffAmpM = kOffFund + al256(kNaMaxK * sizeof(FundSeg));
 constexpr size_t kOffCore = kOffAmpM + al256(2 * kNaMaxAmp * sizeof(double));
 constexpr size_t kOffAmp64 = kOffCore + al256(kNaMaxSeg * sizeof(SegCore));
 constexpr size_t kOffCrit = kOffAmp64 + al256(kNaMaxSeg * sizeof(SegAmp64));
@@ -49,7 +50,7 @@ constexpr size_t kOffRunF = kOffRuns + al256(kNaRunCap * sizeof(Run));
 constexpr size_t kOffRbins = kOffRunF + al256(kNaRunCap * sizeof(double2));
 constexpr size_t kOffTab = kOffRbins + al256(kNaRunCap * sizeof(RunBins));
 constexpr size_t kNaBytes = kOffTab + al256(kTabN * sizeof(double2));
-static_assert(kNaBytes == 6538240, "the size stated in include/emri_fd.h");
+static_assert(kNaBytes == 6570240, "the size stated in include/emri_fd.h");
 
 // The scratch.  In host code this name is only a stand-in for the device
 // symbol; its device address comes from cudaGetSymbolAddress below.
@@ -122,6 +123,7 @@ extern "C" emri_fd_status emri_fd_sum_modes_noalloc(int conj_partners, long long
   s.spl_fac = reinterpret_cast<dbl4*>(base + kOffFac);
   s.spl_ih = reinterpret_cast<double*>(base + kOffIh);
   s.fundM = reinterpret_cast<double*>(base + kOffFundM);
+  s.fund = reinterpret_cast<FundSeg*>(base + kOffFund);
   s.ampM = reinterpret_cast<double*>(base + kOffAmpM);
   s.core = reinterpret_cast<SegCore*>(base + kOffCore);
   s.amp64 = reinterpret_cast<SegAmp64*>(base + kOffAmp64);

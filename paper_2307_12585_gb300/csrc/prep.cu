@@ -162,79 +162,6 @@ __device__ __forceinline__ double rcp_d(double x) {
   return fma(y, e, y);
 }
 
-// per waveform: the forward-sweep factors {c'_i, 1/m_i, s_i/m_i, a_i/m_i} of the
-// reduced system, and 1/h_k (one thread per waveform: the sweep is sequential)
-__global__ void k_spline_factor(int n_wf, const WfInfo* wf, const double* tall, dbl4* fac, double* ih) {
-  int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= n_wf) return;
-  const WfInfo W = wf[w];
-  const double* t = tall + W.ko;
-  int K = (int)W.K;
-  for (int k = 0; k + 1 < K; k++) ih[W.ko + k] = rcp_d(t[k + 1] - t[k]);
-  ih[W.ko + K - 1] = 0.0;
-  double cprev = 0.0;
-  fac[W.ko] = mk_dbl4(0.0, 0.0, 0.0, 0.0);
-  fac[W.ko + K - 1] = mk_dbl4(0.0, 0.0, 0.0, 0.0);
-  for (int i = 1; i <= K - 2; i++) {
-    double a, b, c, sc;
-    tri_row(t, K, i, a, b, c, sc);
-    double inv = rcp_d(b - a * cprev);
-    double cc = (i == K - 2) ? 0.0 : c * inv;
-    fac[W.ko + i] = mk_dbl4(cc, inv, sc * inv, a * inv);
-    cprev = cc;
-  }
-}
-
-// one thread per series; y has stride ys, M is written with stride ms
-__device__ void spline_solve(int K, const double* y, long long ys, double* M, long long ms, const dbl4* fac,
-                             const double* ih) {
-  double rp = 0.0;
-  double y0 = y[0], y1 = y[ys];
-  double d0 = (y1 - y0) * ih[0];
-  for (int i = 1; i <= K - 2; i++) {
-    const double y2 = y[(i + 1) * ys];
-    const double d1 = (y2 - y1) * ih[i];
-    const double r = 6.0 * (d1 - d0);
-    const dbl4 F = fac[i];
-    rp = fma(r, F.z, -rp * F.w);        // (r s - a rp)/m
-    M[i * ms] = rp;                     // forward-swept right-hand side, overwritten below
-    d0 = d1;
-    y1 = y2;
-  }
-  double next = M[(K - 2) * ms];
-  for (int i = K - 3; i >= 1; i--) {
-    double v = M[i * ms] - fac[i].x * next;
-    M[i * ms] = v;
-    next = v;
-  }
-  // M_0 = ((h0+h1) M_1 - h0 M_2)/h1 ;  M_{K-1} = ((ha+hb) M_{K-2} - hb M_{K-3})/ha
-  const double r01 = ih[1] / ih[0];                      // h0 / h1
-  M[0] = (1.0 + r01) * M[ms] - r01 * M[2 * ms];
-  const double rba = ih[K - 3] / ih[K - 2];              // hb / ha
-  M[(K - 1) * ms] = (1.0 + rba) * M[(K - 2) * ms] - rba * M[(K - 3) * ms];
-}
-
-__global__ void k_spline_solve(int n_wf, const WfInfo* wf, const ModeInfo* modes, long long nm_total, DevInputs in,
-                               const dbl4* fac, const double* ih, double* fundM, long long K_total, double* ampM) {
-  long long sid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long nfund = 4LL * n_wf;
-  if (sid < nfund) {
-    int w = (int)(sid >> 2), which = (int)(sid & 3);
-    const WfInfo W = wf[w];
-    const double* y = which == 0 ? in.phi_phi : which == 1 ? in.phi_r : which == 2 ? in.omega_phi : in.omega_r;
-    spline_solve((int)W.K, y + W.ko, 1, fundM + which * K_total + W.ko, 1, fac + W.ko, ih + W.ko);
-    return;
-  }
-  sid -= nfund;
-  if (sid >= 2 * nm_total) return;
-  long long j = sid >> 1;
-  int part = (int)(sid & 1);
-  const ModeInfo Mi = modes[j];
-  const WfInfo W = wf[Mi.wf];
-  spline_solve((int)W.K, in.amp + 2 * Mi.key_base + part, 2, ampM + 2 * Mi.key_base + part, 2, fac + W.ko, ih + W.ko);
-}
-
-// ------------------------------------------------ per (mode, segment) records
 struct dd { double hi, lo; };
 __device__ __forceinline__ dd dd_two_prod(double a, double b) { dd r; r.hi = a * b; r.lo = fma(a, b, -r.hi); return r; }
 __device__ __forceinline__ dd dd_fast(double s, double e) { dd r; r.hi = s + e; r.lo = e - (r.hi - s); return r; }
@@ -262,14 +189,199 @@ __device__ __forceinline__ void ucoef(double y0, double y1, double M0, double M1
   c[3] = h2 * (M1 - M0) * (1.0 / 6.0);
 }
 
-__device__ __forceinline__ void put_ff(float* dst, double x) {
-  const ff v = ff_from_double(x);
-  dst[0] = v.hi;
-  dst[1] = v.lo;
+// ---- warp-parallel forms of the two sequential sweeps (GB300's FP64 latency
+// makes a 200-step dependent chain per thread slow, so each sweep is written as
+// a scan over the warp: every lane composes its stretch of consecutive steps,
+// the compositions are combined with a Hillis-Steele scan, and each lane then
+// replays its stretch from the prefix).
+
+// scale a pair/matrix by a power of two so that its largest entry is O(1)
+__device__ __forceinline__ double pow2_of_max(double m) {
+  const long long e = ((__double_as_longlong(m) >> 52) & 0x7FF);
+  // 2^-(e-1023), clamped to the normal range
+  const long long ee = e < 1 ? 1 : (e > 2045 ? 2045 : e);
+  return __longlong_as_double((2046 - ee) << 52);
 }
 
-__global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, DevInputs in, const double* fundM,
-                           long long K_total, const double* ampM, long long seg_total, SegCore* core,
+struct M22 { double a, b, c, d; };
+__device__ __forceinline__ M22 m22_mul(const M22& X, const M22& Y) {   // X Y
+  M22 r;
+  r.a = fma(X.a, Y.a, X.b * Y.c); r.b = fma(X.a, Y.b, X.b * Y.d);
+  r.c = fma(X.c, Y.a, X.d * Y.c); r.d = fma(X.c, Y.b, X.d * Y.d);
+  const double sc = pow2_of_max(fmax(fmax(fabs(r.a), fabs(r.b)), fmax(fabs(r.c), fabs(r.d))));
+  r.a *= sc; r.b *= sc; r.c *= sc; r.d *= sc;
+  return r;
+}
+__device__ __forceinline__ M22 m22_shfl_up(const M22& X, int o) {
+  M22 r;
+  r.a = __shfl_up_sync(0xffffffffu, X.a, o); r.b = __shfl_up_sync(0xffffffffu, X.b, o);
+  r.c = __shfl_up_sync(0xffffffffu, X.c, o); r.d = __shfl_up_sync(0xffffffffu, X.d, o);
+  return r;
+}
+
+// per waveform (one warp): the forward-sweep factors {c'_i, 1/m_i, s_i/m_i, a_i/m_i}
+// of the reduced system, and 1/h_k.  With v_i = (N_i, D_i) = M_i v_{i-1},
+// M_i = [[0, c_i], [-a_i, b_i]], v_0 = (0, 1): c'_i = N_i / D_i and
+// m_i = b_i - a_i c'_{i-1} = D_i / D_{i-1}.
+__global__ void k_spline_factor(int n_wf, const WfInfo* wf, const double* tall, dbl4* fac, double* ih) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= n_wf) return;
+  const WfInfo W = wf[w];
+  const double* t = tall + W.ko;
+  const int K = (int)W.K, n = K - 2;                 // unknowns i = 1..K-2
+  for (int k = lane; k < K; k += 32) ih[W.ko + k] = (k + 1 < K) ? rcp_d(t[k + 1] - t[k]) : 0.0;
+  if (lane == 0) {
+    fac[W.ko] = mk_dbl4(0.0, 0.0, 0.0, 0.0);
+    fac[W.ko + K - 1] = mk_dbl4(0.0, 0.0, 0.0, 0.0);
+  }
+  const int E = (n + 31) / 32;
+  const int i0 = 1 + lane * E, i1 = min(i0 + E, n + 1);
+  M22 Q = {1.0, 0.0, 0.0, 1.0};
+  for (int i = i0; i < i1; i++) {
+    double a, b, c, sc;
+    tri_row(t, K, i, a, b, c, sc);
+    const M22 Mi = {0.0, c, -a, b};
+    Q = m22_mul(Mi, Q);
+  }
+  M22 S = Q;
+  for (int o = 1; o < 32; o <<= 1) {
+    const M22 X = m22_shfl_up(S, o);
+    if (lane >= o) S = m22_mul(S, X);
+  }
+  M22 P = m22_shfl_up(S, 1);
+  if (lane == 0) P = M22{1.0, 0.0, 0.0, 1.0};
+  double N = P.b, D = P.d;                           // v_{i0-1} = P (0, 1)
+  for (int i = i0; i < i1; i++) {
+    double a, b, c, sc;
+    tri_row(t, K, i, a, b, c, sc);
+    const double Nn = c * D, Dn = fma(-a, N, b * D);
+    const double inv = D * rcp_d(Dn);                // 1/m_i = D_{i-1}/D_i
+    const double cc = (i == K - 2) ? 0.0 : c * inv;
+    fac[W.ko + i] = mk_dbl4(cc, inv, sc * inv, a * inv);
+    const double scl = pow2_of_max(fmax(fabs(Nn), fabs(Dn)));
+    N = Nn * scl;
+    D = Dn * scl;
+  }
+}
+
+// affine map x -> p x + q; compose(g, f) = g after f
+struct Aff { double p, q; };
+__device__ __forceinline__ Aff aff_after(const Aff& g, const Aff& f) { Aff r; r.p = g.p * f.p; r.q = fma(g.p, f.q, g.q); return r; }
+
+// right-hand side of row i times s_i/m_i: q_i = 6 [(y_{i+1}-y_i)/h_i - (y_i-y_{i-1})/h_{i-1}] s_i/m_i
+__device__ __forceinline__ double rhs_q(const double* y, long long ys, const double* ih, const dbl4* fac, int i) {
+  const double d1 = (y[(i + 1) * ys] - y[i * ys]) * ih[i];
+  const double d0 = (y[i * ys] - y[(i - 1) * ys]) * ih[i - 1];
+  return 6.0 * (d1 - d0) * fac[i].z;
+}
+
+// one warp per series: forward sweep rp_i = q_i - (a_i/m_i) rp_{i-1}, back
+// substitution M_i = rp_i - c'_i M_{i+1}, both as warp scans of affine maps
+__device__ void spline_solve_warp(int K, const double* y, long long ys, double* M, long long ms, const dbl4* fac,
+                                  const double* ih, int lane) {
+  const int n = K - 2;
+  const int E = (n + 31) / 32;
+  const int i0 = 1 + lane * E, i1 = min(i0 + E, n + 1);
+  // forward
+  Aff F = {1.0, 0.0};
+  for (int i = i0; i < i1; i++) {
+    const Aff f = {-fac[i].w, rhs_q(y, ys, ih, fac, i)};
+    F = aff_after(f, F);
+  }
+  Aff S = F;
+  for (int o = 1; o < 32; o <<= 1) {
+    Aff X;
+    X.p = __shfl_up_sync(0xffffffffu, S.p, o);
+    X.q = __shfl_up_sync(0xffffffffu, S.q, o);
+    if (lane >= o) S = aff_after(S, X);
+  }
+  double x = __shfl_up_sync(0xffffffffu, S.q, 1);   // exclusive prefix applied to rp_0 = 0
+  if (lane == 0) x = 0.0;
+  for (int i = i0; i < i1; i++) {
+    x = fma(-fac[i].w, x, rhs_q(y, ys, ih, fac, i));
+    M[i * ms] = x;
+  }
+  __syncwarp();
+  // backward, in decreasing i: x_i = rp_i - c'_i x_{i+1}, x_{K-1} = 0 (c'_{K-2} = 0)
+  const int j0 = n - lane * E, j1 = max(j0 - E, 0);   // lane covers i = j0 .. j1+1 downwards
+  Aff B = {1.0, 0.0};
+  for (int i = j0; i > j1; i--) {
+    const Aff f = {-fac[i].x, M[i * ms]};
+    B = aff_after(f, B);
+  }
+  S = B;
+  for (int o = 1; o < 32; o <<= 1) {
+    Aff X;
+    X.p = __shfl_up_sync(0xffffffffu, S.p, o);
+    X.q = __shfl_up_sync(0xffffffffu, S.q, o);
+    if (lane >= o) S = aff_after(S, X);
+  }
+  x = __shfl_up_sync(0xffffffffu, S.q, 1);
+  if (lane == 0) x = 0.0;
+  __syncwarp();
+  for (int i = j0; i > j1; i--) {
+    x = fma(-fac[i].x, x, M[i * ms]);
+    M[i * ms] = x;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    // M_0 = ((h0+h1) M_1 - h0 M_2)/h1 ;  M_{K-1} = ((ha+hb) M_{K-2} - hb M_{K-3})/ha
+    const double r01 = ih[1] / ih[0];                      // h0 / h1
+    M[0] = (1.0 + r01) * M[ms] - r01 * M[2 * ms];
+    const double rba = ih[K - 3] / ih[K - 2];              // hb / ha
+    M[(K - 1) * ms] = (1.0 + rba) * M[(K - 2) * ms] - rba * M[(K - 3) * ms];
+  }
+}
+
+__global__ void k_spline_solve(int n_wf, const WfInfo* wf, const ModeInfo* modes, long long nm_total, DevInputs in,
+                               const dbl4* fac, const double* ih, double* fundM, long long K_total, double* ampM,
+                               FundSeg* fund) {
+  long long sid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  long long nfund = 4LL * n_wf;
+  if (sid < nfund) {
+    int w = (int)(sid >> 2), which = (int)(sid & 3);
+    const WfInfo W = wf[w];
+    const double* y = which == 0 ? in.phi_phi : which == 1 ? in.phi_r : which == 2 ? in.omega_phi : in.omega_r;
+    const double* ys = y + W.ko;
+    const double* Ms = fundM + which * K_total + W.ko;
+    spline_solve_warp((int)W.K, ys, 1, fundM + which * K_total + W.ko, 1, fac + W.ko, ih + W.ko, lane);
+    __syncwarp();
+    // per segment: this series' u-coefficients, and (Phi series) the knot phase in turns
+    const double* t = in.t + W.ko;
+    for (int s = lane; s + 1 < (int)W.K; s += 32) {
+      const double h = t[s + 1] - t[s];
+      double c[4];
+      ucoef(ys[s], ys[s + 1], Ms[s], Ms[s + 1], h * h, c);
+      FundSeg* F = fund + W.ko + s;
+      F->P[which] = mk_dbl4(c[1], c[2], c[3], 0.0);
+      dd x;
+      if (which < 2) x = dd_mul(dd{ys[s], 0.0}, dd{kInv2PiHi, kInv2PiLo});
+      else if (which == 2) x = dd_mul(dd{in.phi[w], 0.0}, dd{kInv2PiHi, kInv2PiLo});
+      else x = dd{0.0, 0.0};
+      F->q[which] = q64_of(x.hi) + q64_of(x.lo);
+    }
+    return;
+  }
+  sid -= nfund;
+  if (sid >= 2 * nm_total) return;
+  long long j = sid >> 1;
+  int part = (int)(sid & 1);
+  const ModeInfo Mi = modes[j];
+  const WfInfo W = wf[Mi.wf];
+  spline_solve_warp((int)W.K, in.amp + 2 * Mi.key_base + part, 2, ampM + 2 * Mi.key_base + part, 2, fac + W.ko,
+                    ih + W.ko, lane);
+}
+
+// ------------------------------------------------ per (mode, segment) records
+__device__ __forceinline__ void put_ff(float* dst, double x) {
+  // hi rounded to nearest; x - hi is exact; lo truncated (|lo| <= |x - hi| <= ulp(hi)/2)
+  const float hi = __double2float_rn(x);
+  dst[0] = hi;
+  dst[1] = d2f_bits(x - f2d_bits(hi));
+}
+
+__global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, DevInputs in, const FundSeg* fund, const double* ampM, long long seg_total, SegCore* core,
                            SegAmp64* amp64, SegAmp32* amp32, SegFF* segff, SegCrit* crit, long long* keyF) {
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= seg_total) return;
@@ -283,33 +395,26 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
   const ModeInfo Mi = modes[j];
   const int m = Mi.m, n = Mi.n;
   long long i0 = W.ko + s;
-  double ts = in.t[i0], h = in.t[i0 + 1] - ts, h2 = h * h;
-  double cPp[4], cPr[4], cOp[4], cOr[4];
-  ucoef(in.phi_phi[i0], in.phi_phi[i0 + 1], fundM[i0], fundM[i0 + 1], h2, cPp);
-  ucoef(in.phi_r[i0], in.phi_r[i0 + 1], fundM[K_total + i0], fundM[K_total + i0 + 1], h2, cPr);
-  ucoef(in.omega_phi[i0], in.omega_phi[i0 + 1], fundM[2 * K_total + i0], fundM[2 * K_total + i0 + 1], h2, cOp);
-  ucoef(in.omega_r[i0], in.omega_r[i0 + 1], fundM[3 * K_total + i0], fundM[3 * K_total + i0 + 1], h2, cOr);
+  const double ts = in.t[i0], h = in.t[i0 + 1] - ts, h2 = h * h;
+  const FundSeg& Fs = fund[i0];
+  const dbl4 cPp = Fs.P[0], cPr = Fs.P[1], cOp = Fs.P[2], cOr = Fs.P[3];
   const double dm = (double)m, dn = (double)n;
   SegCore C;
   C.A = knot_freq(m, n, in.omega_phi[i0], in.omega_r[i0]);
-  C.b = (dm * cOp[1] + dn * cOr[1]) * kInv2PiHi;
-  C.c = (dm * cOp[2] + dn * cOr[2]) * kInv2PiHi;
-  C.d = (dm * cOp[3] + dn * cOr[3]) * kInv2PiHi;
+  C.b = (dm * cOp.x + dn * cOr.x) * kInv2PiHi;
+  C.c = (dm * cOp.y + dn * cOr.y) * kInv2PiHi;
+  C.d = (dm * cOp.z + dn * cOr.z) * kInv2PiHi;
   C.c2 = 2.0 * C.c;
   C.d3 = 3.0 * C.d;
-  double P1 = (dm * cPp[1] + dn * cPr[1]) * kInv2PiHi;
+  double P1 = (dm * cPp.x + dn * cPr.x) * kInv2PiHi;
   C.Q1 = fma(-C.A, h, P1);
-  C.P2 = (dm * cPp[2] + dn * cPr[2]) * kInv2PiHi;
-  C.P3 = (dm * cPp[3] + dn * cPr[3]) * kInv2PiHi;
+  C.P2 = (dm * cPp.y + dn * cPr.y) * kInv2PiHi;
+  C.P3 = (dm * cPp.z + dn * cPr.z) * kInv2PiHi;
   C.h = h;
   C.ts = ts;
-  // theta0 = frac((m Phi_phi_s + n Phi_r_s - m phi)/2pi), double-double then Q0.64
-  dd ph = dd_add(dd_two_prod(dm, in.phi_phi[i0]), dd_two_prod(dn, in.phi_r[i0]));
-  dd az = dd_two_prod(-dm, in.phi[lo]);
-  ph = dd_add(ph, az);
-  dd inv; inv.hi = kInv2PiHi; inv.lo = kInv2PiLo;
-  dd turns = dd_mul(ph, inv);
-  C.theta0 = q64_of(turns.hi) + q64_of(turns.lo);
+  // theta0 = frac((m Phi_phi_s + n Phi_r_s - m phi)/2pi): integer combination of
+  // the Q0.64 knot phases (wraps modulo one turn)
+  C.theta0 = (unsigned long long)(long long)m * (Fs.q[0] - Fs.q[2]) + (unsigned long long)(long long)n * Fs.q[1];
   C.bf = (float)C.b; C.cf = (float)C.c; C.df = (float)C.d; C.pad = 0.f;
   core[r] = C;
 
@@ -677,12 +782,12 @@ void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, 
   k_validate_amp<<<256, 256, 0, st>>>(2 * cs.amp_total, in.amp, s.status);
   k_modes<<<(unsigned)((cs.nm_total + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes, cs.nm_total,
                                                                   s.status);
-  k_spline_factor<<<(cs.n_wf + 63) / 64, 64, 0, st>>>(cs.n_wf, s.wf, in.t, s.spl_fac, s.spl_ih);
+  k_spline_factor<<<(cs.n_wf * 32 + 127) / 128, 128, 0, st>>>(cs.n_wf, s.wf, in.t, s.spl_fac, s.spl_ih);
   long long nser = 4LL * cs.n_wf + 2 * cs.nm_total;
-  k_spline_solve<<<(unsigned)((nser + 127) / 128), 128, 0, st>>>(cs.n_wf, s.wf, s.modes, cs.nm_total, in, s.spl_fac,
-                                                                 s.spl_ih, s.fundM, cs.K_total, s.ampM);
+  k_spline_solve<<<(unsigned)((nser * 32 + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, s.modes, cs.nm_total, in, s.spl_fac,
+                                                                 s.spl_ih, s.fundM, cs.K_total, s.ampM, s.fund);
   k_seg_prep<<<(unsigned)((cs.seg_total + 127) / 128), 128, 0, st>>>(
-      cs.n_wf, s.wf, s.modes, in, s.fundM, cs.K_total, s.ampM, cs.seg_total, s.core,
+      cs.n_wf, s.wf, s.modes, in, s.fund, s.ampM, cs.seg_total, s.core,
       cs.precision == 0 ? s.amp64 : nullptr, cs.precision == 1 ? s.amp32 : nullptr,
       cs.precision == 2 ? s.segff : nullptr, s.crit, s.keyF);
   unsigned wblocks = (unsigned)((cs.nm_total * 32 + 255) / 256);
