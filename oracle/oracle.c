@@ -35,6 +35,10 @@
  *     monotone pieces of each segment (split where Fdot = 0, at most one
  *     turnover per segment in practice, Sec. 2.2) and found by bisection
  *     to the last bit.  A root with Fdot == 0 exactly contributes 0.
+ *  4'. Extended form (spa_form = 1): each root instead contributes
+ *     H_V(t_j) exp(i[2 pi g t_j - Phi_V(t_j)]) G(Fdot_j, Fddot_j), where G is
+ *     the Fourier integral of the phase expanded to third order (Eq. 7-10)
+ *     in terms of K_{1/3}; see ext_factor() for the reading of its sign.
  *  5. Output at f > 0 (h = h+ - i hx, Eq. 1; Fourier sign of Eq. 3):
  *     h+(f) = [H(f) + conj H(-f)]/2,  hx(f) = i [H(f) - conj H(-f)]/2.
  *
@@ -44,6 +48,7 @@
  * evaluated in that order, so every frequency crossing of the whole track is
  * counted exactly once.  Interior turnover frequencies come from the cubic.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -295,10 +300,83 @@ static dd_t dd_spline(const double* c4, double x) {
   return r;
 }
 
-/* contribution of one root: adds H_V e^{i psi}/sqrt|Fdot| to acc[0..1] */
-static int contrib(const traj_t* T, const voice_t* V, int k, const double* fc, double g, double x, double* acc) {
+/* ------------------------------------------------------------------ */
+/* Extended SPA factor (Sec. 2.2, Eq. 7-10)                             */
+/* ------------------------------------------------------------------ */
+/*
+ * E(X) = e^z K_{1/3}(z) at z = -i X, X real and non-zero, straight from an
+ * integral definition of K_nu (DLMF 10.32.8):
+ *   K_nu(z) = sqrt(pi) (z/2)^nu / Gamma(nu + 1/2) int_1^inf e^{-z t} (t^2 - 1)^{nu - 1/2} dt.
+ * For X > 0 the path t = 1 + i s (s >= 0) turns the oscillating integrand
+ * into a decaying one; with s = e^v this gives
+ *   E(X) = sqrt(pi)/Gamma(5/6) (X/2)^{1/3} e^{i pi/4}
+ *          int_R exp(5v/6 - X e^v) (2 + i e^v)^{-1/6} dv,
+ * an analytic integrand that decays exponentially on both sides, so the
+ * trapezoid rule on a fixed step converges geometrically.  For X < 0,
+ * E(X) = conj E(-X) (K_nu(conj z) = conj K_nu(z) for real nu).
+ */
+static double complex ext_E(double X) {
+  const double ax = fabs(X);
+  const double hv = 0.1;
+  const double v0 = log(1e-20 / ax), v1 = log(60.0 / ax);
+  const long long nstep = (long long)ceil((v1 - v0) / hv);
+  double complex sum = 0.0;
+  for (long long i = 0; i <= nstep; i++) {
+    const double v = v0 + hv * (double)i;
+    const double ev = exp(v);
+    sum += exp(5.0 * v / 6.0 - ax * ev) * cpow(2.0 + I * ev, -1.0 / 6.0);
+  }
+  sum *= hv;
+  const double complex e = sqrt(OR_PI) / tgamma(5.0 / 6.0) * cbrt(0.5 * ax) * cexp(I * (OR_PI / 4.0)) * sum;
+  return X > 0.0 ? e : conj(e);
+}
+
+/*
+ * G(Fdot, Fddot): the time integral of Eq. 8 for one root, in the closed form
+ * of Eq. 10, int exp(-i pi [Fdot t^2 + Fddot t^3/3]) dt ->
+ *   -(2/sqrt 3) (i Fdot/|Fddot|) e^z K_{1/3}(z),   z = -2 pi i Fdot^3 / (3 Fddot^2),
+ * with the principal branch of K_{1/3}.  The overall sign is the reading
+ * taken here: Eq. 10 as printed tends to -exp(-i sgn(Fdot) pi/4)/sqrt|Fdot|
+ * when Fddot -> 0, the negative of the Fresnel value that Eq. 10 must reduce
+ * to, so the factor is negated.  With that sign the two roots of a pure
+ * cubic phase add up to its exact (Airy-function) Fourier transform.
+ *   Fddot == 0: the Fresnel value exp(-i sgn(Fdot) pi/4)/sqrt|Fdot|.
+ *   Fdot == 0 (a double root at a turnover): the limit of the two-root sum,
+ *     2 pi (pi |Fddot|)^{-1/3} Ai(0) = 2 pi^{2/3} / (3^{2/3} Gamma(2/3)) |Fddot|^{-1/3}.
+ *   both zero: 0.
+ */
+static double complex ext_factor(double Fd, double Fdd) {
+  if (Fdd == 0.0) {
+    if (Fd == 0.0) return 0.0;
+    return cexp(-I * (Fd > 0.0 ? 1.0 : -1.0) * (OR_PI / 4.0)) / sqrt(fabs(Fd));
+  }
+  if (Fd == 0.0) return 2.0 * pow(OR_PI, 2.0 / 3.0) / (pow(3.0, 2.0 / 3.0) * tgamma(2.0 / 3.0)) / cbrt(fabs(Fdd));
+  const double X = 2.0 * OR_PI * Fd * Fd * Fd / (3.0 * Fdd * Fdd);
+  return -(2.0 / sqrt(3.0)) * (I * Fd / fabs(Fdd)) * ext_E(X);
+}
+
+/* exported for tests: G(Fdot, Fddot) as (re, im) */
+void oracle_ext_factor(long long n, const double* Fd, const double* Fdd, double* out) {
+  for (long long i = 0; i < n; i++) {
+    const double complex g = ext_factor(Fd[i], Fdd[i]);
+    out[2 * i] = creal(g);
+    out[2 * i + 1] = cimag(g);
+  }
+}
+
+/* contribution of one root: adds H_V e^{i psi}/sqrt|Fdot| (standard form) or
+ * H_V e^{i psi0} G(Fdot, Fddot) (extended form) to acc[0..1] */
+static int contrib(const traj_t* T, const voice_t* V, int k, const double* fc, double g, double x, int ext,
+                   double* acc) {
   double Fd = dcubic(fc, x);
-  if (Fd == 0.0) return 1;
+  double complex G = 1.0;
+  if (ext) {
+    const double Fdd = 2.0 * fc[2] + 6.0 * fc[3] * x;
+    G = ext_factor(Fd, Fdd);
+    if (G == 0.0) return 1;
+  } else if (Fd == 0.0) {
+    return 1;
+  }
   /* phase psi = 2 pi g (t_k + x) - Phi_V(t_k + x) - sgn(Fdot) pi / 4 in double-double */
   dd_t tt = two_sum(T->t[k], x);
   dd_t gt = dd_mul_d(tt, g);
@@ -308,7 +386,7 @@ static int contrib(const traj_t* T, const voice_t* V, int k, const double* fc, d
   dd_t PV = dd_add(dd_mul_d(Pp, (double)V->m), dd_mul_d(Pr, (double)V->n));
   dd_t psi = dd_add(wgt, dd_neg(PV));
   dd_t qpi; qpi.hi = OR_QPI_HI; qpi.lo = OR_QPI_LO;
-  psi = dd_add(psi, Fd > 0.0 ? dd_neg(qpi) : qpi);
+  if (!ext) psi = dd_add(psi, Fd > 0.0 ? dd_neg(qpi) : qpi);
   /* reduce modulo 2 pi */
   double kk = nearbyint(psi.hi / OR_TWO_PI_HI);
   psi = dd_add(psi, dd_neg(dd_mul_d(twopi, kk)));
@@ -318,6 +396,12 @@ static int contrib(const traj_t* T, const voice_t* V, int k, const double* fc, d
   double are = cubic(V->are + 4 * k, x), aim = cubic(V->aim + 4 * k, x);
   double hr = T->prefactor * (are * V->Y[0] - aim * V->Y[1]);
   double hi = T->prefactor * (are * V->Y[1] + aim * V->Y[0]);
+  if (ext) {
+    const double complex z = (hr + I * hi) * (cs + I * sn) * G;
+    acc[0] += creal(z);
+    acc[1] += cimag(z);
+    return 0;
+  }
   double w = 1.0 / sqrt(fabs(Fd));
   acc[0] += w * (hr * cs - hi * sn);
   acc[1] += w * (hr * sn + hi * cs);
@@ -364,7 +448,7 @@ static piece_t* build_pieces(const traj_t* T, const voice_t* V, int nv, const do
 /* shared set-up: splines, voices, monotone pieces                     */
 /* ------------------------------------------------------------------ */
 typedef struct {
-  int K, nm, nv, conj;
+  int K, nm, nv, conj, ext;
   spl_sys_t S;
   double* cf;          /* fundamental spline coef: Phi_phi, Phi_r, Om_phi, Om_r, each [K-1][4] */
   double* ac;          /* voice amplitude coef: per voice Re [K-1][4] then Im [K-1][4] */
@@ -457,7 +541,7 @@ static void ctx_forward(const ctx_t* c, long long nf, const double* freqs, doubl
         for (long long b = lo; b < hi; b++) {
           double g = sgn ? -freqs[b] : freqs[b];
           double x = bisect(fc, g, p->ta, p->tb, p->dir);
-          nzero += contrib(&c->T, v, p->seg, fc, g, x, H + 2 * b);
+          nzero += contrib(&c->T, v, p->seg, fc, g, x, c->ext, H + 2 * b);
           nev++;
         }
       }
@@ -478,21 +562,25 @@ static void ctx_forward(const ctx_t* c, long long nf, const double* freqs, doubl
  *   K knots t[K]; phi_phi, phi_r, omega_phi, omega_r [K];
  *   nm modes l, m, n [nm]; amp [nm][K][2] (re, im interleaved);
  *   theta, phi, prefactor; conj_partners (0/1);
+ *   spa_form: 0 standard SPA (item 4), 1 extended SPA (item 4');
  *   nf ascending freqs (> 0); outputs hp, hc [nf][2];
- *   stats[0] = contributions evaluated, stats[1] = roots with Fdot == 0,
+ *   stats[0] = contributions evaluated, stats[1] = roots with no contribution
+ *   (Fdot == 0 in the standard form; Fdot == Fddot == 0 in the extended form),
  *   stats[2] = number of monotone pieces.
  * Returns 0 on success, < 0 on bad input.
  */
 int oracle_sum_modes(int K, const double* t, const double* phi_phi, const double* phi_r,
                      const double* omega_phi, const double* omega_r,
                      int nm, const int* l, const int* m, const int* n, const double* amp,
-                     double theta, double phi, double prefactor, int conj_partners,
+                     double theta, double phi, double prefactor, int conj_partners, int spa_form,
                      long long nf, const double* freqs, double* hp, double* hc,
                      long long* stats, int nthreads) {
   ctx_t c;
+  if (spa_form != 0 && spa_form != 1) return -1;
   int rc = ctx_init(&c, K, t, phi_phi, phi_r, omega_phi, omega_r, nm, l, m, n, amp, theta, phi, prefactor,
                     conj_partners, nf, freqs);
   if (rc) { ctx_free(&c); return rc; }
+  c.ext = spa_form;
   ctx_forward(&c, nf, freqs, hp, hc, stats, nthreads);
   ctx_free(&c);
   return 0;

@@ -48,8 +48,10 @@ def lib():
         L.oracle_swsh.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, dp]
         L.oracle_swsh.restype = None
         L.oracle_sum_modes.argtypes = [C.c_int, dp, dp, dp, dp, dp, C.c_int, ip, ip, ip, dp,
-                                       C.c_double, C.c_double, C.c_double, C.c_int,
+                                       C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
                                        C.c_longlong, dp, dp, dp, C.POINTER(C.c_longlong), C.c_int]
+        L.oracle_ext_factor.argtypes = [C.c_longlong, dp, dp, dp]
+        L.oracle_ext_factor.restype = None
         L.oracle_sum_modes.restype = C.c_int
         L.oracle_loglike_grad.argtypes = [C.c_int, dp, dp, dp, dp, dp, C.c_int, ip, ip, ip, dp,
                                           C.c_double, C.c_double, C.c_double, C.c_int,
@@ -92,9 +94,26 @@ def default_threads():
     return max(1, min(os.cpu_count() or 1, 64))
 
 
-def sum_modes(w, freqs=None, conj_partners=True, nthreads=None, return_stats=False):
+SPA_FORMS = {"standard": 0, "extended": 1}
+
+
+def ext_factor(Fd, Fdd):
+    """Extended-SPA time integral G(Fdot, Fddot) of one root (Eq. 10, sign reading
+    of the oracle source), complex128, elementwise."""
+    Fd = np.atleast_1d(np.asarray(Fd, np.float64))
+    Fdd = np.broadcast_to(np.asarray(Fdd, np.float64), Fd.shape)
+    a, ap = _d(Fd.ravel())
+    b, bp = _d(np.ascontiguousarray(Fdd).ravel())
+    out = np.zeros(2 * a.shape[0])
+    o, op = _d(out)
+    lib().oracle_ext_factor(a.shape[0], ap, bp, op)
+    return o.view(np.complex128).reshape(Fd.shape)
+
+
+def sum_modes(w, freqs=None, conj_partners=True, nthreads=None, return_stats=False, spa="standard"):
     """SPA sum of one synthetic waveform ``w`` (see synth.Waveform) on ``freqs``
-    (default: w.freqs).  Returns (h_plus, h_cross) complex128 arrays."""
+    (default: w.freqs); ``spa`` is "standard" (Fresnel integral per root) or
+    "extended" (Eq. 10 per root).  Returns (h_plus, h_cross) complex128 arrays."""
     f = w.freqs if freqs is None else freqs
     f, fp = _d(f)
     t, tp = _d(w.t)
@@ -114,7 +133,7 @@ def sum_modes(w, freqs=None, conj_partners=True, nthreads=None, return_stats=Fal
     st = (C.c_longlong * 4)()
     rc = lib().oracle_sum_modes(t.shape[0], tp, p1, p2, p3, p4, l.shape[0], lp, mp, np_, ap,
                                 float(w.theta), float(w.phi), float(w.prefactor), int(conj_partners),
-                                f.shape[0], fp, hpptr, hccptr, st,
+                                SPA_FORMS[spa], f.shape[0], fp, hpptr, hccptr, st,
                                 int(nthreads or default_threads()))
     if rc:
         raise ValueError("oracle_sum_modes rejected the input: %d" % rc)
