@@ -255,26 +255,43 @@ def run_paper(args, rank, world, local):
     achieved = FP64_FLOPS_PER_MODE_BIN * mb_per_launch / spa_s / 1e12
     issue = FP64_OPS_PER_MODE_BIN * mb_per_launch / spa_s / (FP64_PER_CLK_PER_SM * n_sms * clk_hz)
 
-    mixed = None
-    if args.precision == "fp64" and not args.no_mixed:
-        # the mixed form on the same waveforms and bins, for the speed-up the metric quotes
-        mplan = api.Plan("mixed", conj_partners=True, max_waveforms=1, max_knots=200, max_modes_total=2000,
-                         max_bins_total=nf, tile_bins=args.tile_bins)
-        mout = (torch.empty(nf, dtype=torch.complex64, device="cuda"), torch.empty(nf, dtype=torch.complex64, device="cuda"))
+    def other_form(prec, spa="standard"):
+        # another form on the same waveforms and bins: its rate, its speed-up over this
+        # FP64 run and its relative L2 difference from this run's FP64 output
+        oplan = api.Plan(prec, conj_partners=True, max_waveforms=1, max_knots=200, max_modes_total=2000,
+                         max_bins_total=nf, tile_bins=64 if prec in ("fp64x", "mixed") else args.tile_bins, spa=spa)
+        oout = (torch.empty(nf, dtype=oplan.out_dtype, device="cuda"), torch.empty(nf, dtype=oplan.out_dtype, device="cuda"))
         for i in range(args.warmup):
-            mplan.sum_modes(dev[i % nw], out=mout, check=False)
-        mplan.sync()
-        mms = event_time(mplan.stream, lambda i: mplan.sum_modes(dev[i % nw], out=mout, check=False), args.steps)
-        mplan.sync()
-        # accuracy of the mixed form against this run's FP64 output of the same waveform
+            oplan.sum_modes(dev[i % nw], out=oout, check=False)
+        oplan.sync()
+        oplan.profile(True)
+        oms = event_time(oplan.stream, lambda i: oplan.sum_modes(dev[i % nw], out=oout, check=False), args.steps)
+        oplan.sync()
+        ost = oplan.stats()
         plan.sum_modes(dev[0], out=outs[0])
-        mplan.sum_modes(dev[0], out=mout)
-        num = (torch.linalg.vector_norm(mout[0].to(torch.complex128) - outs[0][0]) ** 2 +
-               torch.linalg.vector_norm(mout[1].to(torch.complex128) - outs[0][1]) ** 2)
+        oplan.sum_modes(dev[0], out=oout)
+        num = (torch.linalg.vector_norm(oout[0].to(torch.complex128) - outs[0][0]) ** 2 +
+               torch.linalg.vector_norm(oout[1].to(torch.complex128) - outs[0][1]) ** 2)
         den = torch.linalg.vector_norm(outs[0][0]) ** 2 + torch.linalg.vector_norm(outs[0][1]) ** 2
-        mixed = {"value": world * args.steps / (mms * 1e-3), "unit": "waveforms/s", "ms_per_step": mms / args.steps,
-                 "speedup_vs_fp64": ms / mms, "rel_l2_vs_fp64": float(torch.sqrt(num / den))}
-        mplan.close()
+        oplan.close()
+        return {"value": world * args.steps / (oms * 1e-3), "unit": "waveforms/s", "ms_per_step": oms / args.steps,
+                "spa_kernel_ms": ost["spa_ns"] * 1e-6 / max(1, ost["timed_calls"]),
+                "prep_ms": ost["prep_ns"] * 1e-6 / max(1, ost["timed_calls"]),
+                "mode_bin_evals_per_s": world * mb / (oms * 1e-3),
+                "speedup_vs_fp64": ms / oms, "rel_l2_vs_fp64": float(torch.sqrt(num / den)),
+                "tile_bins": 64 if prec in ("fp64x", "mixed") else args.tile_bins}
+
+    mixed = fp64x = ext = None
+    if args.precision == "fp64" and not args.no_mixed:
+        fp64x = other_form("fp64x")
+        fp64x["arithmetic"] = "FP32 pairs (double-float) and integers; FP64 only per tile and in preparation"
+        mixed = other_form("mixed")
+        # the extended SPA (Eq. 10): its cost over the standard form, per precision
+        ext = {}
+        for prec in ("fp64", "fp64x", "mixed"):
+            e = other_form(prec, spa="extended")
+            e["rel_l2_vs_standard_fp64"] = e.pop("rel_l2_vs_fp64")   # the size of the correction
+            ext[prec] = e
 
     e2e = None
     if not args.no_e2e:
@@ -318,7 +335,7 @@ def run_paper(args, rank, world, local):
                          "issue_frac": issue,
                          "note": "FP64 pipe: %d FP64 flops (%d FP64 instructions) per mode-bin; peak = %d FP64 FMA/clk/SM x 2 x SMs x median SM clock" % (
                              FP64_FLOPS_PER_MODE_BIN, FP64_OPS_PER_MODE_BIN, FP64_PER_CLK_PER_SM)},
-            "mixed_form": mixed, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"], "clocks": clocks})
+            "fp64x_form": fp64x, "mixed_form": mixed, "extended_spa": ext, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"], "clocks": clocks})
         line["config"].update({"waveforms_resident": nw, "tile_bins": args.tile_bins,
                                "l2": "inputs larger than L2: %d resident waveforms rotated, ~200 MB touched per step" % nw})
         print(json.dumps(line), flush=True)

@@ -75,6 +75,23 @@ typedef enum {
 
 enum { EMRI_FD_FP64 = 0, EMRI_FD_MIXED = 1, EMRI_FD_FP64X = 2 };
 
+/* Per-root time integral of the SPA sum (Sec. 2.2).
+ * EMRI_FD_SPA_STANDARD: the phase expanded to second order about each root
+ *   (Eq. 4) and the Fresnel integral done exactly:
+ *   exp(-i sgn(Fdot) pi/4) / sqrt|Fdot|; a root with Fdot == 0 contributes 0.
+ * EMRI_FD_SPA_EXTENDED: the phase expanded to third order (Eq. 7-9) and the
+ *   integral taken in closed form (Eq. 10):
+ *   -(2/sqrt 3) (i Fdot/|Fddot|) e^z K_{1/3}(z),  z = -2 pi i Fdot^3/(3 Fddot^2),
+ *   principal branch.  The leading minus sign is a reading of Eq. 10: with it
+ *   the factor tends to the standard one as Fddot -> 0, and the two roots of
+ *   a cubic phase add up to its exact (Airy) Fourier transform.  It is finite
+ *   at turnovers (Fdot -> 0); a root with Fdot == 0 exactly (a double root)
+ *   contributes the limit of the two-root sum,
+ *   2 pi^{2/3} / (3^{2/3} Gamma(2/3)) |Fddot|^{-1/3} with no pi/4 phase.
+ *   K_{1/3} is evaluated to about 3e-12 relative (FP64 and FP64X plans) or
+ *   FP32 precision (mixed plans).  Not available with likelihood = 1. */
+enum { EMRI_FD_SPA_STANDARD = 0, EMRI_FD_SPA_EXTENDED = 1 };
+
 #define EMRI_FD_MAX_L 20
 
 typedef struct {
@@ -93,8 +110,10 @@ typedef struct {
   long long max_bins_total; /* sum of N_f over a call, >= 1 */
   int tile_bins;            /* output bins per work tile: 32, 64 or 128; 0 = default (128) */
   int likelihood;           /* 1: also allocate the scratch of emri_fd_loglike_and_grad
-                               (FP64 plans only); 0: that call returns EMRI_FD_ERR_ARG */
-  int reserved[6];          /* must be zero */
+                               (FP64 standard-form plans only); 0: that call returns
+                               EMRI_FD_ERR_ARG */
+  int spa_form;             /* EMRI_FD_SPA_STANDARD (0) or EMRI_FD_SPA_EXTENDED (1), below */
+  int reserved[5];          /* must be zero */
 } emri_fd_desc;
 
 /*

@@ -33,7 +33,9 @@ class emri_fd_desc(C.Structure):
     _fields_ = [("precision", C.c_int), ("conj_partners", C.c_int), ("max_waveforms", C.c_int),
                 ("max_knots", C.c_int), ("max_knots_total", C.c_longlong), ("max_modes_total", C.c_longlong),
                 ("max_bins_total", C.c_longlong), ("tile_bins", C.c_int), ("likelihood", C.c_int),
-                ("reserved", C.c_int * 6)]
+                ("spa_form", C.c_int), ("reserved", C.c_int * 5)]
+
+SPA_FORMS = {"standard": 0, "extended": 1}
 
 
 _lib = None
@@ -195,12 +197,13 @@ def _addr(x):
 class Plan:
     """A plan of the C library bound to a torch CUDA stream.
 
-    precision: "fp64" (complex128 outputs) or "mixed" (complex64 outputs).
+    precision: "fp64" or "fp64x" (complex128 outputs) or "mixed" (complex64 outputs).
+    spa: "standard" (Fresnel integral per root) or "extended" (Eq. 10 per root).
     Batches are dicts in the layout of synth.concat (numpy or torch)."""
 
     def __init__(self, precision="fp64", conj_partners=True, max_waveforms=1, max_knots=200,
                  max_modes_total=4096, max_bins_total=1 << 22, max_knots_total=0, tile_bins=0,
-                 likelihood=False, device=None, stream=None):
+                 likelihood=False, device=None, stream=None, spa="standard"):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -216,6 +219,8 @@ class Plan:
         d.max_bins_total = int(max_bins_total)
         d.tile_bins = int(tile_bins)
         d.likelihood = int(bool(likelihood))
+        d.spa_form = SPA_FORMS[spa]
+        self.spa = spa
         self.desc = d
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -206,6 +206,7 @@ struct DevScratch {
   SegAmp32* amp32;
   SegFF* segff;                   // FP64X plans
   SegCrit* crit;
+  double* yk;                     // [sum N_m (K-1)] 3/(2 pi h), extended FP64 plans
   long long* keyF;                // [sum N_m K]
   int* run_cnt;                   // [sum N_m + 1], exclusive-scanned in place
   Run* runs;
@@ -242,6 +243,7 @@ struct CallShape {
   int tile_bins;
   int conj;
   int precision;
+  int ext;          // 1: extended SPA (Eq. 10)
 };
 
 constexpr int kPrepKernels = 12;   // kernels launched by launch_prep (memsets excluded)

@@ -111,8 +111,11 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
       d->max_bins_total > 2000000000LL || d->max_knots_total < 0 ||
       !(d->tile_bins == 0 || d->tile_bins == 32 || d->tile_bins == 64 || d->tile_bins == 128))
     return EMRI_FD_ERR_ARG;
-  for (int i = 0; i < 6; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
-  if (d->likelihood != 0 && (d->likelihood != 1 || d->precision != EMRI_FD_FP64)) return EMRI_FD_ERR_ARG;
+  for (int i = 0; i < 5; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
+  if (d->spa_form != EMRI_FD_SPA_STANDARD && d->spa_form != EMRI_FD_SPA_EXTENDED) return EMRI_FD_ERR_ARG;
+  if (d->likelihood != 0 &&
+      (d->likelihood != 1 || d->precision != EMRI_FD_FP64 || d->spa_form != EMRI_FD_SPA_STANDARD))
+    return EMRI_FD_ERR_ARG;
   emri_fd_plan_s* p = new emri_fd_plan_s();
   p->desc = *d;
   if (p->desc.tile_bins == 0) p->desc.tile_bins = 128;
@@ -144,6 +147,7 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
   else if (d->precision == EMRI_FD_MIXED) { AL(s.amp32, p->cap_seg); }
   else { AL(s.segff, p->cap_seg); AL(s.tabf, kTabN); }
   AL(s.crit, p->cap_seg);
+  if (d->spa_form == EMRI_FD_SPA_EXTENDED && d->precision == EMRI_FD_FP64) { AL(s.yk, p->cap_seg); }
   AL(s.keyF, p->cap_amp);
   AL(s.run_cnt, p->cap_nm + 1);
   AL(s.runs, s.run_cap);
@@ -205,6 +209,7 @@ emri_fd_status prepare_call(emri_fd_plan_s* p, int n_wf, const long long* knot_o
   cs.tile_bins = TB;
   cs.conj = p->desc.conj_partners;
   cs.precision = p->desc.precision;
+  cs.ext = p->desc.spa_form;
   long long amp_base = 0, seg_base = 0, tiles = 0;
   int maxK = 0;
   for (int w = 0; w < n_wf; w++) {

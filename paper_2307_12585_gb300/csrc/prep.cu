@@ -382,7 +382,8 @@ __device__ __forceinline__ void put_ff(float* dst, double x) {
 }
 
 __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, DevInputs in, const FundSeg* fund, const double* ampM, long long seg_total, SegCore* core,
-                           SegAmp64* amp64, SegAmp32* amp32, SegFF* segff, SegCrit* crit, long long* keyF) {
+                           SegAmp64* amp64, SegAmp32* amp32, SegFF* segff, SegCrit* crit, long long* keyF,
+                           double* yk) {
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= seg_total) return;
   int lo = 0, hi = n_wf - 1;
@@ -417,6 +418,7 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
   C.theta0 = (unsigned long long)(long long)m * (Fs.q[0] - Fs.q[2]) + (unsigned long long)(long long)n * Fs.q[1];
   C.bf = (float)C.b; C.cf = (float)C.c; C.df = (float)C.d; C.pad = 0.f;
   core[r] = C;
+  if (yk) yk[r] = 0.47746482927568600731 / h;   // 3/(2 pi h), extended SPA
 
   // amplitude, scaled by prefactor sqrt(h) (the weight is sqrt(h)/sqrt|dF/du|)
   double sc = in.prefactor[lo] * sqrt(h);
@@ -789,7 +791,7 @@ void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, 
   k_seg_prep<<<(unsigned)((cs.seg_total + 127) / 128), 128, 0, st>>>(
       cs.n_wf, s.wf, s.modes, in, s.fund, s.ampM, cs.seg_total, s.core,
       cs.precision == 0 ? s.amp64 : nullptr, cs.precision == 1 ? s.amp32 : nullptr,
-      cs.precision == 2 ? s.segff : nullptr, s.crit, s.keyF);
+      cs.precision == 2 ? s.segff : nullptr, s.crit, s.keyF, cs.ext && cs.precision == 0 ? s.yk : nullptr);
   unsigned wblocks = (unsigned)((cs.nm_total * 32 + 255) / 256);
   k_runs<false><<<wblocks, 256, 0, st>>>(s.wf, s.modes, cs.nm_total, s.core, s.crit, s.keyF, nullptr, nullptr,
                                          nullptr, s.run_cap, s.run_cnt, s.status);

@@ -14,6 +14,8 @@
 //   a9  the amplitude cubic;
 //   a10 the voice value A w e^{i psi} times the polarisation weights;
 //   a11 accumulation in registers in a fixed order, one store per bin.
+// Extended plans (EXT) multiply each root's standard factor by the ratio R(X)
+// of the extended SPA (Eq. 10; see ext_spa.cuh).
 //
 // Work decomposition: a persistent grid takes tiles of 32*BPL consecutive bins
 // from a queue.  A tile's (run, sign) entries are collected in shared memory
@@ -22,6 +24,7 @@
 // so every bin's sum has a fixed order (no atomics on the outputs).
 #include "spa_math.cuh"
 #include "ff.cuh"
+#include "ext_spa.cuh"
 
 namespace emrifd {
 namespace {
@@ -43,6 +46,7 @@ struct SpaParams {
   const double2* tab;
   const float4* tabf;
   const double* prefactor;
+  const double* yk;                 // [segments] 3/(2 pi h), extended plans
   unsigned long long* counters;
   const int* status;
   long long tiles_total;
@@ -60,6 +64,7 @@ struct Smem {
 
 // FP64X per-(branch, bin) body: returns the four increments (h+ re, h+ im,
 // hx re, hx im) as FP32 pairs in v[0..7]; false if the root has Fdot == 0
+template <bool EXT>
 __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, double f, ff fx, bool neg, ff ulo, ff uhi,
                                            int dir, ff fa, ff fb, const float4* tabf, float* v) {
   const ff Ax = ff_make(X.A[0], X.A[1]), bx = ff_make(X.b[0], X.b[1]), cx_ = ff_make(X.c[0], X.c[1]),
@@ -92,16 +97,48 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
     kap = fabsf(__fdividef(C.cf + 3.f * C.df * ufc, Dc));
     err = stp * (kap * stp + 4.8e-7f);
   }
-  if (ff_lt(u, ulo)) u = ulo;
-  else if (ff_lt(uhi, u)) u = uhi;
+  bool settle = err > 1e-13f;
+  if (ff_lt(u, ulo)) { u = ulo; settle = true; }
+  else if (ff_lt(uhi, u)) { u = uhi; settle = true; }
+  if (settle) {   // rare: next to a turnover, or a root at the piece's end
+    const double ud = solve_root_safe(C, (neg ? -f : f) - C.A, ff_to_double(ulo), ff_to_double(uhi), dir,
+                                      ff_to_double(u));
+    u = ff_from_double(ud);
+  }
   // a8: dF/du and 1/sqrt|dF/du| (rsqrtf seed, one Newton step in pairs)
   const ff D = ff_add(ff_mul(ff_add(ff_mul(ff_make(X.d3[0], X.d3[1]), u), ff_make(X.c2[0], X.c2[1])), u), bx);
-  if (D.hi == 0.f) return false;
+  bool coal = D.hi == 0.f;   // a double root: no contribution, or (extended) the coalesced limit
+  if (!EXT && coal) return false;
   const bool pos = D.hi > 0.f;
   const ff Da = pos ? D : ff_neg(D);
-  const float y0 = rsqrtf(Da.hi);
-  const ff ee = ff_mul_f(ff_mul_f(Da, y0), y0);
-  const ff wgt = ff_mul_f(ff_add_f(ff_mul_f(ee, -0.5f), 1.5f), y0);
+  // extended form: y = 1/X in FP32 where |y| <= 1e-4, else in FP64
+  float yf = 0.f;
+  double yd = 0.0, D2d = 0.0;
+  bool slow = false;
+  if constexpr (EXT) {
+    const float D2f = fmaf(2.f * X.d3[0], u.hi, X.c2[0]);
+    const float r0 = rsqrtf(Da.hi), r2 = r0 * r0;
+    yf = __fdividef((float)kExt3Over2Pi, X.h[0]) * D2f * D2f * (r2 * r2 * r2);
+    if (!pos) yf = -yf;
+    if (coal || !(fabsf(yf) <= 1e-4f)) {
+      slow = true;
+      D2d = fma(2.0 * C.d3, ff_to_double(u), C.c2);
+      if (!coal) {
+        yd = ext_y(ff_to_double(D), D2d, C.h);
+        if (!(fabs(yd) < INFINITY)) coal = true;
+      }
+    }
+  }
+  ff wgt;
+  if (coal) {
+    const double m0 = ext_coalesced(D2d, C.h);
+    if (m0 == 0.0) return false;
+    wgt = ff_from_double(m0);
+  } else {
+    const float y0 = rsqrtf(Da.hi);
+    const ff ee = ff_mul_f(ff_mul_f(Da, y0), y0);
+    wgt = ff_mul_f(ff_add_f(ff_mul_f(ee, -0.5f), 1.5f), y0);
+  }
   // a7: phase, Q0.64 turns
   const ff dh = ff_mul(dl, ff_make(X.h[0], X.h[1]));
   const ff inner = ff_add(ff_mul(ff_add(ff_mul(ff_make(X.P3[0], X.P3[1]), u), ff_make(X.P2[0], X.P2[1])), u),
@@ -109,7 +146,7 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
   const ff inseg = ff_mul(ff_sub(dh, inner), u);
   const unsigned long long ft = q64_mul(f, C.ts);           // f t_s; the branch sign is applied here
   unsigned long long Th = (neg ? 0ull - ft : ft) - C.theta0 + q64_of_float(inseg.hi) + q64_of_float(inseg.lo);
-  Th += pos ? (0ull - (1ull << 61)) : (1ull << 61);
+  if (!coal) Th += pos ? (0ull - (1ull << 61)) : (1ull << 61);
   // e^{2 pi i Th/2^64}: table entry times (1 - x^2/2) + i (x - x^3/6), |x| <= pi/4096
   const unsigned long long kq = (Th + (1ull << (63 - kTabBits))) >> (64 - kTabBits);
   const long long rr = (long long)(Th - (kq << (64 - kTabBits))) >> 8;   // units of 2^-56 turn
@@ -131,6 +168,24 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
   }
   ar = ff_mul(ar, wgt);
   ai = ff_mul(ai, wgt);
+  if constexpr (EXT) {
+    if (!coal) {
+      if (!slow) {   // R = 1 + delta, |delta| <= 7e-6: the correction in FP32
+        float dr, di;
+        ext_delta_f32(yf, dr, di);
+        const float cr = ar.hi * dr - ai.hi * di, ci = ar.hi * di + ai.hi * dr;
+        ar = ff_add_f(ar, cr);
+        ai = ff_add_f(ai, ci);
+      } else {
+        double rr, ri;
+        ext_ratio(yd, rr, ri);
+        const ff Rr = ff_from_double(rr), Ri = ff_from_double(ri);
+        const ff nr = ff_sub(ff_mul(ar, Rr), ff_mul(ai, Ri));
+        ai = ff_add(ff_mul(ar, Ri), ff_mul(ai, Rr));
+        ar = nr;
+      }
+    }
+  }
   const ff zr = ff_sub(ff_mul(ar, er), ff_mul(ai, ei));
   const ff zi = ff_add(ff_mul(ar, ei), ff_mul(ai, er));
   // a11: h+ += alpha Z (conj Z for F < 0), hx += i beta Z (-i beta conj Z)
@@ -142,6 +197,7 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
 
 // mixed per-(branch, bin) body: FP64 root polish and in-segment phase, FP32
 // weight, sincos, amplitude and products; increments in v[0..3]
+template <bool EXT>
 __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am, double f, bool neg, double ulo,
                                            double uhi, int dir, float fa, float fb, float* v) {
   const double g = neg ? -f : f;
@@ -150,9 +206,47 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
   const double u = solve_root<4>(C, delta, ulo, uhi, dir, uf, Df);
   const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
   const long long Dbits = __double_as_longlong(Dd);
-  if ((Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0) return false;
-  const unsigned long long Th = phase_q64(C, g, delta, u, Dbits >= 0);
-  const float wgt = rsqrtf(fabsf(Df));
+  bool coal = (Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0;
+  if (!EXT && coal) return false;
+  const bool pos = Dbits >= 0;
+  float wgt = rsqrtf(fabsf(Df));
+  float rr = 1.f, ri = 0.f;
+  if constexpr (EXT) {
+    // extended form: R in FP32 where |y| <= 1e-2, else in FP64
+    float yf = 0.f;
+    if (!coal) {
+      const float D2f = fmaf(2.f * C.df * 3.f, uf, 2.f * C.cf);
+      const float r2 = wgt * wgt;
+      yf = __fdividef((float)kExt3Over2Pi, d2f_bits(C.h)) * D2f * D2f * (r2 * r2 * r2);
+      if (!pos) yf = -yf;
+    }
+    if (!coal && fabsf(yf) <= 1e-2f) {
+      float dr, di;
+      ext_delta_f32(yf, dr, di);
+      rr = 1.f + dr;
+      ri = di;
+    } else {
+      const double D2d = fma(2.0 * C.d3, u, C.c2);
+      double y = 0.0;
+      if (!coal) {
+        y = ext_y(Dd, D2d, C.h);
+        if (!(fabs(y) < INFINITY)) coal = true;
+      }
+      if (coal) {
+        const double m0 = ext_coalesced(D2d, C.h);
+        if (m0 == 0.0) return false;
+        wgt = (float)m0;
+      } else {
+        double r0, r1;
+        ext_ratio(y, r0, r1);
+        rr = (float)r0;
+        ri = (float)r1;
+        wgt = (float)(1.0 / sqrt(fabs(Dd)));   // |y| > 1e-2: near a turnover, where FP32 dF/du is too coarse
+      }
+    }
+  }
+  unsigned long long Th = phase_q64(C, g, delta, u, pos);
+  if (coal) Th += pos ? (1ull << 61) : (0ull - (1ull << 61));
   // half-turns in [-1, 1) from the top 46 bits of Th, without conversion instructions
   const long long ts_ = (long long)Th;
   const float th = small_int_to_float((int)(ts_ >> 42)) * 4.76837158203125e-07f +              // 2^-21
@@ -163,13 +257,18 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
   float aim = ((Am.im[3] * uf + Am.im[2]) * uf + Am.im[1]) * uf + Am.im[0];
   are *= wgt;
   aim *= wgt;
+  if constexpr (EXT) {
+    const float nr = are * rr - aim * ri;
+    aim = are * ri + aim * rr;
+    are = nr;
+  }
   const float zr = are * cs - aim * sn;
   const float zi = are * sn + aim * cs;
   v[0] = fa * zr; v[1] = (neg ? -fa : fa) * zi; v[2] = -fb * zi; v[3] = (neg ? -fb : fb) * zr;
   return true;
 }
 
-template <int BPL, int PREC>
+template <int BPL, int PREC, bool EXT>
 __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : 4) k_spa(SpaParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<BPL, PREC>& S = *reinterpret_cast<Smem<BPL, PREC>*>(smem_raw);
@@ -280,11 +379,29 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : 4) k_spa(SpaParams P
             // a8: dF/du and the weight sqrt(h)/sqrt|dF/du| (sqrt(h) is in the amplitude)
             const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
             const long long Dbits = __double_as_longlong(Dd);
-            if ((Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0) continue;   // Fdot == 0: no contribution
+            bool coal = (Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0;   // Fdot == 0
+            if (!EXT && coal) continue;                         // standard form: no contribution
             const bool pos_slope = Dbits >= 0;
-            // a7: phase in Q0.64 turns
-            const unsigned long long Th = phase_q64(C, g, delta, u, pos_slope);
-            const double wgt = rsqrt_abs(Dd);
+            double wgt = coal ? 0.0 : rsqrt_abs(Dd);
+            double rr = 1.0, ri = 0.0;
+            if constexpr (EXT) {
+              // extended form: R(X) from y = 1/X = 3 (d2F/du2)^2 / (2 pi h (dF/du)^3)
+              const double D2 = fma(2.0 * C.d3, u, C.c2);
+              if (!coal) {
+                const double w2 = wgt * wgt;
+                double y = P.yk[M.seg_base + s] * (D2 * D2) * (w2 * w2 * w2);
+                if (!pos_slope) y = -y;
+                if (fabs(y) < INFINITY) ext_ratio(y, rr, ri);
+                else coal = true;
+              }
+              if (coal) {
+                wgt = ext_coalesced(D2, C.h);
+                if (wgt == 0.0) continue;
+              }
+            }
+            // a7: phase in Q0.64 turns (a double root of the extended form has no pi/4 shift)
+            unsigned long long Th = phase_q64(C, g, delta, u, pos_slope);
+            if (EXT && coal) Th += pos_slope ? (1ull << 61) : (0ull - (1ull << 61));
             double er, ei;
             cis_q64(Th, S.tab, er, ei);
             // a9-a10
@@ -293,6 +410,11 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : 4) k_spa(SpaParams P
             double aim = fma(u, fma(u, fma(u, Am.im[3], Am.im[2]), Am.im[1]), Am.im[0]);
             are *= wgt;
             aim *= wgt;
+            if constexpr (EXT) {
+              const double nr = fma(are, rr, -aim * ri);
+              aim = fma(are, ri, aim * rr);
+              are = nr;
+            }
             const double zr = fma(are, er, -aim * ei);
             const double zi = fma(are, ei, aim * er);
             // a11: positive branch h+ += alpha Z, hx += i beta Z;
@@ -323,11 +445,11 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : 4) k_spa(SpaParams P
             float v[8];
             bool ok;
             if constexpr (PREC == 2) {
-              ok = body_fp64x(C, P.segff[M.seg_base + s], fqq, fx, neg, s == R.s0 ? u0x : ff_make(0.f, 0.f),
+              ok = body_fp64x<EXT>(C, P.segff[M.seg_base + s], fqq, fx, neg, s == R.s0 ? u0x : ff_make(0.f, 0.f),
                               s == R.s1 ? u1x : ff_make(1.f, 0.f), R.dir, fa, fb, P.tabf, v);
             } else {
               const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
-              ok = body_mixed(C, P.amp32[M.seg_base + s], fqq, neg, ulo, uhi, R.dir, M.af[0], M.bf[0], v);
+              ok = body_mixed<EXT>(C, P.amp32[M.seg_base + s], fqq, neg, ulo, uhi, R.dir, M.af[0], M.bf[0], v);
             }
             if (!ok) continue;
 #pragma unroll
@@ -386,16 +508,33 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : 4) k_spa(SpaParams P
   }
 }
 
-template <int BPL, int PREC>
+template <int BPL, int PREC, bool EXT>
 void launch_one(const SpaParams& p, int num_sms, cudaStream_t st) {
   size_t sm = sizeof(Smem<BPL, PREC>);
-  cudaFuncSetAttribute(k_spa<BPL, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_spa<BPL, PREC, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spa<BPL, PREC>, kThreads, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spa<BPL, PREC, EXT>, kThreads, sm);
   if (per_sm < 1) per_sm = 1;
   long long grid = (long long)num_sms * per_sm;
   if (grid > p.tiles_total) grid = p.tiles_total > 0 ? p.tiles_total : 1;
-  k_spa<BPL, PREC><<<(unsigned)grid, kThreads, sm, st>>>(p);
+  k_spa<BPL, PREC, EXT><<<(unsigned)grid, kThreads, sm, st>>>(p);
+}
+
+template <bool EXT>
+void launch_prec(const SpaParams& p, int bpl, int precision, int num_sms, cudaStream_t st) {
+  if (precision == 0) {
+    if (bpl == 1) launch_one<1, 0, EXT>(p, num_sms, st);
+    else if (bpl == 4) launch_one<4, 0, EXT>(p, num_sms, st);
+    else launch_one<2, 0, EXT>(p, num_sms, st);
+  } else if (precision == 2) {
+    if (bpl == 1) launch_one<1, 2, EXT>(p, num_sms, st);
+    else if (bpl == 4) launch_one<4, 2, EXT>(p, num_sms, st);
+    else launch_one<2, 2, EXT>(p, num_sms, st);
+  } else {
+    if (bpl == 1) launch_one<1, 1, EXT>(p, num_sms, st);
+    else if (bpl == 4) launch_one<4, 1, EXT>(p, num_sms, st);
+    else launch_one<2, 1, EXT>(p, num_sms, st);
+  }
 }
 
 }  // namespace
@@ -405,22 +544,11 @@ void launch_spa(const CallShape& cs, const DevInputs& in, const DevScratch& s, i
   p.wf = s.wf; p.n_wf = cs.n_wf; p.modes = s.modes; p.core = s.core; p.amp64 = s.amp64; p.amp32 = s.amp32;
   p.keyF = s.keyF; p.runs = s.runs; p.rb = s.rbins; p.freqs = in.freqs; p.hp = in.h_plus; p.hc = in.h_cross;
   p.tab = s.tab; p.counters = s.counters; p.status = s.status; p.tiles_total = cs.tiles_total;
-  p.segff = s.segff; p.tabf = s.tabf; p.prefactor = in.prefactor;
+  p.segff = s.segff; p.tabf = s.tabf; p.prefactor = in.prefactor; p.yk = s.yk;
   cudaMemsetAsync(s.counters, 0, sizeof(unsigned long long), st);
   const int bpl = cs.tile_bins / 32;
-  if (cs.precision == 0) {
-    if (bpl == 1) launch_one<1, 0>(p, num_sms, st);
-    else if (bpl == 4) launch_one<4, 0>(p, num_sms, st);
-    else launch_one<2, 0>(p, num_sms, st);
-  } else if (cs.precision == 2) {
-    if (bpl == 1) launch_one<1, 2>(p, num_sms, st);
-    else if (bpl == 4) launch_one<4, 2>(p, num_sms, st);
-    else launch_one<2, 2>(p, num_sms, st);
-  } else {
-    if (bpl == 1) launch_one<1, 1>(p, num_sms, st);
-    else if (bpl == 4) launch_one<4, 1>(p, num_sms, st);
-    else launch_one<2, 1>(p, num_sms, st);
-  }
+  if (cs.ext) launch_prec<true>(p, bpl, cs.precision, num_sms, st);
+  else launch_prec<false>(p, bpl, cs.precision, num_sms, st);
 }
 
 }  // namespace emrifd

@@ -47,8 +47,37 @@ __device__ __forceinline__ int run_segment(const Run& R, const long long* keyF, 
   return a - 1;
 }
 
+// a6 fallback: bracketed Newton-bisection in FP64 on [ulo, uhi] for the rare
+// roots the fast path does not settle: next to a turnover the FP32 cubic can
+// lose the root altogether (its coefficients' rounding exceeds |F* - f|) and
+// Newton from there converges slowly or leaves the piece.  Bounded iterations.
+static __device__ __noinline__ double solve_root_safe(const SegCore& C, double delta, double ulo, double uhi, int dir,
+                                               double u) {
+  double lo = ulo, hi = uhi;
+  if (!(u > lo && u < hi)) u = 0.5 * (lo + hi);
+  for (int it = 0; it < 200; it++) {
+    const double r = fma(u, fma(u, fma(u, C.d, C.c), C.b), -delta);
+    if (r == 0.0) break;
+    if ((r > 0.0) == (dir > 0)) hi = u;
+    else lo = u;
+    const double D = fma(u, fma(u, C.d3, C.c2), C.b);
+    double un = u - r / D;
+    if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
+    if (un == u || !(hi > lo)) break;
+    u = un;
+  }
+  // the end of the bracket with the smaller residual if the iteration stalled there
+  const double rl = fabs(fma(lo, fma(lo, fma(lo, C.d, C.c), C.b), -delta));
+  const double rh = fabs(fma(hi, fma(hi, fma(hi, C.d, C.c), C.b), -delta));
+  const double ru = fabs(fma(u, fma(u, fma(u, C.d, C.c), C.b), -delta));
+  if (rl < ru && rl <= rh) return lo;
+  if (rh < ru) return hi;
+  return u;
+}
+
 // a6: FP32 start value, FP64 Newton polish (iterated where the predicted error of
-// one step exceeds 1e-13, i.e. near turnovers), clamped into [ulo, uhi]
+// one step exceeds 1e-13, i.e. near turnovers), clamped into [ulo, uhi]; a
+// polish that has not settled or had to be clamped is redone by solve_root_safe
 template <int NIT>
 __device__ __forceinline__ double solve_root(const SegCore& C, double delta, double ulo, double uhi, int dir,
                                              float& uf_out, float& Df_out) {
@@ -72,10 +101,17 @@ __device__ __forceinline__ double solve_root(const SegCore& C, double delta, dou
     kap = fabsf(__fdividef(C.cf + 3.f * C.df * ufc, Dc));
     err = stp * (kap * stp + 4.8e-7f);
   }
-  // clamp into the piece (u >= 0, so integer order of the bits is numeric order)
-  long long ub_ = __double_as_longlong(u);
-  if (ub_ < __double_as_longlong(ulo)) u = ulo;
-  else if (ub_ > __double_as_longlong(uhi)) u = uhi;
+  // clamp into the piece (integer order of the bits is numeric order for u >= 0;
+  // a negative u has the sign bit set and compares below ulo)
+  bool settle = err > 1e-13f;
+  const long long ub_ = __double_as_longlong(u);
+  if (ub_ < __double_as_longlong(ulo)) { u = ulo; settle = true; }
+  else if (ub_ > __double_as_longlong(uhi)) { u = uhi; settle = true; }
+  if (settle) {
+    u = solve_root_safe(C, delta, ulo, uhi, dir, u);
+    uf = d2f_bits(u);
+    Df = (3.f * C.df * uf + 2.f * C.cf) * uf + C.bf;
+  }
   uf_out = uf;
   Df_out = Df;
   return u;

@@ -4,17 +4,17 @@ import numpy as np
 from paper_2307_12585_gb300 import api, synth
 
 
-def plan_for(wfs, precision="fp64", conj=True, tile_bins=0):
+def plan_for(wfs, precision="fp64", conj=True, tile_bins=0, spa="standard"):
     return api.Plan(precision, conj_partners=conj, max_waveforms=len(wfs),
                     max_knots=max(w.K for w in wfs), max_knots_total=sum(w.K for w in wfs),
                     max_modes_total=max(1, sum(w.n_modes for w in wfs)),
-                    max_bins_total=max(1, sum(w.n_freqs for w in wfs)), tile_bins=tile_bins)
+                    max_bins_total=max(1, sum(w.n_freqs for w in wfs)), tile_bins=tile_bins, spa=spa)
 
 
-def run(wfs, precision="fp64", conj=True, tile_bins=0, stats=False):
+def run(wfs, precision="fp64", conj=True, tile_bins=0, stats=False, spa="standard"):
     if not isinstance(wfs, (list, tuple)):
         wfs = [wfs]
-    plan = plan_for(wfs, precision, conj, tile_bins)
+    plan = plan_for(wfs, precision, conj, tile_bins, spa)
     hp, hc = plan.sum_modes(plan.upload(synth.concat(wfs)))
     out = (hp.cpu().numpy(), hc.cpu().numpy())
     st = plan.stats() if stats else None
