@@ -206,12 +206,13 @@ def rel_l2(x, ref):
     return float(np.sqrt(np.sum(np.abs(x - ref) ** 2)) / (den if den > 0 else 1.0))
 
 
-def td_dft(w, dt, conj_partners=True, oversample_T=None):
+def td_dft(w, dt, conj_partners=True, oversample_T=None, window=None):
     """Brute-force check: sample h(t) = sum_V H_V(t) e^{-i Phi_V(t)} (Eq. 2) on
     t_j = t_0 + j dt over the trajectory, using scipy's not-a-knot splines of
     the same knots (an implementation independent of oracle.c), and take the
     DFT with the e^{+2 pi i f t} sign of Eq. 3:
         h~(f_k) = dt sum_j h(t_j) e^{2 pi i f_k t_j},  f_k = k/(N dt).
+    window="hann" multiplies the samples by hann_td(N) first.
     Returns (f_k for k = 1..N/2-1, h+~, hx~)."""
     from scipy.interpolate import CubicSpline
 
@@ -235,6 +236,8 @@ def td_dft(w, dt, conj_partners=True, oversample_T=None):
             Yp = swsh_closed(l, -m, w.theta, w.phi)
             hin += w.prefactor * ((-1) ** l) * np.conj(A) * Yp * np.exp(1j * (m * Pp + n * Pr))
     h[inside] = hin
+    if window == "hann":
+        h = h * hann_td(N)
     hplus = h.real.astype(np.complex128)
     hcross = (-h.imag).astype(np.complex128)   # h = h+ - i hx
     # sum_j x_j e^{+2 pi i k j / N} = N ifft(x)[k]
@@ -243,6 +246,23 @@ def td_dft(w, dt, conj_partners=True, oversample_T=None):
     Hc = dt * N * np.fft.ifft(hcross) * phase0
     k = np.arange(1, N // 2)
     return k / (N * dt), Hp[k], Hc[k]
+
+
+def hann_fd(h):
+    """Hann window applied in the frequency domain (Sec. 2.3: the FD waveform is
+    convolved with the transform of the window).  For w(t) = sin^2(pi t df) =
+    1/2 - e^{2 pi i t df}/4 - e^{-2 pi i t df}/4 on [0, 1/df] and a uniform grid of
+    spacing df, the transform of w h is h(f)/2 - h(f + df)/4 - h(f - df)/4; bins
+    outside the grid are taken as 0.  ``h``: complex array over one grid."""
+    h = np.asarray(h)
+    lo = np.concatenate([np.zeros(1, h.dtype), h[:-1]])
+    hi = np.concatenate([h[1:], np.zeros(1, h.dtype)])
+    return 0.5 * h - 0.25 * (lo + hi)
+
+
+def hann_td(n):
+    """The periodic Hann window sin^2(pi j / n), j = 0..n-1 (time samples)."""
+    return np.sin(np.pi * np.arange(n) / n) ** 2
 
 
 def swsh_closed(l, m, theta, phi):
