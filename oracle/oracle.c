@@ -760,3 +760,52 @@ int oracle_loglike_grad(int K, const double* t, const double* phi_phi, const dou
   free(J); free(gcf); free(gca); free(vstart); free(gv); free(hp); free(hc); free(G); ctx_free(&c);
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Mode selection (Sec. 2.1)                                             */
+/* ------------------------------------------------------------------ */
+/*
+ * At each knot t_k every mode's power is P_j = |A_j(t_k)|^2 = re^2 + im^2.
+ * The modes are ordered by decreasing power (equal powers: increasing mode
+ * index) and their cumulative sums S_1, S_2, ... taken in that order, one
+ * FP64 addition at a time; the total is the last of them.  Walking down the
+ * ordered list, a mode still contributes while the power before it is below
+ * the fraction 1 - eps of the total: mode (i) is kept at t_k when
+ * S_{i-1} < (1 - eps) S_N.  The selected modes are the union over all knots.
+ * amp: [nm][K][2] (re, im); keep: [nm], set to 0/1.  Returns the count kept.
+ */
+typedef struct { double p; int j; } or_pw_t;
+
+static int or_pw_cmp(const void* a, const void* b) {
+  const or_pw_t* x = (const or_pw_t*)a;
+  const or_pw_t* y = (const or_pw_t*)b;
+  if (x->p > y->p) return -1;
+  if (x->p < y->p) return 1;
+  return (x->j > y->j) - (x->j < y->j);
+}
+
+long long oracle_select_modes(int K, int nm, const double* amp, double eps, int* keep) {
+  or_pw_t* P = (or_pw_t*)malloc(sizeof(or_pw_t) * (size_t)(nm > 0 ? nm : 1));
+  for (int j = 0; j < nm; j++) keep[j] = 0;
+  for (int k = 0; k < K; k++) {
+    for (int j = 0; j < nm; j++) {
+      const double re = amp[((size_t)j * K + k) * 2], im = amp[((size_t)j * K + k) * 2 + 1];
+      P[j].p = re * re + im * im;
+      P[j].j = j;
+    }
+    qsort(P, (size_t)nm, sizeof(or_pw_t), or_pw_cmp);
+    double total = 0.0;
+    for (int i = 0; i < nm; i++) total += P[i].p;
+    const double thr = (1.0 - eps) * total;
+    double before = 0.0;
+    for (int i = 0; i < nm; i++) {
+      if (!(before < thr)) break;
+      keep[P[i].j] = 1;
+      before += P[i].p;
+    }
+  }
+  long long n = 0;
+  for (int j = 0; j < nm; j++) n += keep[j];
+  free(P);
+  return n;
+}

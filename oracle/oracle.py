@@ -52,6 +52,8 @@ def lib():
                                        C.c_longlong, dp, dp, dp, C.POINTER(C.c_longlong), C.c_int]
         L.oracle_ext_factor.argtypes = [C.c_longlong, dp, dp, dp]
         L.oracle_ext_factor.restype = None
+        L.oracle_select_modes.argtypes = [C.c_int, C.c_int, dp, C.c_double, ip]
+        L.oracle_select_modes.restype = C.c_longlong
         L.oracle_sum_modes.restype = C.c_int
         L.oracle_loglike_grad.argtypes = [C.c_int, dp, dp, dp, dp, dp, C.c_int, ip, ip, ip, dp,
                                           C.c_double, C.c_double, C.c_double, C.c_int,
@@ -246,6 +248,18 @@ def td_dft(w, dt, conj_partners=True, oversample_T=None, window=None):
     Hc = dt * N * np.fft.ifft(hcross) * phase0
     k = np.arange(1, N // 2)
     return k / (N * dt), Hp[k], Hc[k]
+
+
+def select_modes(amp, eps):
+    """Mode selection of Sec. 2.1 (see oracle_select_modes in oracle.c): amp is
+    [N_m, K] complex knot values; returns a bool mask over modes."""
+    a = np.ascontiguousarray(np.asarray(amp, np.complex128))
+    nm, K = a.shape
+    ar, ap = _d(a.view(np.float64).reshape(-1))
+    keep = np.zeros(max(nm, 1), np.int32)
+    kk, kp = _i(keep)
+    lib().oracle_select_modes(K, nm, ap, float(eps), kp)
+    return kk[:nm].astype(bool)
 
 
 def hann_fd(h):
