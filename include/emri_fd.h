@@ -92,6 +92,19 @@ enum { EMRI_FD_FP64 = 0, EMRI_FD_MIXED = 1, EMRI_FD_FP64X = 2 };
  *   FP32 precision (mixed plans).  Not available with likelihood = 1. */
 enum { EMRI_FD_SPA_STANDARD = 0, EMRI_FD_SPA_EXTENDED = 1 };
 
+/* Window of the time-domain signal, applied in the frequency domain (Sec. 2.3:
+ * the FD waveform is convolved with the transform of the window).
+ * EMRI_FD_WINDOW_HANN: w(t) = sin^2(pi t df) on [0, 1/df], df the spacing of
+ *   the waveform's grid, t the knots' time coordinate (the observation starts
+ *   at t = 0).  Its transform on that grid has three terms:
+ *   h_w(f_i) = h(f_i)/2 - h(f_{i-1})/4 - h(f_{i+1})/4, with h = 0 outside the
+ *   grid (exact when the grid holds every frequency with content, plus one bin
+ *   on each side, e.g. f_i = i df from i = 1).  Each waveform's grid must be
+ *   uniform: a spacing further than 1e-6 relative from the mean spacing
+ *   returns EMRI_FD_ERR_FREQ at the next call or emri_fd_sync.  The plan holds
+ *   an extra output-sized buffer per channel. */
+enum { EMRI_FD_WINDOW_NONE = 0, EMRI_FD_WINDOW_HANN = 1 };
+
 #define EMRI_FD_MAX_L 20
 
 typedef struct {
@@ -113,7 +126,9 @@ typedef struct {
                                (FP64 standard-form plans only); 0: that call returns
                                EMRI_FD_ERR_ARG */
   int spa_form;             /* EMRI_FD_SPA_STANDARD (0) or EMRI_FD_SPA_EXTENDED (1), below */
-  int reserved[5];          /* must be zero */
+  int window;               /* EMRI_FD_WINDOW_NONE (0) or EMRI_FD_WINDOW_HANN (1), below;
+                               not available with likelihood = 1 */
+  int reserved[4];          /* must be zero */
 } emri_fd_desc;
 
 /*
@@ -184,6 +199,27 @@ emri_fd_status emri_fd_loglike_and_grad(emri_fd_plan_t plan, int n_waveforms,
                                         const double* psd, const double* df, double* loglike,
                                         double* g_phi_phi, double* g_phi_r, double* g_omega_phi,
                                         double* g_omega_r, double* g_amp);
+
+/*
+ * Power-based mode selection (Sec. 2.1).  For each waveform and each knot t_k,
+ * the powers |A_j(t_k)|^2 of its modes are ordered by decreasing power (equal
+ * powers: increasing mode index) and summed in that order, one FP64 addition
+ * at a time; the mode at position i is kept when the sum before it is below
+ * (1 - eps) times the total.  The selection is the union over the knots.
+ *   knot_off, mode_off: host int64 [n_waveforms + 1], as emri_fd_sum_modes
+ *     (only the knot counts are used from knot_off; K >= 1 here);
+ *   amp:  [sum N_m K] complex128 knot amplitudes, mode-major, knot-minor;
+ *   eps:  finite (eps <= 0 keeps every mode, eps >= 1 keeps none);
+ *   keep: [sum N_m] int, written 1 (selected) or 0.
+ * Per waveform N_m <= EMRI_FD_SELECT_MAX_MODES (the per-knot sort runs in one
+ * CTA's shared memory), else EMRI_FD_ERR_CAPACITY; sizes are also bounded by
+ * the plan's maxima.  Non-finite powers latch EMRI_FD_ERR_NONFINITE.  The
+ * result is bit-exact: every power, sum and comparison is one IEEE FP64
+ * operation in the stated order.  Pointers may be device or host memory.
+ */
+#define EMRI_FD_SELECT_MAX_MODES 8192
+emri_fd_status emri_fd_select_modes(emri_fd_plan_t plan, int n_waveforms, const long long* knot_off,
+                                    const long long* mode_off, const double* amp, double eps, int* keep);
 
 /*
  * Wait for the plan's stream and return (and clear) the status latched by the

@@ -20,7 +20,8 @@ STATUS = {0: "EMRI_FD_OK", 1: "EMRI_FD_ERR_ARG", 2: "EMRI_FD_ERR_KNOTS", 3: "EMR
           7: "EMRI_FD_ERR_CUDA", 8: "EMRI_FD_ERR_OOM", 9: "EMRI_FD_ERR_TIMEOUT"}
 EXPORTS = ("emri_fd_plan", "emri_fd_sum_modes", "emri_fd_loglike_and_grad", "emri_fd_sync", "emri_fd_stats",
            "emri_fd_profile", "emri_fd_plan_destroy", "emri_fd_strerror", "emri_fd_sum_modes_noalloc",
-           "emri_fd_set_tile", "emri_fd_capture", "emri_fd_replay", "emri_fd_graph_destroy")
+           "emri_fd_set_tile", "emri_fd_capture", "emri_fd_replay", "emri_fd_graph_destroy",
+           "emri_fd_select_modes")
 
 
 class EmriFdError(RuntimeError):
@@ -33,9 +34,10 @@ class emri_fd_desc(C.Structure):
     _fields_ = [("precision", C.c_int), ("conj_partners", C.c_int), ("max_waveforms", C.c_int),
                 ("max_knots", C.c_int), ("max_knots_total", C.c_longlong), ("max_modes_total", C.c_longlong),
                 ("max_bins_total", C.c_longlong), ("tile_bins", C.c_int), ("likelihood", C.c_int),
-                ("spa_form", C.c_int), ("reserved", C.c_int * 5)]
+                ("spa_form", C.c_int), ("window", C.c_int), ("reserved", C.c_int * 4)]
 
 SPA_FORMS = {"standard": 0, "extended": 1}
+WINDOWS = {None: 0, "none": 0, "hann": 1}
 
 
 _lib = None
@@ -61,6 +63,8 @@ def lib():
         L.emri_fd_sum_modes.restype = C.c_int
         L.emri_fd_loglike_and_grad.argtypes = [vp, C.c_int, vp, vp, vp] + [dp] * 5 + [ip] * 3 + [dp] * 5 + [dp] * 10
         L.emri_fd_loglike_and_grad.restype = C.c_int
+        L.emri_fd_select_modes.argtypes = [vp, C.c_int, vp, vp, dp, C.c_double, ip]
+        L.emri_fd_select_modes.restype = C.c_int
         L.emri_fd_set_tile.argtypes = [vp, C.c_int]
         L.emri_fd_set_tile.restype = C.c_int
         L.emri_fd_capture.argtypes = [vp, C.c_int, vp, vp, vp] + [dp] * 5 + [ip] * 3 + [dp] * 5 + [vp, vp,
@@ -177,6 +181,13 @@ def emri_fd_strerror(code) -> str:
     return _strerror(code)
 
 
+def emri_fd_select_modes(plan, n_waveforms, knot_off, mode_off, amp, eps, keep) -> int:
+    """Array arguments are raw addresses (ints); returns the status code."""
+    return lib().emri_fd_select_modes(C.c_void_p(plan), int(n_waveforms), C.c_void_p(int(knot_off)),
+                                      C.c_void_p(int(mode_off)), C.c_void_p(int(amp)), float(eps),
+                                      C.c_void_p(int(keep)))
+
+
 def emri_fd_plan_destroy(plan) -> None:
     lib().emri_fd_plan_destroy(C.c_void_p(plan))
 
@@ -199,11 +210,12 @@ class Plan:
 
     precision: "fp64" or "fp64x" (complex128 outputs) or "mixed" (complex64 outputs).
     spa: "standard" (Fresnel integral per root) or "extended" (Eq. 10 per root).
+    window: None or "hann" (the window's three-term convolution on a uniform grid).
     Batches are dicts in the layout of synth.concat (numpy or torch)."""
 
     def __init__(self, precision="fp64", conj_partners=True, max_waveforms=1, max_knots=200,
                  max_modes_total=4096, max_bins_total=1 << 22, max_knots_total=0, tile_bins=0,
-                 likelihood=False, device=None, stream=None, spa="standard"):
+                 likelihood=False, device=None, stream=None, spa="standard", window=None):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -220,7 +232,9 @@ class Plan:
         d.tile_bins = int(tile_bins)
         d.likelihood = int(bool(likelihood))
         d.spa_form = SPA_FORMS[spa]
+        d.window = WINDOWS[window]
         self.spa = spa
+        self.window = window
         self.desc = d
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -290,6 +304,19 @@ class Plan:
         _check(code, "emri_fd_sum_modes")
         _check(emri_fd_sync(self.handle), "emri_fd_sum_modes (device checks)")
         return out
+
+    def select_modes(self, b, eps, check=True):
+        """emri_fd_select_modes on a batch (device tensors from upload, or numpy):
+        bool tensor [sum N_m] on the plan's device, True for the selected modes."""
+        T = self.torch
+        ko, mo = (np.ascontiguousarray(np.asarray(b[k], np.int64)) for k in ("knot_off", "mode_off"))
+        keep = T.empty(int(mo[-1]), dtype=T.int32, device=self.device)
+        code = emri_fd_select_modes(self.handle, len(ko) - 1, ko.ctypes.data, mo.ctypes.data, _addr(b["amp"]),
+                                    eps, keep.data_ptr())
+        _check(code, "emri_fd_select_modes")
+        if check:
+            _check(emri_fd_sync(self.handle), "emri_fd_select_modes (device checks)")
+        return keep.bool()
 
     def loglike_and_grad(self, b, data_plus, data_cross, psd, df, grad=True, check=True):
         """emri_fd_loglike_and_grad on a device batch.  data_*: complex128 device tensors,

@@ -207,6 +207,7 @@ struct DevScratch {
   SegFF* segff;                   // FP64X plans
   SegCrit* crit;
   double* yk;                     // [sum N_m (K-1)] 3/(2 pi h), extended FP64 plans
+  void *wbuf_p, *wbuf_c;          // [sum N_f] unwindowed h+, hx (windowed plans)
   long long* keyF;                // [sum N_m K]
   int* run_cnt;                   // [sum N_m + 1], exclusive-scanned in place
   Run* runs;
@@ -244,6 +245,7 @@ struct CallShape {
   int conj;
   int precision;
   int ext;          // 1: extended SPA (Eq. 10)
+  int window;       // 1: Hann window applied to the outputs (Sec. 2.3)
 };
 
 constexpr int kPrepKernels = 12;   // kernels launched by launch_prep (memsets excluded)
@@ -251,6 +253,11 @@ constexpr int kAdjointKernels = 8; // kernels launched by launch_adjoint
 
 void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st);
 void launch_spa(const CallShape& cs, const DevInputs& in, const DevScratch& s, int num_sms, cudaStream_t st);
+size_t select_smem_bytes(long long max_modes);
+void launch_select(const DevScratch& s, int n_wf, int max_K, long long max_nm, const double* amp, double eps,
+                   int* keep, long long nm_total, cudaStream_t st);
+void launch_window(const CallShape& cs, const DevScratch& s, const double* freqs, const void* in_p, const void* in_c,
+                   void* out_p, void* out_c, int num_sms, cudaStream_t st);
 void launch_table(double2* tab, cudaStream_t st);
 void launch_table_ff(const double2* tab, float4* tabf, cudaStream_t st);
 void launch_scan(int* cnt, long long n, cudaStream_t st);

@@ -1,5 +1,6 @@
 // C ABI of the GB300 SPA mode sum: plan lifetime, host-side validation,
 // host-pointer staging and the launch sequence (see include/emri_fd.h).
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -111,7 +112,9 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
       d->max_bins_total > 2000000000LL || d->max_knots_total < 0 ||
       !(d->tile_bins == 0 || d->tile_bins == 32 || d->tile_bins == 64 || d->tile_bins == 128))
     return EMRI_FD_ERR_ARG;
-  for (int i = 0; i < 5; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
+  for (int i = 0; i < 4; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
+  if (d->window != EMRI_FD_WINDOW_NONE && d->window != EMRI_FD_WINDOW_HANN) return EMRI_FD_ERR_ARG;
+  if (d->window != EMRI_FD_WINDOW_NONE && d->likelihood) return EMRI_FD_ERR_ARG;
   if (d->spa_form != EMRI_FD_SPA_STANDARD && d->spa_form != EMRI_FD_SPA_EXTENDED) return EMRI_FD_ERR_ARG;
   if (d->likelihood != 0 &&
       (d->likelihood != 1 || d->precision != EMRI_FD_FP64 || d->spa_form != EMRI_FD_SPA_STANDARD))
@@ -148,6 +151,14 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
   else { AL(s.segff, p->cap_seg); AL(s.tabf, kTabN); }
   AL(s.crit, p->cap_seg);
   if (d->spa_form == EMRI_FD_SPA_EXTENDED && d->precision == EMRI_FD_FP64) { AL(s.yk, p->cap_seg); }
+  if (d->window == EMRI_FD_WINDOW_HANN) {
+    unsigned char *wp = nullptr, *wc = nullptr;
+    const long long ob = (d->precision == EMRI_FD_MIXED ? 8 : 16) * p->cap_nf;
+    AL(wp, ob);
+    AL(wc, ob);
+    s.wbuf_p = wp;
+    s.wbuf_c = wc;
+  }
   AL(s.keyF, p->cap_amp);
   AL(s.run_cnt, p->cap_nm + 1);
   AL(s.runs, s.run_cap);
@@ -210,6 +221,7 @@ emri_fd_status prepare_call(emri_fd_plan_s* p, int n_wf, const long long* knot_o
   cs.conj = p->desc.conj_partners;
   cs.precision = p->desc.precision;
   cs.ext = p->desc.spa_form;
+  cs.window = p->desc.window;
   long long amp_base = 0, seg_base = 0, tiles = 0;
   int maxK = 0;
   for (int w = 0; w < n_wf; w++) {
@@ -309,6 +321,16 @@ void run_forward(emri_fd_plan_s* p, const CallShape& cs, const DevInputs& in, si
     if (cs.nm_total == 0) {
       cudaMemsetAsync(in.h_plus, 0, ob, stm);
       cudaMemsetAsync(in.h_cross, 0, ob, stm);
+    } else if (cs.window) {
+      // unwindowed sum into plan buffers, then the window's three-term convolution
+      DevInputs in2 = in;
+      in2.h_plus = p->s.wbuf_p;
+      in2.h_cross = p->s.wbuf_c;
+      if (E) cudaEventRecord(E[1], stm);
+      launch_spa(cs, in2, p->s, p->num_sms, stm);
+      if (E) cudaEventRecord(E[2], stm);
+      launch_window(cs, p->s, in.freqs, in2.h_plus, in2.h_cross, in.h_plus, in.h_cross, p->num_sms, stm);
+      p->launches += 2;
     } else {
       if (E) cudaEventRecord(E[1], stm);
       launch_spa(cs, in, p->s, p->num_sms, stm);
@@ -353,6 +375,48 @@ emri_fd_status emri_fd_sum_modes(emri_fd_plan_t p, int n_wf, const long long* kn
         cudaStreamSynchronize(stm) != cudaSuccess)
       return EMRI_FD_ERR_CUDA;
   }
+  return EMRI_FD_OK;
+}
+
+emri_fd_status emri_fd_select_modes(emri_fd_plan_t p, int n_wf, const long long* knot_off, const long long* mode_off,
+                                    const double* amp, double eps, int* keep) {
+  if (!p || n_wf < 1 || !knot_off || !mode_off) return EMRI_FD_ERR_ARG;
+  if (n_wf > p->desc.max_waveforms) return EMRI_FD_ERR_CAPACITY;
+  if (knot_off[0] != 0 || mode_off[0] != 0 || !(fabs(eps) < INFINITY)) return EMRI_FD_ERR_ARG;
+  if (cudaEventSynchronize(p->wf_done) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_CUDA; }
+  long long amp_base = 0, max_nm = 1;
+  int maxK = 1;
+  for (int w = 0; w < n_wf; w++) {
+    const long long K = knot_off[w + 1] - knot_off[w], nm = mode_off[w + 1] - mode_off[w];
+    if (K < 1 || nm < 0) return EMRI_FD_ERR_ARG;
+    if (K > p->desc.max_knots || nm > EMRI_FD_SELECT_MAX_MODES) return EMRI_FD_ERR_CAPACITY;
+    WfInfo& W = p->wf_pinned[w];
+    W = WfInfo{};
+    W.ko = knot_off[w]; W.K = K; W.mo = mode_off[w]; W.nm = nm; W.amp_base = amp_base;
+    amp_base += nm * K;
+    if (K > maxK) maxK = (int)K;
+    if (nm > max_nm) max_nm = nm;
+  }
+  const long long nm_total = mode_off[n_wf];
+  if (knot_off[n_wf] > p->cap_K || nm_total > p->cap_nm || amp_base > p->cap_amp) return EMRI_FD_ERR_CAPACITY;
+  if (nm_total > 0 && (!amp || !keep)) return EMRI_FD_ERR_ARG;
+  if (nm_total == 0) return EMRI_FD_OK;
+  const void* a = nullptr;
+  emri_fd_status st = stage_in(p, 8, amp, 2 * sizeof(double) * (size_t)amp_base, &a);
+  if (st != EMRI_FD_OK) return st;
+  void* kd = nullptr;
+  bool khost = false;
+  if ((st = stage_out(p, 13, keep, sizeof(int) * (size_t)nm_total, &kd, &khost)) != EMRI_FD_OK) return st;
+  cudaStream_t stm = p->stream;
+  if (cudaMemcpyAsync(p->s.wf, p->wf_pinned, sizeof(WfInfo) * n_wf, cudaMemcpyHostToDevice, stm) != cudaSuccess ||
+      cudaEventRecord(p->wf_done, stm) != cudaSuccess)
+    return EMRI_FD_ERR_CUDA;
+  launch_select(p->s, n_wf, maxK, max_nm, static_cast<const double*>(a), eps, static_cast<int*>(kd), nm_total, stm);
+  p->launches += 1;
+  if (cudaGetLastError() != cudaSuccess) return EMRI_FD_ERR_CUDA;
+  if (khost && (cudaMemcpyAsync(keep, kd, sizeof(int) * (size_t)nm_total, cudaMemcpyDeviceToHost, stm) != cudaSuccess ||
+                cudaStreamSynchronize(stm) != cudaSuccess))
+    return EMRI_FD_ERR_CUDA;
   return EMRI_FD_OK;
 }
 
