@@ -208,20 +208,18 @@ def rel_l2(x, ref):
     return float(np.sqrt(np.sum(np.abs(x - ref) ** 2)) / (den if den > 0 else 1.0))
 
 
-def td_dft(w, dt, conj_partners=True, oversample_T=None, window=None):
-    """Brute-force check: sample h(t) = sum_V H_V(t) e^{-i Phi_V(t)} (Eq. 2) on
-    t_j = t_0 + j dt over the trajectory, using scipy's not-a-knot splines of
-    the same knots (an implementation independent of oracle.c), and take the
-    DFT with the e^{+2 pi i f t} sign of Eq. 3:
-        h~(f_k) = dt sum_j h(t_j) e^{2 pi i f_k t_j},  f_k = k/(N dt).
-    window="hann" multiplies the samples by hann_td(N) first.
-    Returns (f_k for k = 1..N/2-1, h+~, hx~)."""
+def td_samples(w, dt, N=None, conj_partners=True):
+    """Time-domain voice sum (Eq. 2) sampled at t_j = t_0 + j dt, j = 0..N-1
+    (default N = floor((t_last - t_0)/dt)); samples after t_last are 0.  Uses
+    scipy's not-a-knot splines of the same knots and the Wigner-d Y_lm below,
+    an implementation independent of oracle.c:
+        h(t) = prefactor sum_modes [A Y_lm e^{-i Phi} + (partners) (-1)^l conj(A) Y_{l,-m} e^{+i Phi}],
+    Phi = m Phi_phi + n Phi_r; h = h+ - i hx.  Returns (t_j, h+, hx) real arrays."""
     from scipy.interpolate import CubicSpline
 
     t = w.t
-    N = int(np.floor((t[-1] - t[0]) / dt))
-    if oversample_T is not None:
-        N = int(np.floor(oversample_T / dt))
+    if N is None:
+        N = int(np.floor((t[-1] - t[0]) / dt))
     tj = t[0] + dt * np.arange(N)
     inside = tj <= t[-1]
     tin = tj[inside]
@@ -238,14 +236,28 @@ def td_dft(w, dt, conj_partners=True, oversample_T=None, window=None):
             Yp = swsh_closed(l, -m, w.theta, w.phi)
             hin += w.prefactor * ((-1) ** l) * np.conj(A) * Yp * np.exp(1j * (m * Pp + n * Pr))
     h[inside] = hin
+    return tj, h.real.copy(), -h.imag
+
+
+def td_dft(w, dt, conj_partners=True, oversample_T=None, window=None, N=None):
+    """Brute-force check: the DFT of td_samples with the e^{+2 pi i f t} sign of Eq. 3,
+        h~(f_k) = dt sum_j h(t_j) e^{2 pi i f_k t_j},  f_k = k/(N dt).
+    N: number of samples (default from the trajectory length, or oversample_T/dt).
+    window="hann" multiplies the samples by hann_td(N) first.
+    Returns (f_k for k = 1..N/2-1, h+~, hx~)."""
+    t = w.t
+    if N is None:
+        N = int(np.floor((t[-1] - t[0]) / dt))
+        if oversample_T is not None:
+            N = int(np.floor(oversample_T / dt))
+    tj, hp_t, hc_t = td_samples(w, dt, N, conj_partners)
     if window == "hann":
-        h = h * hann_td(N)
-    hplus = h.real.astype(np.complex128)
-    hcross = (-h.imag).astype(np.complex128)   # h = h+ - i hx
+        win = hann_td(N)
+        hp_t, hc_t = hp_t * win, hc_t * win
     # sum_j x_j e^{+2 pi i k j / N} = N ifft(x)[k]
     phase0 = np.exp(2j * np.pi * np.arange(N) / (N * dt) * t[0])
-    Hp = dt * N * np.fft.ifft(hplus) * phase0
-    Hc = dt * N * np.fft.ifft(hcross) * phase0
+    Hp = dt * N * np.fft.ifft(hp_t.astype(np.complex128)) * phase0
+    Hc = dt * N * np.fft.ifft(hc_t.astype(np.complex128)) * phase0
     k = np.arange(1, N // 2)
     return k / (N * dt), Hp[k], Hc[k]
 
