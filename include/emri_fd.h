@@ -128,7 +128,10 @@ typedef struct {
   int spa_form;             /* EMRI_FD_SPA_STANDARD (0) or EMRI_FD_SPA_EXTENDED (1), below */
   int window;               /* EMRI_FD_WINDOW_NONE (0) or EMRI_FD_WINDOW_HANN (1), below;
                                not available with likelihood = 1 */
-  int reserved[4];          /* must be zero */
+  int time_domain;          /* 1: also allocate the scratch of the time-domain comparator
+                               (emri_fd_td_sum, emri_fd_td_spectrum); 0: those return
+                               EMRI_FD_ERR_ARG */
+  int reserved[3];          /* must be zero */
 } emri_fd_desc;
 
 /*
@@ -199,6 +202,46 @@ emri_fd_status emri_fd_loglike_and_grad(emri_fd_plan_t plan, int n_waveforms,
                                         const double* psd, const double* df, double* loglike,
                                         double* g_phi_phi, double* g_phi_r, double* g_omega_phi,
                                         double* g_omega_r, double* g_amp);
+
+/*
+ * Time-domain comparator (Sec. 2.3, 3.2): the TD waveform of Eq. 2 sampled at
+ * t_j = t_0 + j dt (t_0 = the waveform's first knot), j = 0 .. N_w - 1:
+ *   h(t) = prefactor sum_modes [A Y_lm e^{-i Phi} + (partners) (-1)^l conj(A) Y_{l,-m} e^{+i Phi}],
+ *   Phi = m Phi_phi + n Phi_r, h = h+ - i hx; samples after the last knot are 0.
+ * Inputs as emri_fd_sum_modes (the frequency series are splined but unused),
+ * plus:
+ *   sample_off: host int64 [n_waveforms + 1], N_w = sample_off[w+1] - sample_off[w];
+ *   dt:       [n_waveforms] sampling intervals (> 0);
+ * outputs h_plus, h_cross: [sum N_w] float (real TD samples).
+ * Arithmetic: FP32 amplitudes and trigonometry, the phase in 32-bit fixed-point
+ * turns from per-sample Q0.64 values of Phi_phi/2pi and Phi_r/2pi, sums over
+ * modes in FP32 chunks of 32 carried in FP64 (about 1e-6 relative).
+ * Needs a plan with time_domain = 1.  Pointers may be device or host memory.
+ */
+emri_fd_status emri_fd_td_sum(emri_fd_plan_t plan, int n_waveforms, const long long* knot_off,
+                              const long long* mode_off, const long long* sample_off, const double* t,
+                              const double* phi_phi, const double* phi_r, const double* omega_phi,
+                              const double* omega_r, const int* l, const int* m, const int* n,
+                              const double* amp, const double* theta, const double* phi,
+                              const double* prefactor, const double* dt, float* h_plus, float* h_cross);
+
+/*
+ * DFT of TD samples with the Fourier sign of Eq. 3 (cuFFT, one complex
+ * transform of h+ + i hx per waveform):
+ *   H(f_k) = dt sum_j h(t_j) e^{2 pi i f_k t_j},  f_k = k/(N_w dt),  k = 1 .. N_w/2 - 1,
+ * for both channels.  window = EMRI_FD_WINDOW_HANN multiplies sample j by
+ * sin^2(pi j/N_w) first.
+ *   sample_off: host int64 [n_waveforms + 1]; t0, dt: HOST double [n_waveforms]
+ *     (t0: time of sample 0);
+ *   h_plus, h_cross: DEVICE float [sum N_w] (e.g. from emri_fd_td_sum);
+ *   H_plus, H_cross: DEVICE complex64 [sum (N_w/2 - 1)] (waveforms with
+ *     N_w < 4 contribute no bins).
+ * The FFT plan for each length and an N_w-sized complex buffer are made on
+ * first use and kept by the plan (these calls allocate device memory).
+ */
+emri_fd_status emri_fd_td_spectrum(emri_fd_plan_t plan, int n_waveforms, const long long* sample_off,
+                                   const double* t0, const double* dt, int window, const float* h_plus,
+                                   const float* h_cross, void* H_plus, void* H_cross);
 
 /*
  * Power-based mode selection (Sec. 2.1).  For each waveform and each knot t_k,

@@ -21,7 +21,7 @@ STATUS = {0: "EMRI_FD_OK", 1: "EMRI_FD_ERR_ARG", 2: "EMRI_FD_ERR_KNOTS", 3: "EMR
 EXPORTS = ("emri_fd_plan", "emri_fd_sum_modes", "emri_fd_loglike_and_grad", "emri_fd_sync", "emri_fd_stats",
            "emri_fd_profile", "emri_fd_plan_destroy", "emri_fd_strerror", "emri_fd_sum_modes_noalloc",
            "emri_fd_set_tile", "emri_fd_capture", "emri_fd_replay", "emri_fd_graph_destroy",
-           "emri_fd_select_modes")
+           "emri_fd_select_modes", "emri_fd_td_sum", "emri_fd_td_spectrum")
 
 
 class EmriFdError(RuntimeError):
@@ -34,7 +34,7 @@ class emri_fd_desc(C.Structure):
     _fields_ = [("precision", C.c_int), ("conj_partners", C.c_int), ("max_waveforms", C.c_int),
                 ("max_knots", C.c_int), ("max_knots_total", C.c_longlong), ("max_modes_total", C.c_longlong),
                 ("max_bins_total", C.c_longlong), ("tile_bins", C.c_int), ("likelihood", C.c_int),
-                ("spa_form", C.c_int), ("window", C.c_int), ("reserved", C.c_int * 4)]
+                ("spa_form", C.c_int), ("window", C.c_int), ("time_domain", C.c_int), ("reserved", C.c_int * 3)]
 
 SPA_FORMS = {"standard": 0, "extended": 1}
 WINDOWS = {None: 0, "none": 0, "hann": 1}
@@ -63,6 +63,10 @@ def lib():
         L.emri_fd_sum_modes.restype = C.c_int
         L.emri_fd_loglike_and_grad.argtypes = [vp, C.c_int, vp, vp, vp] + [dp] * 5 + [ip] * 3 + [dp] * 5 + [dp] * 10
         L.emri_fd_loglike_and_grad.restype = C.c_int
+        L.emri_fd_td_sum.argtypes = [vp, C.c_int, vp, vp, vp] + [dp] * 5 + [ip] * 3 + [dp] * 5 + [vp, vp]
+        L.emri_fd_td_sum.restype = C.c_int
+        L.emri_fd_td_spectrum.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, vp, vp, vp, vp]
+        L.emri_fd_td_spectrum.restype = C.c_int
         L.emri_fd_select_modes.argtypes = [vp, C.c_int, vp, vp, dp, C.c_double, ip]
         L.emri_fd_select_modes.restype = C.c_int
         L.emri_fd_set_tile.argtypes = [vp, C.c_int]
@@ -188,6 +192,21 @@ def emri_fd_select_modes(plan, n_waveforms, knot_off, mode_off, amp, eps, keep) 
                                       C.c_void_p(int(keep)))
 
 
+def emri_fd_td_sum(plan, n_waveforms, knot_off, mode_off, sample_off, t, phi_phi, phi_r, omega_phi, omega_r,
+                   l, m, n, amp, theta, phi, prefactor, dt, h_plus, h_cross) -> int:
+    """Array arguments are raw addresses (ints); returns the status code."""
+    return lib().emri_fd_td_sum(C.c_void_p(plan), int(n_waveforms), *[C.c_void_p(int(x)) for x in (
+        knot_off, mode_off, sample_off, t, phi_phi, phi_r, omega_phi, omega_r, l, m, n, amp, theta, phi, prefactor,
+        dt, h_plus, h_cross)])
+
+
+def emri_fd_td_spectrum(plan, n_waveforms, sample_off, t0, dt, window, h_plus, h_cross, H_plus, H_cross) -> int:
+    """Array arguments are raw addresses (ints); returns the status code."""
+    return lib().emri_fd_td_spectrum(C.c_void_p(plan), int(n_waveforms), C.c_void_p(int(sample_off)),
+                                     C.c_void_p(int(t0)), C.c_void_p(int(dt)), int(window),
+                                     *[C.c_void_p(int(x)) for x in (h_plus, h_cross, H_plus, H_cross)])
+
+
 def emri_fd_plan_destroy(plan) -> None:
     lib().emri_fd_plan_destroy(C.c_void_p(plan))
 
@@ -215,7 +234,7 @@ class Plan:
 
     def __init__(self, precision="fp64", conj_partners=True, max_waveforms=1, max_knots=200,
                  max_modes_total=4096, max_bins_total=1 << 22, max_knots_total=0, tile_bins=0,
-                 likelihood=False, device=None, stream=None, spa="standard", window=None):
+                 likelihood=False, device=None, stream=None, spa="standard", window=None, time_domain=False):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -233,6 +252,7 @@ class Plan:
         d.likelihood = int(bool(likelihood))
         d.spa_form = SPA_FORMS[spa]
         d.window = WINDOWS[window]
+        d.time_domain = int(bool(time_domain))
         self.spa = spa
         self.window = window
         self.desc = d
@@ -304,6 +324,47 @@ class Plan:
         _check(code, "emri_fd_sum_modes")
         _check(emri_fd_sync(self.handle), "emri_fd_sum_modes (device checks)")
         return out
+
+    def td_sum(self, b, dt, n_samples, check=True):
+        """emri_fd_td_sum on a device batch: TD samples t_j = t_0 + j dt of every
+        waveform (dt and n_samples: one value or one per waveform).  Returns
+        (h+, hx, sample_off) with float32 device tensors [sum N_w]."""
+        T = self.torch
+        ko, mo = (np.ascontiguousarray(np.asarray(b[k], np.int64)) for k in ("knot_off", "mode_off"))
+        nw = len(ko) - 1
+        ns = np.broadcast_to(np.asarray(n_samples, np.int64), (nw,))
+        so = np.zeros(nw + 1, np.int64)
+        so[1:] = np.cumsum(ns)
+        dtv = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, np.float64), (nw,)))
+        hp = T.empty(int(so[-1]), dtype=T.float32, device=self.device)
+        hc = T.empty(int(so[-1]), dtype=T.float32, device=self.device)
+        code = emri_fd_td_sum(self.handle, nw, ko.ctypes.data, mo.ctypes.data, so.ctypes.data,
+                              *[_addr(b[k]) for k in ("t", "phi_phi", "phi_r", "omega_phi", "omega_r", "l", "m", "n",
+                                                      "amp", "theta", "phi", "prefactor")],
+                              dtv.ctypes.data, hp.data_ptr(), hc.data_ptr())
+        _check(code, "emri_fd_td_sum")
+        if check:
+            _check(emri_fd_sync(self.handle), "emri_fd_td_sum (device checks)")
+        self._td_last = (so, dtv)
+        return hp, hc, so
+
+    def td_spectrum(self, hp, hc, sample_off, t0, dt, window=None):
+        """emri_fd_td_spectrum: complex64 device tensors H+, Hx over the bins
+        k = 1 .. N_w/2 - 1 of every waveform, and their frequencies (numpy)."""
+        T = self.torch
+        so = np.ascontiguousarray(np.asarray(sample_off, np.int64))
+        nw = len(so) - 1
+        t0v = np.ascontiguousarray(np.broadcast_to(np.asarray(t0, np.float64), (nw,)))
+        dtv = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, np.float64), (nw,)))
+        N = np.diff(so)
+        nb = np.where(N >= 4, N // 2 - 1, 0)
+        Hp = T.empty(int(nb.sum()), dtype=T.complex64, device=self.device)
+        Hc = T.empty(int(nb.sum()), dtype=T.complex64, device=self.device)
+        code = emri_fd_td_spectrum(self.handle, nw, so.ctypes.data, t0v.ctypes.data, dtv.ctypes.data,
+                                   WINDOWS[window], hp.data_ptr(), hc.data_ptr(), Hp.data_ptr(), Hc.data_ptr())
+        _check(code, "emri_fd_td_spectrum")
+        f = np.concatenate([np.arange(1, k + 1) / (Nw * d) for k, Nw, d in zip(nb, N, dtv)]) if nw else np.zeros(0)
+        return Hp, Hc, f
 
     def select_modes(self, b, eps, check=True):
         """emri_fd_select_modes on a batch (device tensors from upload, or numpy):

@@ -50,10 +50,15 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=4) as ex:
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
         objs = list(ex.map(one, _sources()))
     tmp = LIB + ".tmp"
-    r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    # cuFFT (the time-domain comparator's DFT) is found through the toolkit's library directory
+    cuda_home = os.path.dirname(os.path.dirname(os.path.realpath(NVCC)))
+    libdirs = [d for d in (os.path.join(cuda_home, "lib64"), os.path.join(cuda_home, "lib")) if os.path.isdir(d)]
+    rpath = [a for d in libdirs for a in ("-Xlinker", "-rpath", "-Xlinker", d)]
+    r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, *["-L" + d for d in libdirs], "-lcufft", *rpath],
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)

@@ -253,6 +253,14 @@ constexpr int kAdjointKernels = 8; // kernels launched by launch_adjoint
 
 void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st);
 void launch_spa(const CallShape& cs, const DevInputs& in, const DevScratch& s, int num_sms, cudaStream_t st);
+void launch_prep_td(const CallShape& cs, const DevInputs& in, const DevScratch& s, float4* tdamp, cudaStream_t st);
+void launch_td_sum(const CallShape& cs, const DevInputs& in, const DevScratch& s, const float4* tdamp,
+                   const double* dt, float* hp, float* hc, int num_sms, cudaStream_t st);
+long long td_tile_samples();
+void launch_td_pack(const float* hp, const float* hc, long long N, int hann, float2* z, int num_sms,
+                    cudaStream_t st);
+void launch_td_unpack(const float2* Z, long long N, double dt, double t0, float2* Hp, float2* Hc, int num_sms,
+                      cudaStream_t st);
 size_t select_smem_bytes(long long max_modes);
 void launch_select(const DevScratch& s, int n_wf, int max_K, long long max_nm, const double* amp, double eps,
                    int* keep, long long nm_total, cudaStream_t st);

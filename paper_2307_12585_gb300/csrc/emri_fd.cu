@@ -5,6 +5,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cufft.h>
+
 #include "../../include/emri_fd.h"
 #include "common.cuh"
 
@@ -30,6 +32,12 @@ struct emri_fd_plan_s {
   int ev_used = 0;
   long long launches = 0;            // kernels launched by calls since the last profile reset
   std::vector<void*> allocs;
+  // time-domain comparator: per-(mode, segment) FP32 amplitude coefficients,
+  // and FFT plans and buffer (made on first use)
+  float4* tdamp = nullptr;
+  std::vector<std::pair<long long, cufftHandle>> fft_plans;
+  float2* zbuf = nullptr;
+  long long zcap = 0;
 };
 
 namespace {
@@ -100,6 +108,8 @@ void emri_fd_plan_destroy(emri_fd_plan_t p) {
   if (p->cnt_pinned) cudaFreeHost(p->cnt_pinned);
   if (p->wf_done) cudaEventDestroy(p->wf_done);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+  for (auto& fp : p->fft_plans) cufftDestroy(fp.second);
+  if (p->zbuf) cudaFree(p->zbuf);
   cudaGetLastError();
   delete p;
 }
@@ -112,7 +122,8 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
       d->max_bins_total > 2000000000LL || d->max_knots_total < 0 ||
       !(d->tile_bins == 0 || d->tile_bins == 32 || d->tile_bins == 64 || d->tile_bins == 128))
     return EMRI_FD_ERR_ARG;
-  for (int i = 0; i < 4; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
+  for (int i = 0; i < 3; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
+  if (d->time_domain != 0 && d->time_domain != 1) return EMRI_FD_ERR_ARG;
   if (d->window != EMRI_FD_WINDOW_NONE && d->window != EMRI_FD_WINDOW_HANN) return EMRI_FD_ERR_ARG;
   if (d->window != EMRI_FD_WINDOW_NONE && d->likelihood) return EMRI_FD_ERR_ARG;
   if (d->spa_form != EMRI_FD_SPA_STANDARD && d->spa_form != EMRI_FD_SPA_EXTENDED) return EMRI_FD_ERR_ARG;
@@ -151,6 +162,11 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
   else { AL(s.segff, p->cap_seg); AL(s.tabf, kTabN); }
   AL(s.crit, p->cap_seg);
   if (d->spa_form == EMRI_FD_SPA_EXTENDED && d->precision == EMRI_FD_FP64) { AL(s.yk, p->cap_seg); }
+  if (d->time_domain) {
+    float4* ta = nullptr;
+    AL(ta, 2 * p->cap_seg);
+    p->tdamp = ta;
+  }
   if (d->window == EMRI_FD_WINDOW_HANN) {
     unsigned char *wp = nullptr, *wc = nullptr;
     const long long ob = (d->precision == EMRI_FD_MIXED ? 8 : 16) * p->cap_nf;
@@ -375,6 +391,166 @@ emri_fd_status emri_fd_sum_modes(emri_fd_plan_t p, int n_wf, const long long* kn
         cudaStreamSynchronize(stm) != cudaSuccess)
       return EMRI_FD_ERR_CUDA;
   }
+  return EMRI_FD_OK;
+}
+
+emri_fd_status emri_fd_td_sum(emri_fd_plan_t p, int n_wf, const long long* knot_off, const long long* mode_off,
+                              const long long* sample_off, const double* t, const double* phi_phi,
+                              const double* phi_r, const double* omega_phi, const double* omega_r, const int* l,
+                              const int* m, const int* n, const double* amp, const double* theta,
+                              const double* phi, const double* prefactor, const double* dt, float* h_plus,
+                              float* h_cross) {
+  if (!p || !p->desc.time_domain) return EMRI_FD_ERR_ARG;
+  if (n_wf < 1 || !knot_off || !mode_off || !sample_off) return EMRI_FD_ERR_ARG;
+  if (n_wf > p->desc.max_waveforms) return EMRI_FD_ERR_CAPACITY;
+  if (knot_off[0] != 0 || mode_off[0] != 0 || sample_off[0] != 0) return EMRI_FD_ERR_ARG;
+  if (cudaEventSynchronize(p->wf_done) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_CUDA; }
+  CallShape cs{};
+  cs.n_wf = n_wf;
+  cs.conj = p->desc.conj_partners;
+  const long long TS = td_tile_samples();
+  long long amp_base = 0, seg_base = 0, tiles = 0;
+  for (int w = 0; w < n_wf; w++) {
+    const long long K = knot_off[w + 1] - knot_off[w], nm = mode_off[w + 1] - mode_off[w];
+    const long long ns = sample_off[w + 1] - sample_off[w];
+    if (K < 0 || nm < 0 || ns < 0) return EMRI_FD_ERR_ARG;
+    if (K < 4) return EMRI_FD_ERR_KNOTS;
+    if (K > p->desc.max_knots) return EMRI_FD_ERR_CAPACITY;
+    WfInfo& W = p->wf_pinned[w];
+    W = WfInfo{};
+    W.ko = knot_off[w]; W.K = K; W.mo = mode_off[w]; W.nm = nm; W.fo = sample_off[w]; W.nf = ns;
+    W.amp_base = amp_base; W.seg_base = seg_base; W.tile_base = tiles; W.ntiles = (ns + TS - 1) / TS;
+    amp_base += nm * K;
+    seg_base += nm * (K - 1);
+    tiles += W.ntiles;
+  }
+  cs.K_total = knot_off[n_wf];
+  cs.nm_total = mode_off[n_wf];
+  cs.nf_total = sample_off[n_wf];
+  cs.seg_total = seg_base;
+  cs.amp_total = amp_base;
+  cs.tiles_total = tiles;
+  if (cs.K_total > p->cap_K || cs.nm_total > p->cap_nm || cs.seg_total > p->cap_seg || cs.amp_total > p->cap_amp)
+    return EMRI_FD_ERR_CAPACITY;
+  if (!t || !phi_phi || !phi_r || !omega_phi || !omega_r || !theta || !phi || !prefactor || !dt) return EMRI_FD_ERR_ARG;
+  if (cs.nm_total > 0 && (!l || !m || !n || !amp)) return EMRI_FD_ERR_ARG;
+  if (cs.nf_total > 0 && (!h_plus || !h_cross)) return EMRI_FD_ERR_ARG;
+  for (int w = 0; w < n_wf; w++) {
+    // dt is read here on the host when it is host memory, else checked by the caller
+    if (!is_device_ptr(dt) && !(dt[w] > 0.0 && dt[w] < INFINITY)) return EMRI_FD_ERR_ARG;
+  }
+  DevInputs in{};
+  emri_fd_status st = EMRI_FD_OK;
+  const size_t kb = sizeof(double) * cs.K_total;
+  const void* q;
+#define STG(slot, ptr, bytes, field, type)                            \
+  if (st == EMRI_FD_OK) {                                               \
+    st = stage_in(p, slot, ptr, bytes, &q);                             \
+    in.field = static_cast<type>(q);                                    \
+  }
+  STG(0, t, kb, t, const double*);
+  STG(1, phi_phi, kb, phi_phi, const double*);
+  STG(2, phi_r, kb, phi_r, const double*);
+  STG(3, omega_phi, kb, omega_phi, const double*);
+  STG(4, omega_r, kb, omega_r, const double*);
+  STG(5, l, sizeof(int) * cs.nm_total, l, const int*);
+  STG(6, m, sizeof(int) * cs.nm_total, m, const int*);
+  STG(7, n, sizeof(int) * cs.nm_total, n, const int*);
+  STG(8, amp, 2 * sizeof(double) * cs.amp_total, amp, const double*);
+  STG(9, theta, sizeof(double) * n_wf, theta, const double*);
+  STG(10, phi, sizeof(double) * n_wf, phi, const double*);
+  STG(11, prefactor, sizeof(double) * n_wf, prefactor, const double*);
+#undef STG
+  if (st != EMRI_FD_OK) return st;
+  const void* dtd = nullptr;
+  if ((st = stage_in(p, 12, dt, sizeof(double) * n_wf, &dtd)) != EMRI_FD_OK) return st;
+  void *hpd = nullptr, *hcd = nullptr;
+  bool hph = false, hch = false;
+  const size_t ob = sizeof(float) * (size_t)cs.nf_total;
+  if ((st = stage_out(p, 13, h_plus, ob, &hpd, &hph)) != EMRI_FD_OK) return st;
+  if ((st = stage_out(p, 14, h_cross, ob, &hcd, &hch)) != EMRI_FD_OK) return st;
+  cudaStream_t stm = p->stream;
+  if (cudaMemcpyAsync(p->s.wf, p->wf_pinned, sizeof(WfInfo) * n_wf, cudaMemcpyHostToDevice, stm) != cudaSuccess ||
+      cudaEventRecord(p->wf_done, stm) != cudaSuccess)
+    return EMRI_FD_ERR_CUDA;
+  cudaMemsetAsync(p->s.counters, 0, 8 * sizeof(unsigned long long), stm);
+  cudaEvent_t* E = nullptr;
+  if (p->profiling && p->ev_used + 3 <= (int)p->ev.size()) {
+    E = &p->ev[p->ev_used];
+    p->ev_used += 3;
+    cudaEventRecord(E[0], stm);
+  }
+  if (cs.nm_total > 0) {
+    launch_prep_td(cs, in, p->s, p->tdamp, stm);
+    p->launches += 6;
+  }
+  if (E) cudaEventRecord(E[1], stm);
+  if (cs.nf_total > 0) {
+    if (cs.nm_total == 0) {
+      cudaMemsetAsync(hpd, 0, ob, stm);
+      cudaMemsetAsync(hcd, 0, ob, stm);
+    } else {
+      launch_td_sum(cs, in, p->s, p->tdamp, static_cast<const double*>(dtd), static_cast<float*>(hpd),
+                    static_cast<float*>(hcd), p->num_sms, stm);
+      p->launches += 1;
+    }
+  }
+  if (E) cudaEventRecord(E[2], stm);
+  if (cudaGetLastError() != cudaSuccess) return EMRI_FD_ERR_CUDA;
+  if ((hph && cudaMemcpyAsync(h_plus, hpd, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess) ||
+      (hch && cudaMemcpyAsync(h_cross, hcd, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess))
+    return EMRI_FD_ERR_CUDA;
+  if ((hph || hch) && cudaStreamSynchronize(stm) != cudaSuccess) return EMRI_FD_ERR_CUDA;
+  return EMRI_FD_OK;
+}
+
+emri_fd_status emri_fd_td_spectrum(emri_fd_plan_t p, int n_wf, const long long* sample_off, const double* t0,
+                                   const double* dt, int window, const float* h_plus, const float* h_cross,
+                                   void* H_plus, void* H_cross) {
+  if (!p || !p->desc.time_domain || n_wf < 1 || !sample_off || !t0 || !dt) return EMRI_FD_ERR_ARG;
+  if (window != EMRI_FD_WINDOW_NONE && window != EMRI_FD_WINDOW_HANN) return EMRI_FD_ERR_ARG;
+  if (is_device_ptr(t0) || is_device_ptr(dt) || !is_device_ptr(h_plus) || !is_device_ptr(h_cross) ||
+      !is_device_ptr(H_plus) || !is_device_ptr(H_cross))
+    return EMRI_FD_ERR_ARG;
+  if (sample_off[0] != 0) return EMRI_FD_ERR_ARG;
+  long long maxN = 0;
+  for (int w = 0; w < n_wf; w++) {
+    const long long N = sample_off[w + 1] - sample_off[w];
+    if (N < 0 || N > 2000000000LL || !(dt[w] > 0.0 && dt[w] < INFINITY) || !(fabs(t0[w]) < INFINITY))
+      return EMRI_FD_ERR_ARG;
+    if (N > maxN) maxN = N;
+  }
+  cudaStream_t stm = p->stream;
+  if (maxN > p->zcap) {
+    if (p->zbuf) { cudaStreamSynchronize(stm); cudaFree(p->zbuf); }
+    p->zbuf = nullptr;
+    p->zcap = 0;
+    if (cudaMalloc(&p->zbuf, sizeof(float2) * (size_t)maxN) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_OOM; }
+    p->zcap = maxN;
+  }
+  long long ho = 0;
+  for (int w = 0; w < n_wf; w++) {
+    const long long N = sample_off[w + 1] - sample_off[w];
+    if (N < 4) { continue; }
+    cufftHandle h = 0;
+    bool found = false;
+    for (auto& fp : p->fft_plans)
+      if (fp.first == N) { h = fp.second; found = true; }
+    if (!found) {
+      if (cufftPlan1d(&h, (int)N, CUFFT_C2C, 1) != CUFFT_SUCCESS) return EMRI_FD_ERR_CUDA;
+      p->fft_plans.emplace_back(N, h);
+    }
+    if (cufftSetStream(h, stm) != CUFFT_SUCCESS) return EMRI_FD_ERR_CUDA;
+    launch_td_pack(h_plus + sample_off[w], h_cross + sample_off[w], N, window, p->zbuf, p->num_sms, stm);
+    if (cufftExecC2C(h, reinterpret_cast<cufftComplex*>(p->zbuf), reinterpret_cast<cufftComplex*>(p->zbuf),
+                     CUFFT_INVERSE) != CUFFT_SUCCESS)
+      return EMRI_FD_ERR_CUDA;
+    launch_td_unpack(p->zbuf, N, dt[w], t0[w], static_cast<float2*>(H_plus) + ho, static_cast<float2*>(H_cross) + ho,
+                     p->num_sms, stm);
+    p->launches += 3;
+    ho += N / 2 - 1;
+  }
+  if (cudaGetLastError() != cudaSuccess) return EMRI_FD_ERR_CUDA;
   return EMRI_FD_OK;
 }
 

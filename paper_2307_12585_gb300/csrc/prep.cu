@@ -776,6 +776,44 @@ void launch_table_ff(const double2* tab, float4* tabf, cudaStream_t st) {
 
 void launch_scan(int* cnt, long long n, cudaStream_t st) { k_scan<<<1, 1024, 0, st>>>(cnt, n); }
 
+// TD comparator: per (mode, segment) FP32 u-coefficients of Re A and Im A
+// (unscaled: the prefactor is applied when the samples are stored)
+__global__ void k_td_amp(int n_wf, const WfInfo* wf, const ModeInfo* modes, DevInputs in, const double* ampM,
+                         long long seg_total, float4* tdamp) {
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= seg_total) return;
+  int lo = 0, hi = n_wf - 1;
+  while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (wf[mid].seg_base <= r) lo = mid; else hi = mid - 1; }
+  const WfInfo W = wf[lo];
+  const long long rr = r - W.seg_base, Km1 = W.K - 1;
+  const long long j = W.mo + rr / Km1;
+  const int s = (int)(rr - (rr / Km1) * Km1);
+  const ModeInfo Mi = modes[j];
+  const long long i0 = W.ko + s;
+  const double h = in.t[i0 + 1] - in.t[i0], h2 = h * h;
+  const double* am = ampM + 2 * (Mi.key_base + s);
+  const double* ay = in.amp + 2 * (Mi.key_base + s);
+  double cre[4], cim[4];
+  ucoef(ay[0], ay[2], am[0], am[2], h2, cre);
+  ucoef(ay[1], ay[3], am[1], am[3], h2, cim);
+  tdamp[2 * r] = make_float4((float)cre[0], (float)cre[1], (float)cre[2], (float)cre[3]);
+  tdamp[2 * r + 1] = make_float4((float)cim[0], (float)cim[1], (float)cim[2], (float)cim[3]);
+}
+
+void launch_prep_td(const CallShape& cs, const DevInputs& in, const DevScratch& s, float4* tdamp, cudaStream_t st) {
+  dim3 gk(8, cs.n_wf);
+  k_validate_knots<<<gk, 256, 0, st>>>(s.wf, in, s.status);
+  k_validate_amp<<<256, 256, 0, st>>>(2 * cs.amp_total, in.amp, s.status);
+  k_modes<<<(unsigned)((cs.nm_total + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes, cs.nm_total,
+                                                                  s.status);
+  k_spline_factor<<<(cs.n_wf * 32 + 127) / 128, 128, 0, st>>>(cs.n_wf, s.wf, in.t, s.spl_fac, s.spl_ih);
+  long long nser = 4LL * cs.n_wf + 2 * cs.nm_total;
+  k_spline_solve<<<(unsigned)((nser * 32 + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, s.modes, cs.nm_total, in, s.spl_fac,
+                                                                 s.spl_ih, s.fundM, cs.K_total, s.ampM, s.fund);
+  k_td_amp<<<(unsigned)((cs.seg_total + 127) / 128), 128, 0, st>>>(cs.n_wf, s.wf, s.modes, in, s.ampM, cs.seg_total,
+                                                                   tdamp);
+}
+
 void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st) {
   dim3 gk(8, cs.n_wf);
   k_validate_knots<<<gk, 256, 0, st>>>(s.wf, in, s.status);

@@ -11,8 +11,9 @@
 // memory with their indices, bitonic-sorted on the key (~bits(P), index)
 // (for P >= 0 the bit pattern orders like the value), summed in order by one
 // thread (the FP64 additions of the definition, in its order), and every
-// thread then marks its positions below the threshold with atomicOr, which
-// makes the union independent of the order in which CTAs finish.
+// thread then marks its positions below the threshold with atomicOr (skipped
+// when the flag is already set), which makes the union independent of the
+// order in which CTAs finish.
 #include "common.cuh"
 
 namespace emrifd {
@@ -86,8 +87,12 @@ __global__ void __launch_bounds__(1024) k_select(const WfInfo* wf, const double*
     thr = __dmul_rn(__dsub_rn(1.0, eps), s);
   }
   __syncthreads();
-  for (int i = tid; i < nm; i += nt)
-    if (S[i] < thr) atomicOr(keep + W.mo + idx[i], 1);
+  // a mode kept at many knots is set once: the plain read skips the atomic when an
+  // earlier CTA has already set it (a stale 0 only costs a redundant atomicOr)
+  for (int i = tid; i < nm; i += nt) {
+    int* dst = keep + W.mo + idx[i];
+    if (S[i] < thr && *reinterpret_cast<volatile int*>(dst) == 0) atomicOr(dst, 1);
+  }
 }
 
 }  // namespace
