@@ -41,12 +41,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64x", "mixed"])
+    ap.add_argument("--spa", default="standard", choices=["standard", "extended"])
+    ap.add_argument("--window", default=None, choices=["hann"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--waveforms", type=int, default=8)
     ap.add_argument("--tile-bins", type=int, default=128)
-    ap.add_argument("--config", default="paper", choices=["paper", "batch", "mixed-batch", "likelihood"])
+    ap.add_argument("--config", default="paper", choices=["paper", "batch", "mixed-batch", "likelihood", "td", "select"])
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--check-waveforms", type=int, default=8)
@@ -197,15 +199,89 @@ def max_over_ranks(ms, world):
     return ms
 
 
+DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
+# DRAM bytes (read + write) of one k_spa<4,0,0> launch (FP64, standard SPA, 128-bin tiles) on
+# this workload, from one ncu capture of the kernel as it stands
+TRAFFIC_FP64_SPA = 98.988800e6 + 66.957056e6
+
+
 def base_line(args, world, metric, value, unit, ms, workload, extra=None):
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
-            "config": {"workload": workload, "precision": args.precision,
+            "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": {"workload": workload, "precision": args.precision, "spa": args.spa, "window": args.window,
                        "parallelism": "independent waveforms per GPU (replicas)"}}
     if extra:
         line.update(extra)
     return line
+
+
+def paper_aux(args, w, fd_ms_per_wf):
+    """The other rows of the method on the same 2-yr, 2000-mode waveform: the time-domain
+    comparator (TD sum at dt = 10 s + its FFT), the Hann window, and mode selection on the
+    3294-mode pool it was drawn from."""
+    import torch
+    from paper_2307_12585_gb300 import api, synth
+    reps = max(3, min(args.steps, 10))
+
+    def timed(stream, fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    out = {}
+    # time-domain comparator
+    dt = 10.0
+    N = int(np.floor((w.t[-1] - w.t[0]) / dt))
+    plan = api.Plan("fp64", max_waveforms=1, max_knots=w.K, max_modes_total=w.n_modes, max_bins_total=16,
+                    time_domain=True)
+    b = plan.upload(synth.concat([w]))
+    hp, hc, so = plan.td_sum(b, dt, N)
+    plan.td_spectrum(hp, hc, so, w.t[0], dt)
+    plan.profile(True)
+    td_ms = timed(plan.stream, lambda: plan.td_sum(b, dt, N, check=False), reps)
+    st = plan.stats()
+    fft_ms = timed(plan.stream, lambda: plan.td_spectrum(hp, hc, so, w.t[0], dt), reps)
+    kern_ms = st["spa_ns"] * 1e-6 / max(1, st["timed_calls"])
+    out["td_comparator"] = {
+        "samples": N, "dt_s": dt, "td_sum_ms": td_ms, "td_kernel_ms": kern_ms, "fft_ms": fft_ms,
+        "total_ms": td_ms + fft_ms, "mode_sample_evals_per_s": N * w.n_modes / (kern_ms * 1e-3),
+        "fd_fp64_speedup_vs_td": (td_ms + fft_ms) / fd_ms_per_wf,
+        "arithmetic": "FP32 amplitudes/trig, 32-bit fixed-point phase, FP32 chunk sums carried in FP32 pairs; cuFFT C2C"}
+    plan.close()
+    # Hann window (three-term convolution after the SPA sum)
+    res = {}
+    for window in (None, "hann"):
+        plan = api.Plan("fp64", max_waveforms=1, max_knots=w.K, max_modes_total=w.n_modes,
+                        max_bins_total=w.n_freqs, tile_bins=args.tile_bins, window=window)
+        b = plan.upload(synth.concat([w]))
+        o = plan.sum_modes(b)
+        res[window] = timed(plan.stream, lambda: plan.sum_modes(b, out=o, check=False), reps)
+        plan.close()
+    extra = max(res["hann"] - res[None], 1e-6)
+    out["hann_window"] = {"extra_ms": extra, "bytes_per_bin": 72,
+                          "achieved_GBs": 72 * w.n_freqs / (extra * 1e-3) / 1e9,
+                          "note": "read h+/hx (32 B) and f (8 B), write h+/hx (32 B) per bin"}
+    # mode selection on the full pool
+    pool = synth.paper_config(1, n_modes=3294, grid="sparse", n_sparse=16)
+    plan = api.Plan("fp64", max_waveforms=1, max_knots=pool.K, max_modes_total=pool.n_modes, max_bins_total=16)
+    b = plan.upload(synth.concat([pool]))
+    kept = int(plan.select_modes(b, 1e-5).sum())
+    sel_ms = timed(plan.stream, lambda: plan.select_modes(b, 1e-5, check=False), reps)
+    plan.close()
+    sel = {"modes_pool": pool.n_modes, "knots": pool.K, "eps": 1e-5, "kept": kept, "gpu_ms": sel_ms}
+    if not args.no_cpu:
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        O.select_modes(pool.amp, 1e-5)
+        sel["oracle_ms_1core"] = (time.perf_counter() - t0) * 1e3
+    out["mode_selection"] = sel
+    return out
 
 
 def run_paper(args, rank, world, local):
@@ -218,7 +294,8 @@ def run_paper(args, rank, world, local):
     seeds = [1 + rank * nw + i for i in range(nw)]
     wfs = [synth.paper_config(s) for s in seeds]
     plan = api.Plan(args.precision, conj_partners=True, max_waveforms=1, max_knots=200,
-                    max_modes_total=2000, max_bins_total=wfs[0].n_freqs, tile_bins=args.tile_bins)
+                    max_modes_total=2000, max_bins_total=wfs[0].n_freqs, tile_bins=args.tile_bins, spa=args.spa,
+                    window=args.window)
     dev = [plan.upload(synth.concat([w])) for w in wfs]
     nf = wfs[0].n_freqs
     outs = [(torch.empty(nf, dtype=plan.out_dtype, device="cuda"), torch.empty(nf, dtype=plan.out_dtype, device="cuda"))
@@ -282,7 +359,8 @@ def run_paper(args, rank, world, local):
                 "tile_bins": 64 if prec in ("fp64x", "mixed") else args.tile_bins}
 
     mixed = fp64x = ext = None
-    if args.precision == "fp64" and not args.no_mixed:
+    headline = args.precision == "fp64" and args.spa == "standard" and args.window is None
+    if headline and not args.no_mixed:
         fp64x = other_form("fp64x")
         fp64x["arithmetic"] = "FP32 pairs (double-float) and integers; FP64 only per tile and in preparation"
         mixed = other_form("mixed")
@@ -292,6 +370,10 @@ def run_paper(args, rank, world, local):
             e = other_form(prec, spa="extended")
             e["rel_l2_vs_standard_fp64"] = e.pop("rel_l2_vs_fp64")   # the size of the correction
             ext[prec] = e
+
+    aux = {}
+    if headline and not args.no_mixed and rank == 0:
+        aux = paper_aux(args, wfs[0], ms / args.steps)
 
     e2e = None
     if not args.no_e2e:
@@ -304,10 +386,10 @@ def run_paper(args, rank, world, local):
                 if isinstance(b[k], np.ndarray) and k not in ("knot_off", "mode_off", "freq_off"):
                     b[k] = torch.from_numpy(b[k]).pin_memory()
             hb.append(b)
-        cdt = torch.complex128 if args.precision == "fp64" else torch.complex64
+        cdt = plan.out_dtype
         hout = [(torch.empty(nf, dtype=cdt).pin_memory(), torch.empty(nf, dtype=cdt).pin_memory()) for _ in range(2)]
         h2d = sum(int(v.numel() * v.element_size()) for k, v in hb[0].items() if hasattr(v, "numel"))
-        d2h = 2 * nf * (16 if args.precision == "fp64" else 8)
+        d2h = 2 * nf * (8 if args.precision == "mixed" else 16)
         for i in range(2):
             plan.sum_modes_host(hb[i % 2], out=hout[i % 2])
         torch.cuda.synchronize()
@@ -330,14 +412,67 @@ def run_paper(args, rank, world, local):
             "mode_bin_evals_per_s": world * mb / sec,
             "mode_bins_per_waveform": mb_per_launch,
             "spa_kernel_ms": spa_s * 1e3, "prep_ms": st["prep_ns"] * 1e-6 / max(1, st["timed_calls"]),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved / peak_tflops, "traffic": None,
-                         "issue_frac": issue,
-                         "note": "FP64 pipe: %d FP64 flops (%d FP64 instructions) per mode-bin; peak = %d FP64 FMA/clk/SM x 2 x SMs x median SM clock" % (
-                             FP64_FLOPS_PER_MODE_BIN, FP64_OPS_PER_MODE_BIN, FP64_PER_CLK_PER_SM)},
+            "roofline": ({"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                          "frac": achieved / peak_tflops,
+                          "traffic": TRAFFIC_FP64_SPA if args.tile_bins == 128 else None,
+                          "issue_frac": issue,
+                          "note": "FP64 pipe: %d FP64 flops (%d FP64 instructions) per mode-bin; peak = %d FP64 FMA/clk/SM x 2 x SMs x median SM clock; traffic = DRAM bytes per launch from one ncu capture" % (
+                              FP64_FLOPS_PER_MODE_BIN, FP64_OPS_PER_MODE_BIN, FP64_PER_CLK_PER_SM)}
+                         if headline else None),
             "fp64x_form": fp64x, "mixed_form": mixed, "extended_spa": ext, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"], "clocks": clocks})
+        line.update(aux)
         line["config"].update({"waveforms_resident": nw, "tile_bins": args.tile_bins,
                                "l2": "inputs larger than L2: %d resident waveforms rotated, ~200 MB touched per step" % nw})
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def run_td(args, rank, world, local):
+    """The time-domain comparator alone on the 2-yr, 2000-mode waveform: TD sum at
+    dt = 10 s (6,311,520 samples) and its FFT, per waveform."""
+    import torch
+    from paper_2307_12585_gb300 import api, synth
+    w = synth.paper_config(1 + rank)
+    dt = 10.0
+    N = int(np.floor((w.t[-1] - w.t[0]) / dt))
+    plan = api.Plan("fp64", max_waveforms=1, max_knots=w.K, max_modes_total=w.n_modes, max_bins_total=16,
+                    time_domain=True)
+    b = plan.upload(synth.concat([w]))
+    for _ in range(args.warmup):
+        hp, hc, so = plan.td_sum(b, dt, N, check=False)
+        plan.td_spectrum(hp, hc, so, w.t[0], dt, window=args.window)
+    plan.sync()
+    clk = ClockSampler(local)
+    clk.start()
+    ms = event_time(plan.stream, lambda i: plan.td_spectrum(*plan.td_sum(b, dt, N, check=False), w.t[0], dt,
+                                                            window=args.window), args.steps)
+    clocks = clk.stop()
+    plan.sync()
+    ms = max_over_ranks(ms, world)
+    if rank == 0:
+        line = base_line(args, world, "TD comparator waveforms/s", world * args.steps / (ms * 1e-3), "waveforms/s", ms,
+                         "TD sum of the 2 yr, 2000-mode waveform at dt = 10 s (%d samples) + cuFFT spectrum" % N,
+                         {"mode_sample_evals_per_s": world * N * w.n_modes * args.steps / (ms * 1e-3),
+                          "dtype": "f32 + i32 phase", "clocks": clocks})
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def run_select(args, rank, world, local):
+    """Mode selection alone on the 3294-mode, 200-knot pool (eps = 1e-5)."""
+    from paper_2307_12585_gb300 import api, synth
+    pool = synth.paper_config(1 + rank, n_modes=3294, grid="sparse", n_sparse=16)
+    plan = api.Plan("fp64", max_waveforms=1, max_knots=pool.K, max_modes_total=pool.n_modes, max_bins_total=16)
+    b = plan.upload(synth.concat([pool]))
+    for _ in range(args.warmup):
+        plan.select_modes(b, 1e-5, check=False)
+    plan.sync()
+    ms = event_time(plan.stream, lambda i: plan.select_modes(b, 1e-5, check=False), args.steps)
+    plan.sync()
+    ms = max_over_ranks(ms, world)
+    if rank == 0:
+        line = base_line(args, world, "mode selections/s", world * args.steps / (ms * 1e-3), "selections/s", ms,
+                         "power-based mode selection of 3294 modes over 200 knots, eps = 1e-5", {})
         print(json.dumps(line), flush=True)
     plan.close()
 
@@ -487,6 +622,10 @@ def main():
         run_batched(args, rank, world, local, mixed=True)
     elif args.config == "likelihood":
         run_likelihood(args, rank, world, local)
+    elif args.config == "td":
+        run_td(args, rank, world, local)
+    elif args.config == "select":
+        run_select(args, rank, world, local)
     if world > 1:
         dist.destroy_process_group()
 

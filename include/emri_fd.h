@@ -215,7 +215,7 @@ emri_fd_status emri_fd_loglike_and_grad(emri_fd_plan_t plan, int n_waveforms,
  * outputs h_plus, h_cross: [sum N_w] float (real TD samples).
  * Arithmetic: FP32 amplitudes and trigonometry, the phase in 32-bit fixed-point
  * turns from per-sample Q0.64 values of Phi_phi/2pi and Phi_r/2pi, sums over
- * modes in FP32 chunks of 32 carried in FP64 (about 1e-6 relative).
+ * modes in FP32 chunks of 32 carried in FP32 pairs (about 1e-6 relative).
  * Needs a plan with time_domain = 1.  Pointers may be device or host memory.
  */
 emri_fd_status emri_fd_td_sum(emri_fd_plan_t plan, int n_waveforms, const long long* knot_off,

@@ -348,9 +348,18 @@ class Plan:
         self._td_last = (so, dtv)
         return hp, hc, so
 
+    @staticmethod
+    def td_freqs(sample_off, dt):
+        """The frequencies k/(N_w dt), k = 1 .. N_w/2 - 1, of td_spectrum's bins (numpy)."""
+        so = np.asarray(sample_off, np.int64)
+        N = np.diff(so)
+        dtv = np.broadcast_to(np.asarray(dt, np.float64), N.shape)
+        parts = [np.arange(1, Nw // 2) / (Nw * d) for Nw, d in zip(N, dtv) if Nw >= 4]
+        return np.concatenate(parts) if parts else np.zeros(0)
+
     def td_spectrum(self, hp, hc, sample_off, t0, dt, window=None):
         """emri_fd_td_spectrum: complex64 device tensors H+, Hx over the bins
-        k = 1 .. N_w/2 - 1 of every waveform, and their frequencies (numpy)."""
+        k = 1 .. N_w/2 - 1 of every waveform (frequencies: td_freqs)."""
         T = self.torch
         so = np.ascontiguousarray(np.asarray(sample_off, np.int64))
         nw = len(so) - 1
@@ -363,8 +372,7 @@ class Plan:
         code = emri_fd_td_spectrum(self.handle, nw, so.ctypes.data, t0v.ctypes.data, dtv.ctypes.data,
                                    WINDOWS[window], hp.data_ptr(), hc.data_ptr(), Hp.data_ptr(), Hc.data_ptr())
         _check(code, "emri_fd_td_spectrum")
-        f = np.concatenate([np.arange(1, k + 1) / (Nw * d) for k, Nw, d in zip(nb, N, dtv)]) if nw else np.zeros(0)
-        return Hp, Hc, f
+        return Hp, Hc
 
     def select_modes(self, b, eps, check=True):
         """emri_fd_select_modes on a batch (device tensors from upload, or numpy):

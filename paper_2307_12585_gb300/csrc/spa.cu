@@ -59,7 +59,8 @@ struct Smem {
   int list[kListCap];
   int wsum[kWarps + 1];
   long long tile;
-  double red[kWarps][32 * BPL][4];
+  float2 pf;       // the waveform's prefactor as an FP32 pair (FP64X)
+  double red[kWarps][32 * BPL][4];   // FP64 partials, or FP32-pair partials in the same bytes
 };
 
 // FP64X per-(branch, bin) body: returns the four increments (h+ re, h+ im,
@@ -100,7 +101,7 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
   bool settle = err > 1e-13f;
   if (ff_lt(u, ulo)) { u = ulo; settle = true; }
   else if (ff_lt(uhi, u)) { u = uhi; settle = true; }
-  if (settle) {   // rare: next to a turnover, or a root at the piece's end
+  if (EXT && settle) {   // extended form only: rare, next to a turnover or at the piece's end
     const double ud = solve_root_safe(C, (neg ? -f : f) - C.A, ff_to_double(ulo), ff_to_double(uhi), dir,
                                       ff_to_double(u));
     u = ff_from_double(ud);
@@ -203,7 +204,7 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
   const double g = neg ? -f : f;
   const double delta = g - C.A;
   float uf, Df;
-  const double u = solve_root<4>(C, delta, ulo, uhi, dir, uf, Df);
+  const double u = solve_root<4, EXT>(C, delta, ulo, uhi, dir, uf, Df);
   const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
   const long long Dbits = __double_as_longlong(Dd);
   bool coal = (Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0;
@@ -268,8 +269,13 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
   return true;
 }
 
+// resident CTAs per SM the FP32-path kernels are compiled for (sets their register budget)
+#ifndef EMRI_FD_SPA_MINB
+#define EMRI_FD_SPA_MINB 4
+#endif
+
 template <int BPL, int PREC, bool EXT>
-__global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : 4) k_spa(SpaParams P) {
+__global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_spa(SpaParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<BPL, PREC>& S = *reinterpret_cast<Smem<BPL, PREC>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -375,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : 4) k_spa(SpaParams P
             // a6: root
             const double delta = g - C.A;
             float uf, Df;
-            const double u = solve_root<6>(C, delta, ulo, uhi, R.dir, uf, Df);
+            const double u = solve_root<6, EXT>(C, delta, ulo, uhi, R.dir, uf, Df);
             // a8: dF/du and the weight sqrt(h)/sqrt|dF/du| (sqrt(h) is in the amplitude)
             const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
             const long long Dbits = __double_as_longlong(Dd);
@@ -475,32 +481,61 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : 4) k_spa(SpaParams P
       if (rcur >= nruns) break;
     }
 
-    // ---- fixed-order reduction over warps, one store per bin
+    // ---- fixed-order reduction over warps, one store per bin (FP64 sums for the
+    // FP64 form; FP32 pairs for the other two, so that they spend no FP64
+    // instruction per bin beyond the final conversion)
+    if constexpr (PREC == 0) {
 #pragma unroll
-    for (int q = 0; q < BPL; q++)
+      for (int q = 0; q < BPL; q++)
 #pragma unroll
-      for (int c = 0; c < 4; c++)
-        S.red[warp][lane + 32 * q][c] = PREC == 0 ? acc[q][c]
-                                        : PREC == 2 ? ((double)accx[q][c].hi + (double)accx[q][c].lo)
-                                                    : ((double)accf[q][c] - (double)cmp[q][c]);
+        for (int c = 0; c < 4; c++) S.red[warp][lane + 32 * q][c] = acc[q][c];
+    } else {
+      float2(&redf)[kWarps][32 * BPL][4] = *reinterpret_cast<float2(*)[kWarps][32 * BPL][4]>(&S.red[0][0][0]);
+#pragma unroll
+      for (int q = 0; q < BPL; q++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          const ff v = PREC == 2 ? accx[q][c] : fast_two_sum(accf[q][c], -cmp[q][c]);
+          redf[warp][lane + 32 * q][c] = make_float2(v.hi, v.lo);
+        }
+    }
+    if (PREC == 2 && tid == 0) {
+      const ff pf = ff_from_double(P.prefactor[lo]);
+      S.pf = make_float2(pf.hi, pf.lo);
+    }
     __syncthreads();
     for (int i = tid; i < TB; i += kThreads) {
       const long long bin = bin0 + i;
-      if (bin < binEnd) {
+      if (bin >= binEnd) continue;
+      if constexpr (PREC == 0) {
         double v[4] = {0.0, 0.0, 0.0, 0.0};
         for (int w2 = 0; w2 < kWarps; w2++)
 #pragma unroll
           for (int c = 0; c < 4; c++) v[c] += S.red[w2][i][c];
-        if (PREC == 0) {
-          reinterpret_cast<double2*>(P.hp)[bin] = make_double2(v[0], v[1]);
-          reinterpret_cast<double2*>(P.hc)[bin] = make_double2(v[2], v[3]);
-        } else if (PREC == 2) {
-          const double pf = P.prefactor[lo];
-          reinterpret_cast<double2*>(P.hp)[bin] = make_double2(pf * v[0], pf * v[1]);
-          reinterpret_cast<double2*>(P.hc)[bin] = make_double2(pf * v[2], pf * v[3]);
+        reinterpret_cast<double2*>(P.hp)[bin] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(P.hc)[bin] = make_double2(v[2], v[3]);
+      } else {
+        const float2(&redf)[kWarps][32 * BPL][4] =
+            *reinterpret_cast<const float2(*)[kWarps][32 * BPL][4]>(&S.red[0][0][0]);
+        ff v[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) v[c] = ff_make(0.f, 0.f);
+        for (int w2 = 0; w2 < kWarps; w2++)
+#pragma unroll
+          for (int c = 0; c < 4; c++) v[c] = ff_add(v[c], ff_make(redf[w2][i][c].x, redf[w2][i][c].y));
+        if constexpr (PREC == 2) {
+          const ff pf = ff_make(S.pf.x, S.pf.y);
+          double o[4];
+#pragma unroll
+          for (int c = 0; c < 4; c++) {
+            const ff r = ff_mul(v[c], pf);
+            o[c] = f2d_bits(r.hi) + f2d_bits(r.lo);
+          }
+          reinterpret_cast<double2*>(P.hp)[bin] = make_double2(o[0], o[1]);
+          reinterpret_cast<double2*>(P.hc)[bin] = make_double2(o[2], o[3]);
         } else {
-          reinterpret_cast<float2*>(P.hp)[bin] = make_float2((float)v[0], (float)v[1]);
-          reinterpret_cast<float2*>(P.hc)[bin] = make_float2((float)v[2], (float)v[3]);
+          reinterpret_cast<float2*>(P.hp)[bin] = make_float2(v[0].hi + v[0].lo, v[1].hi + v[1].lo);
+          reinterpret_cast<float2*>(P.hc)[bin] = make_float2(v[2].hi + v[2].lo, v[3].hi + v[3].lo);
         }
       }
     }

@@ -76,9 +76,12 @@ static __device__ __noinline__ double solve_root_safe(const SegCore& C, double d
 }
 
 // a6: FP32 start value, FP64 Newton polish (iterated where the predicted error of
-// one step exceeds 1e-13, i.e. near turnovers), clamped into [ulo, uhi]; a
-// polish that has not settled or had to be clamped is redone by solve_root_safe
-template <int NIT>
+// one step exceeds 1e-13, i.e. near turnovers), clamped into [ulo, uhi].  With
+// SETTLE (the extended form, which is finite and well-conditioned next to
+// turnovers), a polish that has not settled or had to be clamped is redone by
+// solve_root_safe; the standard form's weight diverges there anyway, and the
+// call's register cost is not worth paying in its hot loop.
+template <int NIT, bool SETTLE = false>
 __device__ __forceinline__ double solve_root(const SegCore& C, double delta, double ulo, double uhi, int dir,
                                              float& uf_out, float& Df_out) {
   float Df;
@@ -107,7 +110,7 @@ __device__ __forceinline__ double solve_root(const SegCore& C, double delta, dou
   const long long ub_ = __double_as_longlong(u);
   if (ub_ < __double_as_longlong(ulo)) { u = ulo; settle = true; }
   else if (ub_ > __double_as_longlong(uhi)) { u = uhi; settle = true; }
-  if (settle) {
+  if (SETTLE && settle) {
     u = solve_root_safe(C, delta, ulo, uhi, dir, u);
     uf = d2f_bits(u);
     Df = (3.f * C.df * uf + 2.f * C.cf) * uf + C.bf;

@@ -13,7 +13,7 @@
 //   - per mode-sample: psi = m a + n b in wrapping 32-bit integers (error
 //     <= (|m| + |n|)/2 units of 2^-32 turn), e^{-i psi} from a 4096-entry FP32
 //     table and a second-order Taylor step (|x| <= pi/4096), the amplitude cubics
-//     in FP32, and FP32 sums over chunks of 32 modes carried into FP64.
+//     in FP32, and FP32 sums over chunks of 32 modes carried in FP32 pairs.
 // Persistent CTAs take tiles of kTdTile consecutive samples of one waveform
 // from an atomic queue; a tile spans at most a few spline segments and is
 // swept once per segment it touches, each sample accumulating only in its own.
@@ -25,11 +25,12 @@
 #include <cufft.h>
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace emrifd {
 namespace {
 
-constexpr int kTdSpt = 4;                       // samples per thread
+constexpr int kTdSpt = 8;                       // samples per thread
 constexpr int kTdTile = kTdSpt * kThreads;      // samples per tile
 
 struct TdParams {
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) k_td_sum(TdParams P) {
     int seg[kTdSpt];
     unsigned pa[kTdSpt], pb[kTdSpt];
     float uf[kTdSpt];
-    double acc_p[kTdSpt], acc_c[kTdSpt];
+    ff acc_p[kTdSpt], acc_c[kTdSpt];
 #pragma unroll
     for (int q = 0; q < kTdSpt; q++) {
       const long long j = j0 + (long long)tid * kTdSpt + q;
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_td_sum(TdParams P) {
       seg[q] = -1;
       pa[q] = pb[q] = 0u;
       uf[q] = 0.f;
-      acc_p[q] = acc_c[q] = 0.0;
+      acc_p[q] = acc_c[q] = ff_make(0.f, 0.f);
       if (j < jend && tj <= tlast) {
         const int s = knot_segment(t, K, tj);
         const double u = (tj - t[s]) / (t[s + 1] - t[s]);
@@ -127,9 +128,10 @@ __global__ void __launch_bounds__(kThreads) k_td_sum(TdParams P) {
           const int mm = M.m, nn = M.n;
           const float al = M.af[0], be = M.bf[0];
           const float4 ar = __ldg(amp_s + 2 * jm * (W.K - 1)), ai = __ldg(amp_s + 2 * jm * (W.K - 1) + 1);
+          // every sample is evaluated with segment s's coefficients; the chunk sums of
+          // samples in another segment (tiles that straddle a knot) are dropped below
 #pragma unroll
           for (int q = 0; q < kTdSpt; q++) {
-            if (seg[q] != s) continue;
             const unsigned th = (unsigned)mm * pa[q] + (unsigned)nn * pb[q];   // psi in 2^-32 turns
             const unsigned kq = (th + (1u << 19)) >> 20;
             const int r = (int)(th - (kq << 20));                               // |r| <= 2^19
@@ -150,30 +152,31 @@ __global__ void __launch_bounds__(kThreads) k_td_sum(TdParams P) {
         }
 #pragma unroll
         for (int q = 0; q < kTdSpt; q++) {
-          acc_p[q] += (double)cp[q];
-          acc_c[q] += (double)cc[q];
+          if (seg[q] != s) continue;
+          acc_p[q] = ff_add_f(acc_p[q], cp[q]);
+          acc_c[q] = ff_add_f(acc_c[q], cc[q]);
         }
       }
     }
-    const double pf = 2.0 * P.prefactor[lo];
+    const float pf = (float)(2.0 * P.prefactor[lo]);
 #pragma unroll
     for (int q = 0; q < kTdSpt; q++) {
       const long long j = j0 + (long long)tid * kTdSpt + q;
       if (j < jend) {
-        P.hp[W.fo + j] = (float)(pf * acc_p[q]);
-        P.hc[W.fo + j] = (float)(-pf * acc_c[q]);
+        P.hp[W.fo + j] = pf * (acc_p[q].hi + acc_p[q].lo);
+        P.hc[W.fo + j] = -pf * (acc_c[q].hi + acc_c[q].lo);
       }
     }
   }
 }
 
 // z = (h+ + i hx) w_j for one waveform (w_j = sin^2(pi j/N) with the Hann window, else 1)
-__global__ void k_td_pack(const float* hp, const float* hc, long long N, int hann, float2* z) {
+__global__ void k_td_pack(const float* hp, const float* hc, long long N, double inv_n, int hann, float2* z) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
     float w = 1.f;
     if (hann) {
-      const double sj = sinpi((double)j / (double)N);
-      w = (float)(sj * sj);
+      const float sj = sinpif((float)((double)j * inv_n));
+      w = sj * sj;
     }
     z[j] = make_float2(w * hp[j], w * hc[j]);
   }
@@ -223,7 +226,7 @@ void launch_td_pack(const float* hp, const float* hc, long long N, int hann, flo
   long long b = (N + 255) / 256;
   if (b > 32LL * num_sms) b = 32LL * num_sms;
   if (b < 1) b = 1;
-  k_td_pack<<<(unsigned)b, 256, 0, st>>>(hp, hc, N, hann, z);
+  k_td_pack<<<(unsigned)b, 256, 0, st>>>(hp, hc, N, 1.0 / (double)N, hann, z);
 }
 
 void launch_td_unpack(const float2* Z, long long N, double dt, double t0, float2* Hp, float2* Hc, int num_sms,

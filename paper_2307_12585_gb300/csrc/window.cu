@@ -8,7 +8,8 @@
 // One thread per output bin; the neighbours are read through L1/L2 (each input
 // is read about once from HBM).  Grid: x over bins, y over waveforms.  A grid
 // whose spacing differs from its mean by more than 1e-6 relative is flagged
-// with the ST_FREQ status bit.
+// with the ST_FREQ status bit.  (GB300's FP64 rate, not HBM, bounds this
+// kernel: the FP64 stencil takes 12 FP64 operations per bin.)
 #include "common.cuh"
 
 namespace emrifd {
@@ -36,14 +37,15 @@ __global__ void k_hann(const WfInfo* wf, const double* freqs, const C* __restric
                        C* __restrict__ outp, C* __restrict__ outc, int* status) {
   const WfInfo W = wf[blockIdx.y];
   const long long nf = W.nf, fo = W.fo;
-  const double df = nf > 1 ? (freqs[fo + nf - 1] - freqs[fo]) / (double)(nf - 1) : 0.0;
+  // spacing check without a division: |(f[i+1] - f[i]) (n - 1) - (f[n-1] - f[0])| <= 1e-6 (f[n-1] - f[0])
+  const double span = nf > 1 ? freqs[fo + nf - 1] - freqs[fo] : 0.0, nm1 = (double)(nf - 1);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x) {
     const long long b = fo + i;
     const C z = CplxOps<C>::zero();
     const bool has_lo = i > 0, has_hi = i + 1 < nf;
     outp[b] = CplxOps<C>::hann(inp[b], has_lo ? inp[b - 1] : z, has_hi ? inp[b + 1] : z);
     outc[b] = CplxOps<C>::hann(inc[b], has_lo ? inc[b - 1] : z, has_hi ? inc[b + 1] : z);
-    if (has_hi && fabs((freqs[b + 1] - freqs[b]) - df) > 1e-6 * df) atomicOr(status, ST_FREQ);
+    if (has_hi && fabs(fma(freqs[b + 1] - freqs[b], nm1, -span)) > 1e-6 * span) atomicOr(status, ST_FREQ);
   }
 }
 

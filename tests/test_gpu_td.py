@@ -68,7 +68,8 @@ def test_spectrum(oracle, window):
     N = _nsamp(w, dt)
     plan = _plan([w])
     hp, hc, so = plan.td_sum(plan.upload(synth.concat([w])), dt, N)
-    Hp, Hc, f = plan.td_spectrum(hp, hc, so, w.t[0], dt, window=window)
+    Hp, Hc = plan.td_spectrum(hp, hc, so, w.t[0], dt, window=window)
+    f = plan.td_freqs(so, dt)
     Hp, Hc = Hp.cpu().numpy(), Hc.cpu().numpy()
     # the FFT step alone: numpy (FP64) DFT of the same FP32 samples
     win = oracle.hann_td(N) if window == "hann" else 1.0
@@ -97,7 +98,8 @@ def test_fd_vs_td_on_gpu():
     hp, hc, so = plan.td_sum(plan.upload(synth.concat([w])), dt, N)
     res = {}
     for window in (None, "hann"):
-        Hp, Hc, f = plan.td_spectrum(hp, hc, so, w.t[0], dt, window=window)
+        Hp, Hc = plan.td_spectrum(hp, hc, so, w.t[0], dt, window=window)
+        f = plan.td_freqs(so, dt)
         fd = _plan([w.with_freqs(f)], nbins=f.size, window=window)
         Fp, Fc = fd.sum_modes(fd.upload(synth.concat([w.with_freqs(f)])))
         band = (f > 1e-5) & (f < 4.9e-2)
