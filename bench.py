@@ -547,7 +547,7 @@ def run_batched(args, rank, world, local, mixed):
         p64.close()
     if rank == 0:
         line = base_line(args, world, "waveforms/s", world * nb * args.steps / sec, "waveforms/s", ms, workload, extra)
-        line["dtype"] = "f64" if prec == "fp64" else "f64+f32"
+        line["dtype"] = DTYPES[prec]
         line["config"]["precision"] = prec
         print(json.dumps(line), flush=True)
     g.close()
