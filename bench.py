@@ -190,13 +190,27 @@ def event_time(stream, fn, steps):
 
 
 def max_over_ranks(ms, world):
+    """The slowest rank's time (the whole job's time); one all-reduce of a scalar, on the
+    process group's own device (CUDA for NCCL, the host for gloo)."""
     import torch
     import torch.distributed as dist
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     return ms
+
+
+def rank_seeds(rank, nw, base=1):
+    """Seeds of the waveforms rank `rank` holds: independent problems, disjoint across
+    ranks (weak scaling: every rank does the same amount of work)."""
+    return [base + rank * nw + i for i in range(nw)]
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
 
 
 DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
@@ -291,7 +305,7 @@ def run_paper(args, rank, world, local):
     from paper_2307_12585_gb300 import api, synth
 
     nw = args.waveforms
-    seeds = [1 + rank * nw + i for i in range(nw)]
+    seeds = rank_seeds(rank, nw)
     wfs = [synth.paper_config(s) for s in seeds]
     plan = api.Plan(args.precision, conj_partners=True, max_waveforms=1, max_knots=200,
                     max_modes_total=2000, max_bins_total=wfs[0].n_freqs, tile_bins=args.tile_bins, spa=args.spa,
@@ -323,7 +337,7 @@ def run_paper(args, rank, world, local):
     ms = max_over_ranks(ms, world)
     mb = sum(mode_bins[i % nw] for i in range(args.steps))
     sec = ms * 1e-3
-    value = world * args.steps / sec
+    value = job_rate(args.steps, world, ms)
     spa_s = st["spa_ns"] * 1e-9 / max(1, st["timed_calls"])
     mb_per_launch = mb / args.steps
     clk_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
