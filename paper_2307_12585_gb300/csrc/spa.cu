@@ -29,6 +29,15 @@
 namespace emrifd {
 namespace {
 
+// FP32 Newton steps of the FP64X root's start value (the pair polish that follows
+// iterates until its predicted error is below 1e-13)
+#ifndef EMRI_FD_X_ROOT_NIT
+#define EMRI_FD_X_ROOT_NIT 4
+#endif
+
+constexpr int kRpt = 4;   // runs tested per thread and pass when a tile collects its entries
+static_assert(2 * kRpt * kThreads <= kListCap, "a pass must fit the entry list");
+
 struct SpaParams {
   const WfInfo* wf;
   int n_wf;
@@ -74,7 +83,7 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
   const ff dl = ff_sub(gx, Ax);
   // a6: FP32 start, then Newton with the residual in FP32 pairs
   float Df;
-  const float uf = root_f32<4>(C.bf, C.cf, C.df, dl.hi, ulo.hi, uhi.hi, dir, Df);
+  const float uf = root_f32<EMRI_FD_X_ROOT_NIT>(C.bf, C.cf, C.df, dl.hi, ulo.hi, uhi.hi, dir, Df);
   ff t = ff_add(ff_mul_f(dx, uf), cx_);
   t = ff_add(ff_mul_f(t, uf), bx);
   ff res = ff_sub(ff_mul_f(t, uf), dl);
@@ -323,17 +332,23 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
     long long rcur = 0;
     const long long nruns = W.nruns;
     while (rcur < nruns || rcur == 0) {
-      // ---- collect (run, sign) entries overlapping [bin0, binEnd), ascending
+      // ---- collect (run, sign) entries overlapping [bin0, binEnd), ascending; each
+      // thread tests kRpt consecutive runs per pass (one block-wide scan per
+      // kRpt * kThreads runs), so the list order is the run order as before
       int cnt = 0;
-      while (rcur < nruns && cnt + 2 * kThreads <= kListCap) {
-        long long r = rcur + tid;
-        int fp = 0, fn = 0;
-        if (r < nruns) {
-          const RunBins B = P.rb[W.run_base + r];
-          fp = (B.b0p < binEnd && B.b1p > bin0) ? 1 : 0;
-          fn = (B.b0n < binEnd && B.b1n > bin0) ? 1 : 0;
+      while (rcur < nruns && cnt + 2 * kRpt * kThreads <= kListCap) {
+        const long long rb = rcur + (long long)tid * kRpt;
+        unsigned flags = 0u;   // bit 2k: run rb + k covers the tile for +f, bit 2k + 1: for -f
+#pragma unroll
+        for (int k = 0; k < kRpt; k++) {
+          if (rb + k < nruns) {
+            const RunBins B = P.rb[W.run_base + rb + k];
+            if (B.b0p < binEnd && B.b1p > bin0) flags |= 1u << (2 * k);
+            if (B.b0n < binEnd && B.b1n > bin0) flags |= 2u << (2 * k);
+          }
         }
-        int c = fp + fn, incl = c;
+        const int c = __popc(flags);
+        int incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           int v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -349,10 +364,13 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
           total += v;
         }
         int pos = cnt + before + incl - c;
-        if (fp) S.list[pos++] = (int)(r << 1);
-        if (fn) S.list[pos] = (int)((r << 1) | 1);
+#pragma unroll
+        for (int k = 0; k < kRpt; k++) {
+          if (flags & (1u << (2 * k))) S.list[pos++] = (int)((rb + k) << 1);
+          if (flags & (2u << (2 * k))) S.list[pos++] = (int)(((rb + k) << 1) | 1);
+        }
         cnt += total;
-        rcur += kThreads;
+        rcur += (long long)kRpt * kThreads;
         __syncthreads();
       }
       if (rcur == 0) rcur = 1;   // no runs at all: leave the loop after this pass

@@ -11,7 +11,8 @@ constexpr double kTwoPiOver2p64 = 3.4061215800865545e-19;   // 2 pi / 2^64 (exac
 constexpr double kMagic = 6755399441055744.0;               // 1.5 * 2^52
 
 // root of b u + c u^2 + d u^3 = delta on [ulo, uhi] (monotone, direction dir):
-// FP32 safeguarded Newton from a regula-falsi start; returns u and dF/du (FP32)
+// FP32 safeguarded Newton from a regula-falsi start, at most NIT steps, stopping
+// once a step is below 4e-7; returns u and dF/du (FP32)
 template <int NIT>
 __device__ __forceinline__ float root_f32(float bf, float cf, float df, float dl, float lo, float hi, int dir,
                                           float& Dout) {
@@ -28,7 +29,9 @@ __device__ __forceinline__ float root_f32(float bf, float cf, float df, float dl
     if ((fu > 0.f) == (dir > 0)) hi = u; else lo = u;
     float un = u - __fdividef(fu, D);
     if (!(un >= lo && un <= hi)) un = 0.5f * (lo + hi);
+    const bool done = fabsf(un - u) <= 4e-7f;   // the next step would be below FP32 resolution
     u = un;
+    if (done) break;
   }
   D = (3.f * df * u + 2.f * cf) * u + bf;
   Dout = D;
@@ -143,12 +146,15 @@ __device__ __forceinline__ void cis_q64(unsigned long long Th, const double2* ta
   ei = fma(T.y, cx, T.x * sx);
 }
 
-// a8: 1/sqrt|D| from an FP32 seed and one FP64 Newton step
+// a8: 1/sqrt|D| from an FP32 seed y0 and one FP64 Newton step,
+// y = y0 + (y0/2)(1 - |D| y0^2); y0/2 is formed exactly in FP32, so the step
+// takes three FP64 instructions
 __device__ __forceinline__ double rsqrt_abs(double Dd) {
   const double Dabs = fabs(Dd);
-  const double y0 = f2d_bits(rsqrtf(d2f_bits(Dabs)));
-  const double ee = (Dabs * y0) * y0;
-  return fma(y0, fma(ee, -0.5, 0.5), y0);
+  const float y0f = rsqrtf(d2f_bits(Dabs));
+  const double y0 = f2d_bits(y0f), y0h = f2d_bits(0.5f * y0f);
+  const double e = fma(-Dabs * y0, y0, 1.0);
+  return fma(y0h, e, y0);
 }
 
 }  // namespace emrifd
