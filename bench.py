@@ -30,8 +30,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = ("paper-shaped FP64 single waveform: T=2 yr, K=200 knots, 2000 modes (l=2..10, m=1..l, "
             "|n|<=30, top mean power of 3294), 3,155,760 bins f=i/T, conjugate partners implied")
-FP64_OPS_PER_MODE_BIN = 42       # FP64-pipe instructions per mode-bin in the FP64 output kernel
-FP64_FLOPS_PER_MODE_BIN = 68     # of which 26 are FMA (2 flops) and 16 single-flop
+FP64_OPS_PER_MODE_BIN = 40      # 27 DFMA + 13 DMUL/DADD per mode-bin in k_spa<*, 0, 0> (counted from the source)
+FP64_FLOPS_PER_MODE_BIN = 67    # 27 x 2 + 13
 FP64_PER_CLK_PER_SM = 2          # GB300 FP64 issue rate (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
 
 
