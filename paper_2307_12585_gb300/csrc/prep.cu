@@ -73,47 +73,54 @@ __device__ __forceinline__ double ipow(double x, int n) {
   return r;
 }
 
-__device__ double swsh_theta(int l, int m, double ch, double sh) {
+// one warp: lane k takes the terms k, k + 32 of the sum; the partial sums are
+// combined by a fixed xor tree (deterministic)
+__device__ double swsh_theta_warp(int l, int m, double ch, double sh, int lane) {
   const int a = m, b = 2;
   // sqrt((l+a)!(l-a)!(l+b)!(l-b)!) = 1/sqrt(product of inverse factorials)
-  double root = rsqrt(c_invfact[l + a] * c_invfact[l - a] * c_invfact[l + b] * c_invfact[l - b]);
+  const double root = rsqrt(c_invfact[l + a] * c_invfact[l - a] * c_invfact[l + b] * c_invfact[l - b]);
   double sum = 0.0;
-  for (int k = 0; k <= 2 * l; k++) {
-    int f0 = l + b - k, f1 = k, f2 = a - b + k, f3 = l - a - k;
+  for (int k = lane; k <= 2 * l; k += 32) {
+    const int f0 = l + b - k, f1 = k, f2 = a - b + k, f3 = l - a - k;
     if (f0 < 0 || f2 < 0 || f3 < 0) continue;
     double term = root * (c_invfact[f0] * c_invfact[f1]) * (c_invfact[f2] * c_invfact[f3]);
     term *= ipow(ch, 2 * l + b - a - 2 * k) * ipow(sh, a - b + 2 * k);
     sum += ((a - b + k) & 1) ? -term : term;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   // (-1)^s = +1 for s = -2
   return sqrt((2.0 * l + 1.0) / (2.0 * kTwoPi)) * sum;
 }
 
+// one warp per mode (the Wigner-d sums are short dependent FP64 chains: spread
+// over lanes they overlap instead of running back to back in one thread)
 __global__ void k_modes(int n_wf, const WfInfo* wf, DevInputs in, int conj, ModeInfo* modes,
                         long long nm_total, int* status) {
-  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long j = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (j >= nm_total) return;
   int lo = 0, hi = n_wf - 1;     // waveform holding mode j: last w with mo <= j
   while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (wf[mid].mo <= j) lo = mid; else hi = mid - 1; }
   const WfInfo W = wf[lo];
-  int l = in.l[j], m = in.m[j], n = in.n[j];
+  const int l = in.l[j], m = in.m[j], n = in.n[j];
   ModeInfo M;
   M.wf = lo; M.l = l; M.m = m; M.n = n;
   M.seg_base = W.seg_base + (j - W.mo) * (W.K - 1);
   M.key_base = W.amp_base + (j - W.mo) * W.K;
   M.alpha = 0.0; M.beta = 0.0;
-  bool ok = (l >= 2 && l <= 20 && m >= -l && m <= l && (!conj || m >= 0) && n > -1000000 && n < 1000000);
-  double th = in.theta[lo];
-  if (!finite(th) || !finite(in.phi[lo]) || !finite(in.prefactor[lo])) atomicOr(status, ST_NONFINITE);
+  const bool ok = (l >= 2 && l <= 20 && m >= -l && m <= l && (!conj || m >= 0) && n > -1000000 && n < 1000000);
+  const double th = in.theta[lo];
+  if (lane == 0 && (!finite(th) || !finite(in.phi[lo]) || !finite(in.prefactor[lo]))) atomicOr(status, ST_NONFINITE);
   if (!ok) {
-    atomicOr(status, ST_MODE);
+    if (lane == 0) atomicOr(status, ST_MODE);
   } else {
     // c+ = alpha e^{i m phi}, cx = i beta e^{i m phi} (the e^{i m phi} goes into the phase)
     double sh, ch;
     sincos(0.5 * th, &sh, &ch);
-    double S = swsh_theta(l, m, ch, sh);
+    const double S = swsh_theta_warp(l, m, ch, sh, lane);
     if (conj) {
-      double Sp = swsh_theta(l, -m, ch, sh) * ((l & 1) ? -1.0 : 1.0);
+      const double Sp = swsh_theta_warp(l, -m, ch, sh, lane) * ((l & 1) ? -1.0 : 1.0);
       M.alpha = 0.5 * (S + Sp);
       M.beta = 0.5 * (S - Sp);
     } else {
@@ -121,11 +128,11 @@ __global__ void k_modes(int n_wf, const WfInfo* wf, DevInputs in, int conj, Mode
       M.beta = 0.5 * S;
     }
   }
-  {
+  if (lane == 0) {
     const ff a = ff_from_double(M.alpha), b = ff_from_double(M.beta);
     M.af[0] = a.hi; M.af[1] = a.lo; M.bf[0] = b.hi; M.bf[1] = b.lo;
+    modes[j] = M;
   }
-  modes[j] = M;
 }
 
 // --------------------------------------------------------- not-a-knot splines
@@ -282,10 +289,12 @@ __device__ void spline_solve_warp(int K, const double* y, long long ys, double* 
   const int n = K - 2;
   const int E = (n + 31) / 32;
   const int i0 = 1 + lane * E, i1 = min(i0 + E, n + 1);
-  // forward
+  // forward (the right-hand sides are kept in M for the replay below)
   Aff F = {1.0, 0.0};
   for (int i = i0; i < i1; i++) {
-    const Aff f = {-fac[i].w, rhs_q(y, ys, ih, fac, i)};
+    const double q = rhs_q(y, ys, ih, fac, i);
+    M[i * ms] = q;
+    const Aff f = {-fac[i].w, q};
     F = aff_after(f, F);
   }
   Aff S = F;
@@ -298,7 +307,7 @@ __device__ void spline_solve_warp(int K, const double* y, long long ys, double* 
   double x = __shfl_up_sync(0xffffffffu, S.q, 1);   // exclusive prefix applied to rp_0 = 0
   if (lane == 0) x = 0.0;
   for (int i = i0; i < i1; i++) {
-    x = fma(-fac[i].w, x, rhs_q(y, ys, ih, fac, i));
+    x = fma(-fac[i].w, x, M[i * ms]);
     M[i * ms] = x;
   }
   __syncwarp();
@@ -804,8 +813,8 @@ void launch_prep_td(const CallShape& cs, const DevInputs& in, const DevScratch& 
   dim3 gk(8, cs.n_wf);
   k_validate_knots<<<gk, 256, 0, st>>>(s.wf, in, s.status);
   k_validate_amp<<<256, 256, 0, st>>>(2 * cs.amp_total, in.amp, s.status);
-  k_modes<<<(unsigned)((cs.nm_total + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes, cs.nm_total,
-                                                                  s.status);
+  k_modes<<<(unsigned)((cs.nm_total * 32 + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes,
+                                                                       cs.nm_total, s.status);
   k_spline_factor<<<(cs.n_wf * 32 + 127) / 128, 128, 0, st>>>(cs.n_wf, s.wf, in.t, s.spl_fac, s.spl_ih);
   long long nser = 4LL * cs.n_wf + 2 * cs.nm_total;
   k_spline_solve<<<(unsigned)((nser * 32 + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, s.modes, cs.nm_total, in, s.spl_fac,
@@ -817,11 +826,14 @@ void launch_prep_td(const CallShape& cs, const DevInputs& in, const DevScratch& 
 void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st) {
   dim3 gk(8, cs.n_wf);
   k_validate_knots<<<gk, 256, 0, st>>>(s.wf, in, s.status);
-  dim3 gf(256, cs.n_wf);
+  // about one bin per thread per waveform, at most 1216 CTAs (8 per SM of a 152-SM GB300)
+  long long gx = (cs.nf_total / (cs.n_wf > 0 ? cs.n_wf : 1) + 255) / 256;
+  gx = gx < 1 ? 1 : (gx > 1216 ? 1216 : gx);
+  dim3 gf((unsigned)gx, cs.n_wf);
   k_validate_freqs<<<gf, 256, 0, st>>>(s.wf, in, s.status);
   k_validate_amp<<<256, 256, 0, st>>>(2 * cs.amp_total, in.amp, s.status);
-  k_modes<<<(unsigned)((cs.nm_total + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes, cs.nm_total,
-                                                                  s.status);
+  k_modes<<<(unsigned)((cs.nm_total * 32 + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes,
+                                                                       cs.nm_total, s.status);
   k_spline_factor<<<(cs.n_wf * 32 + 127) / 128, 128, 0, st>>>(cs.n_wf, s.wf, in.t, s.spl_fac, s.spl_ih);
   long long nser = 4LL * cs.n_wf + 2 * cs.nm_total;
   k_spline_solve<<<(unsigned)((nser * 32 + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, s.modes, cs.nm_total, in, s.spl_fac,
