@@ -213,10 +213,12 @@ def job_rate(units_per_rank, world, ms):
     return world * units_per_rank / (ms * 1e-3)
 
 
+# tile sizes of the other forms on this workload (the fastest of 32/64/128 bins when measured)
+FORM_TILE = {"fp64x": 64, "mixed": 128}
 DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
 # DRAM bytes (read + write) of one k_spa<4,0,0> launch (FP64, standard SPA, 128-bin tiles) on
 # this workload, from one ncu capture of the kernel as it stands
-TRAFFIC_FP64_SPA = 98.968832e6 + 45.283840e6
+TRAFFIC_FP64_SPA = 99.315456e6 + 45.410304e6
 
 
 def base_line(args, world, metric, value, unit, ms, workload, extra=None):
@@ -362,7 +364,7 @@ def run_paper(args, rank, world, local):
         # another form on the same waveforms and bins: its rate, its speed-up over this
         # FP64 run and its relative L2 difference from this run's FP64 output
         oplan = api.Plan(prec, conj_partners=True, max_waveforms=1, max_knots=200, max_modes_total=2000,
-                         max_bins_total=nf, tile_bins=64 if prec in ("fp64x", "mixed") else args.tile_bins, spa=spa)
+                         max_bins_total=nf, tile_bins=FORM_TILE.get(prec, args.tile_bins), spa=spa)
         oout = (torch.empty(nf, dtype=oplan.out_dtype, device="cuda"), torch.empty(nf, dtype=oplan.out_dtype, device="cuda"))
         for i in range(args.warmup):
             oplan.sum_modes(dev[i % nw], out=oout, check=False)
@@ -382,7 +384,7 @@ def run_paper(args, rank, world, local):
                 "prep_ms": ost["prep_ns"] * 1e-6 / max(1, ost["timed_calls"]),
                 "mode_bin_evals_per_s": world * mb / (oms * 1e-3),
                 "speedup_vs_fp64": ms / oms, "rel_l2_vs_fp64": float(torch.sqrt(num / den)),
-                "tile_bins": 64 if prec in ("fp64x", "mixed") else args.tile_bins}
+                "tile_bins": FORM_TILE.get(prec, args.tile_bins)}
 
     mixed = fp64x = ext = None
     headline = args.precision == "fp64" and args.spa == "standard" and args.window is None

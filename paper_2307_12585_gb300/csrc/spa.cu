@@ -384,6 +384,18 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
         const RunBins B = P.rb[r];
         const int b0 = neg ? B.b0n : B.b0p, b1 = neg ? B.b1n : B.b1p;
         const ModeInfo M = P.modes[R.mode];
+        // a5 for the whole warp (FP32-path kernels, which are issue-bound; in the FP64
+        // kernel the per-bin integer search overlaps the FP64 pipe for free): when the
+        // first and last of the tile's bins this entry covers lie in one segment,
+        // every bin between does too
+        int s_uni = -1;
+        if constexpr (PREC != 0) {
+          const long long lo_b = max((long long)b0, bin0), hi_b = min((long long)b1, binEnd) - 1;
+          const double flo = P.freqs[lo_b], fhi = P.freqs[hi_b];
+          const int s_lo = run_segment_warp(R, P.keyF, M.key_base, ordkey(neg ? -flo : flo), lane);
+          const int s_hi = run_segment_warp(R, P.keyF, M.key_base, ordkey(neg ? -fhi : fhi), lane);
+          s_uni = s_lo == s_hi ? s_lo : -1;
+        }
         if constexpr (PREC == 0) {
           const double sa = M.alpha, sb = neg ? -M.beta : M.beta;   // h+ += alpha Z~, hx += i sb Z~
 #pragma unroll
@@ -464,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
 #pragma unroll
             for (int qq = 1; qq < BPL; qq++)
               if (qq == q) { fqq = fq[qq]; kq_ = neg ? kn[qq] : kp[qq]; fx = fqf[qq]; }
-            const int s = run_segment(R, P.keyF, M.key_base, kq_);
+            const int s = s_uni >= 0 ? s_uni : run_segment(R, P.keyF, M.key_base, kq_);
             const SegCore C = P.core[M.seg_base + s];
             float v[8];
             bool ok;
