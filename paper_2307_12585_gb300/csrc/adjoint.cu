@@ -326,65 +326,107 @@ __global__ void k_fund_knot(int n_wf, const WfInfo* wf, const double* t, const d
   }
 }
 
-// Transpose of the not-a-knot map y -> M (the forward solve of prep.cu) applied
-// to gM, added to gY: out = gY + (dM/dy)^T gM.  One thread per series.
-__device__ __forceinline__ void tri_row_t(const double* t, int K, int i, double& a, double& b, double& c, double& scale) {
-  double h0 = t[i] - t[i - 1], h1 = t[i + 1] - t[i];
-  scale = 1.0;
-  if (i == 1) { a = 0.0; b = h0 + 2.0 * h1; c = h1 - h0; scale = h1 / (h0 + h1); }
-  else if (i == K - 2) { a = h0 - h1; b = 2.0 * h0 + h1; c = 0.0; scale = h0 / (h0 + h1); }
-  else { a = h0; b = 2.0 * (h0 + h1); c = h1; }
+// Transpose of the not-a-knot map y -> M (the forward solve of the preparation)
+// applied to gM, added to gY: out = gY + (dM/dy)^T gM.  One warp per series; the
+// two triangular sweeps of the transposed factorisation are warp scans of affine
+// maps, as in the forward solve.
+struct AffT { double p, q; };
+__device__ __forceinline__ AffT afft_after(const AffT& g, const AffT& f) {
+  AffT r; r.p = g.p * f.p; r.q = fma(g.p, f.q, g.q); return r;
+}
+// exclusive prefix (over lanes) of the composition of per-lane maps, applied to 0
+__device__ __forceinline__ double afft_scan_exclusive(AffT S, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    AffT X;
+    X.p = __shfl_up_sync(0xffffffffu, S.p, o);
+    X.q = __shfl_up_sync(0xffffffffu, S.q, o);
+    if (lane >= o) S = afft_after(S, X);
+  }
+  const double x = __shfl_up_sync(0xffffffffu, S.q, 1);
+  return lane == 0 ? 0.0 : x;
 }
 
-__device__ void spline_adjoint(const double* t, int K, const double* gY, long long ys, const double* gM0, long long ms,
-                               const dbl4* fac, double* out, long long os, double* z) {
-  // z holds K doubles of scratch with stride os (written into out first)
-  for (int i = 0; i < K; i++) z[i * os] = gM0[i * ms];
-  {
-    double h0 = t[1] - t[0], h1 = t[2] - t[1];
-    z[1 * os] += z[0] * (h0 + h1) / h1;
-    z[2 * os] += -z[0] * h0 / h1;
-    double ha = t[K - 2] - t[K - 3], hb = t[K - 1] - t[K - 2];
-    z[(K - 2) * os] += z[(K - 1) * os] * (ha + hb) / ha;
-    z[(K - 3) * os] += -z[(K - 1) * os] * hb / ha;
+__device__ void spline_adjoint_warp(const double* t, const double* ih, int K, const double* gY, long long ys,
+                                    const double* gM0, long long ms, const dbl4* fac, double* out, long long os,
+                                    double* z, int lane) {
+  for (int i = lane; i < K; i += 32) z[i * os] = gM0[i * ms];
+  __syncwarp();
+  if (lane == 0) {
+    // adjoint of M_0 = (1 + h0/h1) M_1 - (h0/h1) M_2 and of its mirror at the far end
+    const double r01 = ih[1] / ih[0], z0 = z[0];
+    z[os] += z0 * (1.0 + r01);
+    z[2 * os] += -z0 * r01;
+    const double rba = ih[K - 3] / ih[K - 2], zl = z[(K - 1) * os];
+    z[(K - 2) * os] += zl * (1.0 + rba);
+    z[(K - 3) * os] += -zl * rba;
   }
-  // Tri = L U with L lower bidiagonal (diag m_i, sub a_i), U unit upper (super c'_i):
-  // Tri^T lam = g  <=>  U^T w = g (forward), L^T lam = w (backward)
-  for (int i = 2; i <= K - 2; i++) z[i * os] -= fac[i - 1].x * z[(i - 1) * os];
+  __syncwarp();
+  const int n = K - 2, E = (n + 31) / 32;
+  // Tri = L U (L lower bidiagonal: diag m_i, sub a_i; U unit upper: super c'_i);
+  // Tri^T lam = g  <=>  U^T w = g, then L^T lam = w.
+  // U^T w = g: w_i = g_i - c'_{i-1} w_{i-1}, i = 1 .. K-2 (c'_0 = 0)
   {
-    double a, b, c, s;
-    z[(K - 2) * os] *= fac[K - 2].y;
-    for (int i = K - 3; i >= 1; i--) {
-      tri_row_t(t, K, i + 1, a, b, c, s);
-      z[i * os] = (z[i * os] - a * z[(i + 1) * os]) * fac[i].y;
+    const int i0 = 1 + lane * E, i1 = min(i0 + E, n + 1);
+    AffT F = {1.0, 0.0};
+    for (int i = i0; i < i1; i++) F = afft_after(AffT{-fac[i - 1].x, z[i * os]}, F);
+    double x = afft_scan_exclusive(F, lane);
+    for (int i = i0; i < i1; i++) {
+      x = fma(-fac[i - 1].x, x, z[i * os]);
+      z[i * os] = x;
     }
   }
-  // lam -> y through rhs_i = s_i * 6 [(y_{i+1} - y_i)/h_i - (y_i - y_{i-1})/h_{i-1}]
-  for (int i = 0; i < K; i++) out[i * os] = gY[i * ys];
-  for (int i = 1; i <= K - 2; i++) {
-    double a, b, c, s;
-    tri_row_t(t, K, i, a, b, c, s);
-    const double gr = z[i * os] * s * 6.0;
-    const double h0 = t[i] - t[i - 1], h1 = t[i + 1] - t[i];
-    out[(i + 1) * os] += gr / h1;
-    out[i * os] -= gr * (1.0 / h1 + 1.0 / h0);
-    out[(i - 1) * os] += gr / h0;
+  __syncwarp();
+  // L^T lam = w: lam_i = (w_i - a_{i+1} lam_{i+1}) / m_i, i = K-2 .. 1 (lam_{K-1} = 0)
+  {
+    const int j0 = n - lane * E, j1 = max(j0 - E, 0);
+    auto map = [&](int i) {
+      double a = 0.0;                                   // a_{i+1}: sub-diagonal of row i + 1
+      if (i + 1 == K - 2) a = (t[K - 2] - t[K - 3]) - (t[K - 1] - t[K - 2]);
+      else if (i + 1 < K - 2) a = t[i + 1] - t[i];
+      const double y = fac[i].y;                        // 1/m_i
+      return AffT{-a * y, z[i * os] * y};
+    };
+    AffT B = {1.0, 0.0};
+    for (int i = j0; i > j1; i--) B = afft_after(map(i), B);
+    double x = afft_scan_exclusive(B, lane);
+    __syncwarp();
+    for (int i = j0; i > j1; i--) {
+      const AffT g = map(i);
+      x = fma(g.p, x, g.q);
+      z[i * os] = x;
+    }
+  }
+  __syncwarp();
+  // lam -> y through rhs_i = s_i 6 [(y_{i+1} - y_i)/h_i - (y_i - y_{i-1})/h_{i-1}], rows i = 1 .. K-2
+  auto srow = [&](int i) {       // s_i: 1 except the not-a-knot rows
+    if (i == 1) return (t[2] - t[1]) / (t[2] - t[0]);
+    if (i == K - 2) return (t[K - 2] - t[K - 3]) / (t[K - 1] - t[K - 3]);
+    return 1.0;
+  };
+  for (int j = lane; j < K; j += 32) {
+    double v = gY[j * ys];
+    if (j - 1 >= 1 && j - 1 <= K - 2) v += 6.0 * z[(j - 1) * os] * srow(j - 1) * ih[j - 1];
+    if (j >= 1 && j <= K - 2) v -= 6.0 * z[j * os] * srow(j) * (ih[j] + ih[j - 1]);
+    if (j + 1 <= K - 2) v += 6.0 * z[(j + 1) * os] * srow(j + 1) * ih[j];
+    out[j * os] = v;
   }
 }
 
 __global__ void k_spline_adj(int n_wf, const WfInfo* wf, const ModeInfo* modes, long long nm_total, const double* t,
-                             const dbl4* fac, const double* fgY, const double* fgM,
+                             const dbl4* fac, const double* ihall, const double* fgY, const double* fgM,
                              long long K_total, const double* agY, const double* agM, double* zf, double* za,
                              double* g_pp, double* g_pr, double* g_op, double* g_or, double* g_amp) {
-  long long sid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long sid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   long long nfund = 4LL * n_wf;
   if (sid < nfund) {
     int w = (int)(sid >> 2), q = (int)(sid & 3);
     const WfInfo W = wf[w];
     double* outp = q == 0 ? g_pp : q == 1 ? g_pr : q == 2 ? g_op : g_or;
     if (!outp) return;
-    spline_adjoint(t + W.ko, (int)W.K, fgY + q * K_total + W.ko, 1, fgM + q * K_total + W.ko, 1, fac + W.ko,
-                   outp + W.ko, 1, zf + q * K_total + W.ko);
+    spline_adjoint_warp(t + W.ko, ihall + W.ko, (int)W.K, fgY + q * K_total + W.ko, 1, fgM + q * K_total + W.ko, 1,
+                        fac + W.ko, outp + W.ko, 1, zf + q * K_total + W.ko, lane);
     return;
   }
   sid -= nfund;
@@ -393,8 +435,8 @@ __global__ void k_spline_adj(int n_wf, const WfInfo* wf, const ModeInfo* modes, 
   int part = (int)(sid & 1);
   const ModeInfo M = modes[j];
   const WfInfo W = wf[M.wf];
-  spline_adjoint(t + W.ko, (int)W.K, agY + 2 * M.key_base + part, 2, agM + 2 * M.key_base + part, 2, fac + W.ko,
-                 g_amp + 2 * M.key_base + part, 2, za + 2 * M.key_base + part);
+  spline_adjoint_warp(t + W.ko, ihall + W.ko, (int)W.K, agY + 2 * M.key_base + part, 2, agM + 2 * M.key_base + part, 2,
+                      fac + W.ko, g_amp + 2 * M.key_base + part, 2, za + 2 * M.key_base + part, lane);
 }
 
 }  // namespace
@@ -431,8 +473,8 @@ void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& 
   dim3 gk((cs.max_K + 127) / 128, cs.n_wf);
   k_fund_knot<<<gk, 128, 0, st>>>(cs.n_wf, s.wf, in.t, s.fseg, cs.K_total, s.fgY, s.fgM);
   long long nser = 4LL * cs.n_wf + 2 * cs.nm_total;
-  k_spline_adj<<<(unsigned)((nser + 127) / 128), 128, 0, st>>>(
-      cs.n_wf, s.wf, s.modes, cs.nm_total, in.t, s.spl_fac, s.fgY, s.fgM, cs.K_total, s.agY, s.agM, s.zf,
+  k_spline_adj<<<(unsigned)((nser * 32 + 255) / 256), 256, 0, st>>>(
+      cs.n_wf, s.wf, s.modes, cs.nm_total, in.t, s.spl_fac, s.spl_ih, s.fgY, s.fgM, cs.K_total, s.agY, s.agM, s.zf,
       s.za, li.g_phi_phi, li.g_phi_r, li.g_omega_phi, li.g_omega_r, li.g_amp);
 }
 
