@@ -25,7 +25,6 @@
 namespace emrifd {
 namespace {
 
-constexpr int kLChunks = 64;
 constexpr double kTwoPi = 6.283185307179586;
 constexpr double kInv2Pi = 0.15915494309189535;
 
@@ -45,7 +44,7 @@ __global__ void k_residual(const WfInfo* wf, const double2* hp, const double2* h
     if (!(S > 0.0) || !isfinite(S)) bad = ST_NONFINITE;
     const double2 a = hp[b], c = hc[b], x = dp[b], y = dc[b];
     const double rpr = x.x - a.x, rpi = x.y - a.y, rcr = y.x - c.x, rci = y.y - c.y;
-    const double w = 4.0 * df / S;
+    const double w = 4.0 * df * rcp_d(S);
     acc += (rpr * rpr + rpi * rpi + rcr * rcr + rci * rci) * (-0.5 * w);
     G[b] = mk_dbl4(w * rpr, w * rpi, w * rcr, w * rci);
   }
@@ -59,12 +58,19 @@ __global__ void k_residual(const WfInfo* wf, const double2* hp, const double2* h
   if (threadIdx.x == 0) Lpart[blockIdx.y * kLChunks + blockIdx.x] = red[0];
 }
 
+// one CTA of 256 threads per waveform: chunk partials summed in a fixed tree order
 __global__ void k_loglike_final(int n_wf, const double* Lpart, double* L) {
-  int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= n_wf) return;
+  __shared__ double red[256];
+  const int w = blockIdx.x, tid = threadIdx.x;
   double s = 0.0;
-  for (int c = 0; c < kLChunks; c++) s += Lpart[w * kLChunks + c];
-  L[w] = s;
+  for (int c = tid; c < kLChunks; c += 256) s += Lpart[(long long)w * kLChunks + c];
+  red[tid] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (tid < o) red[tid] += red[tid + o];
+    __syncthreads();
+  }
+  if (tid == 0) L[w] = red[0];
 }
 
 // ---------------------------------------------------------- adjoint items
@@ -448,7 +454,7 @@ void launch_loglike(const CallShape& cs, const LikeInputs& li, const DevScratch&
                                 reinterpret_cast<const double2*>(li.data_plus),
                                 reinterpret_cast<const double2*>(li.data_cross), li.psd, li.df,
                                 reinterpret_cast<dbl4*>(s.Gbuf), s.Lpart, s.status);
-  k_loglike_final<<<(cs.n_wf + 63) / 64, 64, 0, st>>>(cs.n_wf, s.Lpart, li.loglike);
+  k_loglike_final<<<cs.n_wf, 256, 0, st>>>(cs.n_wf, s.Lpart, li.loglike);
 }
 
 void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& li, const DevScratch& s, int num_sms,

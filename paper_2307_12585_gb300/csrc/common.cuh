@@ -126,6 +126,18 @@ __device__ __forceinline__ double f2d_bits(float x) {
   return __longlong_as_double((long long)(s | (ed << 52) | ((unsigned long long)(u & 0x7FFFFF) << 29)));
 }
 
+// reciprocal of a normal double from an FP32 seed and two FP64 Newton steps
+__device__ __forceinline__ double rcp_d(double x) {
+  const float xf = d2f_bits(x);
+  const float yf = __fdividef(1.f, xf);
+  if (!(fabsf(yf) > 0.f && fabsf(yf) < 3.0e38f)) return 1.0 / x;
+  double y = f2d_bits(yf);
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 // frac(x) in Q0.64 turns (x in turns), by the bit fields of x
 __device__ __forceinline__ unsigned long long q64_of(double x) {
   unsigned long long u = (unsigned long long)__double_as_longlong(x);
@@ -219,7 +231,7 @@ struct DevScratch {
   // likelihood / adjoint scratch (plans created with likelihood = 1)
   double* hbuf;                   // [2][sum N_f] complex128: h+ then hx
   double* Gbuf;                   // [sum N_f][4] 4 df (d - h)/S, both channels
-  double* Lpart;                  // [max_waveforms][64] partial sums of L
+  double* Lpart;                  // [max_waveforms][kLChunks] partial sums of L
   int* item_off;                  // [run_cap + 1] adjoint items (run, segment), scanned
   double* slots;                  // [sum N_m (K-1)][3 sub-pieces][16] per-segment gradients
   double *agY, *agM;              // [sum N_m K][2] amplitude knot-value / second-derivative gradients
@@ -248,6 +260,7 @@ struct CallShape {
   int window;       // 1: Hann window applied to the outputs (Sec. 2.3)
 };
 
+constexpr int kLChunks = 512;      // per-waveform chunks of the likelihood's partial sums
 constexpr int kPrepKernels = 12;   // kernels launched by launch_prep (memsets excluded)
 constexpr int kAdjointKernels = 8; // kernels launched by launch_adjoint
 

@@ -184,7 +184,7 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
   if (d->likelihood) {
     AL(s.hbuf, 4 * p->cap_nf);
     AL(s.Gbuf, 4 * p->cap_nf);
-    AL(s.Lpart, 64 * (long long)d->max_waveforms);
+    AL(s.Lpart, (long long)kLChunks * d->max_waveforms);
     AL(s.item_off, s.run_cap + 1);
     AL(s.slots, 48 * p->cap_seg);
     AL(s.agY, 2 * p->cap_amp);

@@ -157,17 +157,6 @@ __device__ __forceinline__ void tri_row(const double* t, int K, int i, double& a
   } else { a = h0; b = 2.0 * (h0 + h1); c = h1; }
 }
 
-// reciprocal of a normal double from an FP32 seed and two FP64 Newton steps
-__device__ __forceinline__ double rcp_d(double x) {
-  const float xf = d2f_bits(x);
-  const float yf = __fdividef(1.f, xf);
-  if (!(fabsf(yf) > 0.f && fabsf(yf) < 3.0e38f)) return 1.0 / x;
-  double y = f2d_bits(yf);
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
-}
 
 struct dd { double hi, lo; };
 __device__ __forceinline__ dd dd_two_prod(double a, double b) { dd r; r.hi = a * b; r.lo = fma(a, b, -r.hi); return r; }
