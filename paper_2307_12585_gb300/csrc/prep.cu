@@ -158,14 +158,11 @@ __device__ __forceinline__ void tri_row(const double* t, int K, int i, double& a
 }
 
 
+// double-double product (Dekker/Knuth error-free transforms), for the knot
+// phases Phi/(2 pi) in Q0.64 turns
 struct dd { double hi, lo; };
 __device__ __forceinline__ dd dd_two_prod(double a, double b) { dd r; r.hi = a * b; r.lo = fma(a, b, -r.hi); return r; }
 __device__ __forceinline__ dd dd_fast(double s, double e) { dd r; r.hi = s + e; r.lo = e - (r.hi - s); return r; }
-__device__ __forceinline__ dd dd_add(dd a, dd b) {
-  double s = a.hi + b.hi, v = s - a.hi;
-  double e = (a.hi - (s - v)) + (b.hi - v);
-  return dd_fast(s, e + a.lo + b.lo);
-}
 __device__ __forceinline__ dd dd_mul(dd a, dd b) {
   dd p = dd_two_prod(a.hi, b.hi);
   return dd_fast(p.hi, p.lo + (a.hi * b.lo + a.lo * b.hi));
