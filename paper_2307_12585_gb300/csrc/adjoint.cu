@@ -185,7 +185,8 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjParams P) {
         const double QZr = QEr * Ar - QEi * Ai, QZi = QEr * Ai + QEi * Ar;
         const double Dp = fma(2.0 * C.d3, u, C.c2);           // d^2F/du^2
         const double dpsi = kTwoPi * (delta * C.h - C.Q1 - u * (2.0 * C.P2 + 3.0 * C.P3 * u));  // 2 pi g h - Phi_V'(u)
-        const double invD = 1.0 / Dd;
+        const double w2 = wgt * wgt;                          // 1/|dF/du| from the weight: no FP64 division
+        const double invD = Dbits >= 0 ? w2 : -w2;
         const double T = (QEr * dAr - QEi * dAi) - 0.5 * QZr * Dp * invD - QZi * dpsi;
         const double up[4] = {1.0, u, u * u, u * u * u};
         const double tD = -T * invD, hD = -0.5 * QZr * invD;
