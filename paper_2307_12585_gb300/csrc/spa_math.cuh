@@ -8,7 +8,6 @@
 namespace emrifd {
 
 constexpr double kTwoPiOver2p64 = 3.4061215800865545e-19;   // 2 pi / 2^64 (exact scaling of 2 pi)
-constexpr double kMagic = 6755399441055744.0;               // 1.5 * 2^52
 
 // root of b u + c u^2 + d u^3 = delta on [ulo, uhi] (monotone, direction dir):
 // FP32 safeguarded Newton from a regula-falsi start, at most NIT steps, stopping
@@ -156,11 +155,21 @@ __device__ __forceinline__ unsigned long long phase_q64(const SegCore& C, double
   return Th;
 }
 
+// exact double of an integer with |r| < 2^52, from its bits (integer instructions only)
+__device__ __forceinline__ double small_ll_to_double(long long r) {
+  if (r == 0) return 0.0;
+  const unsigned long long a = r < 0 ? 0ull - (unsigned long long)r : (unsigned long long)r;
+  const int e = 63 - __clzll(a);                                   // 2^e <= a < 2^(e+1), e <= 51
+  const unsigned long long bits = ((unsigned long long)(e + 1023) << 52) | ((a << (52 - e)) & 0xFFFFFFFFFFFFFull) |
+                                  ((unsigned long long)r & 0x8000000000000000ull);
+  return __longlong_as_double((long long)bits);
+}
+
 // e^{2 pi i Th/2^64}: 4096-entry table times 1 + i x - x^2/2 - i x^3/6, |x| <= pi/4096
 __device__ __forceinline__ void cis_q64(unsigned long long Th, const double2* tab, double& er, double& ei) {
   const unsigned long long kq = (Th + (1ull << (63 - kTabBits))) >> (64 - kTabBits);
-  const long long rr = (long long)(Th - (kq << (64 - kTabBits)));
-  const double x = (__longlong_as_double(0x4338000000000000LL + rr) - kMagic) * kTwoPiOver2p64;
+  const long long rr = (long long)(Th - (kq << (64 - kTabBits)));   // |rr| <= 2^51
+  const double x = small_ll_to_double(rr) * kTwoPiOver2p64;
   const double x2 = x * x;
   const double cx = fma(x2, -0.5, 1.0);
   const double sx = x * fma(x2, -1.0 / 6.0, 1.0);
