@@ -295,6 +295,14 @@ def paper_aux(args, w, fd_ms_per_wf):
                           "peak_GBs": peak, "frac": (gbs / peak) if peak else None,
                           "note": "read h+/hx (32 B) and f (8 B), write h+/hx (32 B) per bin; bound by GB300's "
                                   "FP64 rate (12 FP64 operations per bin), not HBM; peak = measured copy bandwidth"}
+    # the same waveform on a sparse grid of 1e4 log-spaced bins (the paper's downsampled FD, Sec. 3.3)
+    ws = synth.paper_config(1, grid="sparse")
+    plan = api.Plan("fp64", max_waveforms=1, max_knots=ws.K, max_modes_total=ws.n_modes, max_bins_total=ws.n_freqs)
+    b = plan.upload(synth.concat([ws]))
+    o = plan.sum_modes(b)
+    out["sparse_grid"] = {"bins": ws.n_freqs, "fp64_ms": timed(plan.stream, lambda: plan.sum_modes(b, out=o, check=False),
+                                                               reps)}
+    plan.close()
     # mode selection on the full pool
     pool = synth.paper_config(1, n_modes=3294, grid="sparse", n_sparse=16)
     plan = api.Plan("fp64", max_waveforms=1, max_knots=pool.K, max_modes_total=pool.n_modes, max_bins_total=16)

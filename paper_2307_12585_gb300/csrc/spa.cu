@@ -538,8 +538,8 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
       const long long bin = bin0 + i;
       if (bin >= binEnd) continue;
       if constexpr (PREC == 0) {
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int w2 = 0; w2 < kWarps; w2++)
+        double v[4] = {S.red[0][i][0], S.red[0][i][1], S.red[0][i][2], S.red[0][i][3]};
+        for (int w2 = 1; w2 < kWarps; w2++)
 #pragma unroll
           for (int c = 0; c < 4; c++) v[c] += S.red[w2][i][c];
         reinterpret_cast<double2*>(P.hp)[bin] = make_double2(v[0], v[1]);

@@ -11,9 +11,9 @@
 //     frac(Phi_r/2pi) as Q0.64 turns (knot value in Q0.64 from preparation plus
 //     the in-segment cubic in FP64), rounded to Q0.32;
 //   - per mode-sample: psi = m a + n b in wrapping 32-bit integers (error
-//     <= (|m| + |n|)/2 units of 2^-32 turn), e^{-i psi} from a 4096-entry FP32
-//     table and a second-order Taylor step (|x| <= pi/4096), the amplitude cubics
-//     in FP32, and FP32 sums over chunks of 32 modes carried in FP32 pairs.
+//     <= (|m| + |n|)/2 units of 2^-32 turn), e^{-i psi} from the hardware FP32
+//     sin/cos of psi in [-pi, pi) (about 4e-7 absolute), the amplitude cubics in
+//     FP32, and FP32 sums over chunks of 32 modes carried in FP32 pairs.
 // Persistent CTAs take tiles of kTdTile consecutive samples of one waveform
 // from an atomic queue; a tile spans at most a few spline segments and is
 // swept once per segment it touches, each sample accumulating only in its own.
@@ -42,7 +42,6 @@ struct TdParams {
   const double* t;
   const double* dt;
   const double* prefactor;
-  const double2* tab;
   float* hp;
   float* hc;
   unsigned long long* counters;
@@ -60,15 +59,9 @@ __device__ __forceinline__ int knot_segment(const double* t, int K, double x) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_td_sum(TdParams P) {
-  __shared__ float2 tab[kTabN];
   __shared__ long long s_tile;
   const int tid = threadIdx.x;
   if (*P.status != 0) return;
-  for (int i = tid; i < kTabN; i += kThreads) {
-    const double2 v = P.tab[i];
-    tab[i] = make_float2((float)v.x, (float)v.y);
-  }
-  __syncthreads();
   for (;;) {
     if (tid == 0) s_tile = (long long)atomicAdd(&P.counters[0], 1ull);
     __syncthreads();
@@ -133,13 +126,11 @@ __global__ void __launch_bounds__(kThreads) k_td_sum(TdParams P) {
 #pragma unroll
           for (int q = 0; q < kTdSpt; q++) {
             const unsigned th = (unsigned)mm * pa[q] + (unsigned)nn * pb[q];   // psi in 2^-32 turns
-            const unsigned kq = (th + (1u << 19)) >> 20;
-            const int r = (int)(th - (kq << 20));                               // |r| <= 2^19
-            const float x = (__int_as_float(0x4B400000 + r) - 12582912.f) * 1.4629180792671596e-09f;  // 2 pi / 2^32
-            const float2 T = tab[kq & (kTabN - 1)];
-            const float h2 = 0.5f * x * x;
-            const float cs = fmaf(-T.y, x, fmaf(-T.x, h2, T.x));   // cos(a + x)
-            const float sn = fmaf(T.x, x, fmaf(-T.y, h2, T.y));    // sin(a + x)
+            // psi in [-pi, pi) as FP32 radians; the hardware sin/cos approximations are
+            // accurate to about 4e-7 absolute there, ample for an FP32 comparator
+            const float x = (float)(int)th * 1.4629180792671596e-09f;           // 2 pi / 2^32
+            float sn, cs;
+            __sincosf(x, &sn, &cs);
             const float u = uf[q];
             const float are = fmaf(fmaf(fmaf(ar.w, u, ar.z), u, ar.y), u, ar.x);
             const float aim = fmaf(fmaf(fmaf(ai.w, u, ai.z), u, ai.y), u, ai.x);
@@ -208,7 +199,7 @@ void launch_td_sum(const CallShape& cs, const DevInputs& in, const DevScratch& s
                    const double* dt, float* hp, float* hc, int num_sms, cudaStream_t st) {
   TdParams p;
   p.wf = s.wf; p.n_wf = cs.n_wf; p.modes = s.modes; p.tdamp = tdamp; p.fund = s.fund; p.t = in.t; p.dt = dt;
-  p.prefactor = in.prefactor; p.tab = s.tab; p.hp = hp; p.hc = hc; p.counters = s.counters; p.status = s.status;
+  p.prefactor = in.prefactor; p.hp = hp; p.hc = hc; p.counters = s.counters; p.status = s.status;
   p.tiles_total = cs.tiles_total;
   cudaMemsetAsync(s.counters, 0, sizeof(unsigned long long), st);
   int per_sm = 0;
