@@ -218,7 +218,7 @@ FORM_TILE = {"fp64x": 64, "mixed": 128}
 DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
 # DRAM bytes (read + write) of one k_spa<4,0,0> launch (FP64, standard SPA, 128-bin tiles) on
 # this workload, from one ncu capture of the kernel as it stands
-TRAFFIC_FP64_SPA = 99.171584e6 + 45.075200e6
+TRAFFIC_FP64_SPA = 98.915328e6 + 45.252864e6
 
 
 def base_line(args, world, metric, value, unit, ms, workload, extra=None):
@@ -297,12 +297,17 @@ def paper_aux(args, w, fd_ms_per_wf):
                                   "FP64 rate (12 FP64 operations per bin), not HBM; peak = measured copy bandwidth"}
     # the same waveform on a sparse grid of 1e4 log-spaced bins (the paper's downsampled FD, Sec. 3.3)
     ws = synth.paper_config(1, grid="sparse")
-    plan = api.Plan("fp64", max_waveforms=1, max_knots=ws.K, max_modes_total=ws.n_modes, max_bins_total=ws.n_freqs)
-    b = plan.upload(synth.concat([ws]))
-    o = plan.sum_modes(b)
-    out["sparse_grid"] = {"bins": ws.n_freqs, "fp64_ms": timed(plan.stream, lambda: plan.sum_modes(b, out=o, check=False),
-                                                               reps)}
-    plan.close()
+    best = None
+    for tb in (32, 64, 128):      # few bins: the tile size sets how many SMs take part
+        plan = api.Plan("fp64", max_waveforms=1, max_knots=ws.K, max_modes_total=ws.n_modes,
+                        max_bins_total=ws.n_freqs, tile_bins=tb)
+        b = plan.upload(synth.concat([ws]))
+        o = plan.sum_modes(b)
+        t = timed(plan.stream, lambda: plan.sum_modes(b, out=o, check=False), reps)
+        plan.close()
+        if best is None or t < best[0]:
+            best = (t, tb)
+    out["sparse_grid"] = {"bins": ws.n_freqs, "fp64_ms": best[0], "tile_bins": best[1]}
     # mode selection on the full pool
     pool = synth.paper_config(1, n_modes=3294, grid="sparse", n_sparse=16)
     plan = api.Plan("fp64", max_waveforms=1, max_knots=pool.K, max_modes_total=pool.n_modes, max_bins_total=16)
