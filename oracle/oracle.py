@@ -208,19 +208,21 @@ def rel_l2(x, ref):
     return float(np.sqrt(np.sum(np.abs(x - ref) ** 2)) / (den if den > 0 else 1.0))
 
 
-def td_samples(w, dt, N=None, conj_partners=True):
+def td_samples(w, dt, N=None, conj_partners=True, idx=None):
     """Time-domain voice sum (Eq. 2) sampled at t_j = t_0 + j dt, j = 0..N-1
     (default N = floor((t_last - t_0)/dt)); samples after t_last are 0.  Uses
     scipy's not-a-knot splines of the same knots and the Wigner-d Y_lm below,
     an implementation independent of oracle.c:
         h(t) = prefactor sum_modes [A Y_lm e^{-i Phi} + (partners) (-1)^l conj(A) Y_{l,-m} e^{+i Phi}],
-    Phi = m Phi_phi + n Phi_r; h = h+ - i hx.  Returns (t_j, h+, hx) real arrays."""
+    Phi = m Phi_phi + n Phi_r; h = h+ - i hx.  Returns (t_j, h+, hx) real arrays.
+    idx: evaluate only the samples j in idx (a full-size check on a subset)."""
     from scipy.interpolate import CubicSpline
 
     t = w.t
     if N is None:
         N = int(np.floor((t[-1] - t[0]) / dt))
-    tj = t[0] + dt * np.arange(N)
+    j = np.arange(N) if idx is None else np.asarray(idx, np.int64)
+    tj = t[0] + dt * j
     inside = tj <= t[-1]
     tin = tj[inside]
     sp = lambda y: CubicSpline(t, y, bc_type="not-a-knot")(tin)

@@ -93,3 +93,26 @@ def test_nonuniform_grid_refused():
 def test_likelihood_plan_refuses_window():
     with pytest.raises(api.EmriFdError):
         api.Plan("fp64", max_modes_total=10, max_bins_total=100, likelihood=True, window="hann")
+
+
+def test_paper_size_sampled(oracle):
+    """The full 3,155,760-bin grid windowed on the GPU; the oracle evaluates the SPA sum
+    at 1500 sampled bins and their two neighbours and applies the three-term form."""
+    w = synth.paper_config(3)
+    got = _run([w], "fp64", "hann")
+    rng = np.random.default_rng(5)
+    occ = np.nonzero(np.abs(got[0]) > 0)[0]
+    sel = np.unique(np.concatenate([rng.choice(occ, 1000, replace=False),
+                                    rng.integers(1, w.n_freqs - 1, 500), [0, w.n_freqs - 1]]))
+    trip = np.unique(np.clip(np.concatenate([sel - 1, sel, sel + 1]), 0, w.n_freqs - 1))
+    rp, rc = oracle.sum_modes(w, freqs=w.freqs[trip])
+    pos = {b: i for i, b in enumerate(trip)}
+    def win(h):
+        out = []
+        for b in sel:
+            v = 0.5 * h[pos[b]]
+            v -= 0.25 * (h[pos[b - 1]] if b - 1 >= 0 else 0.0)
+            v -= 0.25 * (h[pos[b + 1]] if b + 1 < w.n_freqs else 0.0)
+            out.append(v)
+        return np.array(out)
+    assert rel_l2(got[0][sel], win(rp)) <= 1e-10 and rel_l2(got[1][sel], win(rc)) <= 1e-10
