@@ -218,7 +218,7 @@ FORM_TILE = {"fp64x": 64, "mixed": 128}
 DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
 # DRAM bytes (read + write) of one k_spa<4,0,0> launch (FP64, standard SPA, 128-bin tiles) on
 # this workload, from one ncu capture of the kernel as it stands
-TRAFFIC_FP64_SPA = 98.915328e6 + 45.252864e6
+TRAFFIC_FP64_SPA = 98.877696e6 + 45.069312e6
 
 
 def base_line(args, world, metric, value, unit, ms, workload, extra=None):

@@ -63,8 +63,6 @@ struct SpaParams {
 
 template <int BPL, int PREC>
 struct Smem {
-  double2 tab[PREC == 0 ? kTabN : 1];
-
   int list[kListCap];
   int wsum[kWarps + 1];
   long long tile;
@@ -290,10 +288,6 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int TB = 32 * BPL;
   if (*P.status != 0) return;
-  if (PREC == 0)
-    for (int i = tid; i < kTabN; i += kThreads) S.tab[i] = P.tab[i];
-
-  __syncthreads();
 
   for (;;) {
     if (tid == 0) S.tile = (long long)atomicAdd(&P.counters[0], 1ull);
@@ -439,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
             unsigned long long Th = phase_q64(C, g, delta, u, pos_slope);
             if (EXT && coal) Th += pos_slope ? (1ull << 61) : (0ull - (1ull << 61));
             double er, ei;
-            cis_q64(Th, S.tab, er, ei);
+            cis_q64(Th, P.tab, er, ei);   // the 64 KB table is read through L1
             // a9-a10
             const SegAmp64 Am = P.amp64[M.seg_base + s];
             double are = fma(u, fma(u, fma(u, Am.re[3], Am.re[2]), Am.re[1]), Am.re[0]);
