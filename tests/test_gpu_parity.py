@@ -212,3 +212,32 @@ def test_autotuner(tmp_path, monkeypatch):
     r2 = autotune.tune(plan, b, out)
     assert r2["cached"] and r2["tile_bins"] == r1["tile_bins"]
     plan.close()
+
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_long_trajectory_and_high_l(oracle, prec):
+    """1000 knots (every lane of the spline scans carries about 31 rows) and modes up
+    to l = 20, the largest the library accepts, with partners, on a ragged grid."""
+    T = 1.0 * synth.YEAR_S
+    t, pp, pr, op, orr = synth.trajectory(T, 1000)
+    l = np.array([2, 5, 9, 14, 20, 20, 17, 20], np.int32)
+    m = np.array([2, 3, 9, 1, 20, 7, 0, 13], np.int32)
+    n = np.array([0, -2, 4, 1, 0, -3, 2, 5], np.int32)
+    A = synth.amplitudes(np.random.default_rng(11), t, l, m, n, 1.0)
+    f = np.sort(np.random.default_rng(12).uniform(1e-4, 1.2e-2, 7777))
+    w = synth.Waveform(t, pp, pr, op, orr, l, m, n, A, 0.9, 0.3, 1.0, f)
+    _cmp(run(w, precision=prec), oracle.sum_modes(w), TOL64)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_many_nonuniform_knots(oracle, prec):
+    """Linear chirp and quadratic voice on 1000 and 700 random knots (no partners)."""
+    for w, p in (AN.linear_chirp(K=1000, seed=5), AN.quadratic_voice(K=700, seed=6)):
+        got = run(w, conj=False, precision=prec)
+        ref = oracle.sum_modes(w, conj_partners=False)
+        # bins within 1e-6 of a turnover frequency are ill-conditioned (|H| ~ |f - F*|^(-1/4))
+        far = np.abs(w.freqs - p.get("Fs", -1.0)) > 1e-6 * p.get("Fs", 0.0)
+        for g, r in zip(got, ref):
+            assert rel_l2(g[far], r[far]) <= TOL64
+        assert np.array_equal(np.abs(got[0]) > 0, np.abs(ref[0]) > 0)
