@@ -30,8 +30,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = ("paper-shaped FP64 single waveform: T=2 yr, K=200 knots, 2000 modes (l=2..10, m=1..l, "
             "|n|<=30, top mean power of 3294), 3,155,760 bins f=i/T, conjugate partners implied")
-FP64_OPS_PER_MODE_BIN = 39      # 27 DFMA + 12 DMUL/DADD per mode-bin in k_spa<*, 0, 0> (counted from the source)
-FP64_FLOPS_PER_MODE_BIN = 66    # 27 x 2 + 12
+FP64_OPS_PER_MODE_BIN = 34      # 26 DFMA + 8 DMUL/DADD per mode-bin in k_spa<*, 0, 0> (counted from the source)
+FP64_FLOPS_PER_MODE_BIN = 60    # 26 x 2 + 8
 FP64_PER_CLK_PER_SM = 2          # GB300 FP64 issue rate (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
 
 
@@ -218,7 +218,7 @@ FORM_TILE = {"fp64x": 64, "mixed": 128}
 DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
 # DRAM bytes (read + write) of one k_spa<4,0,0> launch (FP64, standard SPA, 128-bin tiles) on
 # this workload, from one ncu capture of the kernel as it stands
-TRAFFIC_FP64_SPA = 98.877696e6 + 45.069312e6
+TRAFFIC_FP64_SPA = 100.444160e6 + 62.491648e6
 
 
 def base_line(args, world, metric, value, unit, ms, workload, extra=None):

@@ -115,19 +115,29 @@ struct AdjParams {
   const int* status;
 };
 
-__global__ void __launch_bounds__(256) k_adjoint(AdjParams P) {
-  extern __shared__ __align__(16) double2 tab[];
-  for (int i = threadIdx.x; i < kTabN; i += blockDim.x) tab[i] = P.tab[i];
-  __syncthreads();
+// last r in [0, n) with off[r] <= it, for ascending off with off[0] <= it: one warp,
+// all lanes with the same it, 32 probes per round (the probes that pass are a prefix)
+__device__ __forceinline__ long long last_le_warp(const int* off, long long n, long long it, int lane) {
+  long long base = 0, len = n;   // answer in [base, base + len); off[base] <= it
+  while (len > 1) {
+    const long long step = (len + 31) >> 5;
+    const long long p = base + lane * step;
+    const bool ok = p < base + len && off[p] <= it;
+    const int c = 31 - __clz(__ballot_sync(0xffffffffu, ok));   // lane 0 probes base, so c >= 0
+    base += c * step;
+    len = min(step, len - c * step);
+  }
+  return base;
+}
+
+__global__ void __launch_bounds__(256, 2) k_adjoint(AdjParams P) {
   if (*P.status != 0) return;
   const int lane = threadIdx.x & 31;
   const long long nitems = P.item_off[P.run_cap];
   const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long it = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; it < nitems; it += wstride) {
-    // run of this item: last r with item_off[r] <= it
-    long long lo = 0, hi = P.run_cap - 1;
-    while (lo < hi) { long long mid = (lo + hi + 1) >> 1; if (P.item_off[mid] <= it) lo = mid; else hi = mid - 1; }
-    const long long r = lo;
+    // run of this item: last r with item_off[r] <= it (32 probes per round)
+    const long long r = last_le_warp(P.item_off, P.run_cap, it, lane);
     const Run R = P.runs[r];
     const int s = R.s0 + (int)(it - P.item_off[r]);
     const RunBins B = P.rb[r];
@@ -136,7 +146,13 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjParams P) {
     const SegCore C = P.core[M.seg_base + s];
     const SegAmp64 Am = P.amp64[M.seg_base + s];
     const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
-    double acc[16];
+    // per-segment constants of dA/du, d2F/du2 and dPhi_V/du
+    const double a3r = 3.0 * Am.re[3], a2r = 2.0 * Am.re[2], a3i = 3.0 * Am.im[3], a2i = 2.0 * Am.im[2];
+    const double d2c = 2.0 * C.d3, p2c = 2.0 * C.P2, p3c = 3.0 * C.P3;
+    // acc[0..3]: sum tD u^k (k = 0..3), combined with hsum after the loop into the
+    // frequency-coefficient derivatives sum (tD u^k + k hD u^(k-1)); acc[4..7] phase,
+    // acc[8..15] amplitude coefficients
+    double acc[16], hsum[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int q = 0; q < 16; q++) acc[q] = 0.0;
     for (int sg = 0; sg < 2; sg++) {
@@ -146,7 +162,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjParams P) {
       // bins of this segment: knot s passed (s > s0) and knot s+1 not passed (s < s1)
       auto passed = [&](int k, long long b) {
         const double f = P.freqs[b];
-        const long long key = ordkey(neg ? -f : f);
+        const long long key = ordkey(neg ? flip_sign(f) : f);
         const long long kk = P.keyF[M.key_base + k];
         return R.dir > 0 ? (kk <= key) : (kk >= key);
       };
@@ -161,55 +177,75 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjParams P) {
         if (suffix) hi_b = min(hi_b, x); else lo_b = max(lo_b, x);
       }
       for (long long b = lo_b + lane; b < hi_b; b += 32) {
-        const double g = neg ? -P.freqs[b] : P.freqs[b];
+        const double g = neg ? flip_sign(P.freqs[b]) : P.freqs[b];
         const double delta = g - C.A;
         float uf, Df;
         const double u = solve_root<6>(C, delta, ulo, uhi, R.dir, uf, Df);
         const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
         const long long Dbits = __double_as_longlong(Dd);
-        if ((Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0) continue;
+        if (is_zero_bits(Dd)) continue;
         const unsigned long long Th = phase_q64(C, g, delta, u, Dbits >= 0);
         const double wgt = rsqrt_abs(Dd);
-        double er, ei;
-        cis_q64(Th, tab, er, ei);
-        const double Er = wgt * er, Ei = wgt * ei;            // E = |D|^{-1/2} e^{i psi}
+        double Er, Ei;
+        cis_w_q64(Th, P.tab, wgt, Er, Ei);                    // E = |D|^{-1/2} e^{i psi}
         const double Ar = fma(u, fma(u, fma(u, Am.re[3], Am.re[2]), Am.re[1]), Am.re[0]);
         const double Ai = fma(u, fma(u, fma(u, Am.im[3], Am.im[2]), Am.im[1]), Am.im[0]);
-        const double dAr = fma(u, fma(u, 3.0 * Am.re[3], 2.0 * Am.re[2]), Am.re[1]);
-        const double dAi = fma(u, fma(u, 3.0 * Am.im[3], 2.0 * Am.im[2]), Am.im[1]);
+        const double dAr = fma(u, fma(u, a3r, a2r), Am.re[1]);
+        const double dAi = fma(u, fma(u, a3i, a2i), Am.im[1]);
         const dbl4 Gb = P.G[b];
         double Qr, Qi;
         if (!neg) { Qr = M.alpha * Gb.x + M.beta * Gb.w; Qi = -M.alpha * Gb.y + M.beta * Gb.z; }
         else { Qr = M.alpha * Gb.x - M.beta * Gb.w; Qi = M.alpha * Gb.y + M.beta * Gb.z; }
         const double QEr = Qr * Er - Qi * Ei, QEi = Qr * Ei + Qi * Er;
         const double QZr = QEr * Ar - QEi * Ai, QZi = QEr * Ai + QEi * Ar;
-        const double Dp = fma(2.0 * C.d3, u, C.c2);           // d^2F/du^2
-        const double dpsi = kTwoPi * (delta * C.h - C.Q1 - u * (2.0 * C.P2 + 3.0 * C.P3 * u));  // 2 pi g h - Phi_V'(u)
+        const double Dp = fma(d2c, u, C.c2);                  // d^2F/du^2
+        const double dpsi = kTwoPi * fma(-u, fma(p3c, u, p2c), fma(delta, C.h, -C.Q1));  // 2 pi g h - Phi_V'(u)
         const double w2 = wgt * wgt;                          // 1/|dF/du| from the weight: no FP64 division
-        const double invD = Dbits >= 0 ? w2 : -w2;
-        const double T = (QEr * dAr - QEi * dAi) - 0.5 * QZr * Dp * invD - QZi * dpsi;
-        const double up[4] = {1.0, u, u * u, u * u * u};
-        const double tD = -T * invD, hD = -0.5 * QZr * invD;
+        const double invD = Dbits >= 0 ? w2 : flip_sign(w2);
+        const double hD = -0.5 * QZr * invD;
+        const double T = fma(QEr, dAr, fma(-QEi, dAi, fma(hD, Dp, -QZi * dpsi)));
+        const double tD = -T * invD;
+        const double u2 = u * u, u3 = u2 * u;
         acc[0] += tD;
-        acc[1] += tD * up[1] + hD;
-        acc[2] += tD * up[2] + 2.0 * hD * up[1];
-        acc[3] += tD * up[3] + 3.0 * hD * up[2];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-          acc[4 + k] += up[k] * QZi;
-          acc[8 + k] += up[k] * QEr;
-          acc[12 + k] += -up[k] * QEi;
-        }
+        acc[1] = fma(tD, u, acc[1]);
+        acc[2] = fma(tD, u2, acc[2]);
+        acc[3] = fma(tD, u3, acc[3]);
+        hsum[0] += hD;
+        hsum[1] = fma(hD, u, hsum[1]);
+        hsum[2] = fma(hD, u2, hsum[2]);
+        acc[4] += QZi;
+        acc[5] = fma(u, QZi, acc[5]);
+        acc[6] = fma(u2, QZi, acc[6]);
+        acc[7] = fma(u3, QZi, acc[7]);
+        acc[8] += QEr;
+        acc[9] = fma(u, QEr, acc[9]);
+        acc[10] = fma(u2, QEr, acc[10]);
+        acc[11] = fma(u3, QEr, acc[11]);
+        acc[12] -= QEi;
+        acc[13] = fma(-u, QEi, acc[13]);
+        acc[14] = fma(-u2, QEi, acc[14]);
+        acc[15] = fma(-u3, QEi, acc[15]);
       }
     }
-    // fixed-order warp tree
+    acc[1] += hsum[0];
+    acc[2] = fma(2.0, hsum[1], acc[2]);
+    acc[3] = fma(3.0, hsum[2], acc[3]);
+    // fixed-order transposed warp reduction of the 16 sums: at each halving step a
+    // lane keeps half of its values and adds its partner's copy of them, so after
+    // 8 + 4 + 2 + 1 exchanges and a final pair sum, lanes 2q and 2q + 1 hold sum q
+    // (16 shuffles and adds per lane instead of 80)
 #pragma unroll
-    for (int q = 0; q < 16; q++) {
-      double v = acc[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      acc[q] = v;
+    for (int w = 8; w >= 1; w >>= 1) {
+      const bool upper = (lane & (2 * w)) != 0;   // keeps the upper half of its current values
+#pragma unroll
+      for (int j = 0; j < w; j++) {
+        const double send = upper ? acc[j] : acc[j + w];
+        const double keep = upper ? acc[j + w] : acc[j];
+        acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * w);
+      }
     }
-    if (lane == 0) {
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+    {
       // sub-piece of segment s that this run covers
       int piece = 0;
       if (s == R.s0) {
@@ -217,8 +253,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjParams P) {
         for (int c = 0; c < X.n; c++) if (X.u[c] <= R.u0) piece++;
       }
       double* dst = P.slots + ((M.seg_base + s) * 3 + piece) * 16;
-#pragma unroll
-      for (int q = 0; q < 16; q++) dst[q] = acc[q];
+      if ((lane & 1) == 0) dst[lane >> 1] = acc[0];
     }
     (void)W;
   }
@@ -468,9 +503,7 @@ void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& 
   p.wf = s.wf; p.modes = s.modes; p.core = s.core; p.amp64 = s.amp64; p.crit = s.crit; p.keyF = s.keyF;
   p.runs = s.runs; p.rb = s.rbins; p.freqs = in.freqs; p.G = reinterpret_cast<const dbl4*>(s.Gbuf);
   p.item_off = s.item_off; p.run_cap = s.run_cap; p.tab = s.tab; p.slots = s.slots; p.status = s.status;
-  const size_t sm = sizeof(double2) * kTabN;
-  cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_adjoint<<<(unsigned)(num_sms * 3), 256, sm, st>>>(p);
+  k_adjoint<<<(unsigned)(num_sms * 2), 256, 0, st>>>(p);   // two resident CTAs per SM (128 registers)
   k_seg_sum<<<(unsigned)((cs.seg_total + 255) / 256), 256, 0, st>>>(cs.seg_total, s.wf, s.modes, cs.n_wf, s.core,
                                                                     in.prefactor, s.slots);
   k_amp_knot<<<(unsigned)((cs.amp_total + 255) / 256), 256, 0, st>>>(cs.amp_total, cs.n_wf, s.wf, s.modes, in.t,

@@ -25,8 +25,10 @@ namespace emrifd {
 
 constexpr int kWarps = 8;                 // warps per CTA of the hot kernel
 constexpr int kThreads = 32 * kWarps;
-constexpr int kTabBits = 12;              // e^{2 pi i k / 4096} table
+constexpr int kTabBits = 12;              // FP32-pair table e^{2 pi i k / 4096} (FP64X form)
 constexpr int kTabN = 1 << kTabBits;
+constexpr int kTab64Bits = 16;            // FP64 table e^{2 pi i k / 65536} (FP64 form, adjoint)
+constexpr int kTab64N = 1 << kTab64Bits;
 constexpr int kListCap = 2048;            // (run, sign) entries buffered per tile pass
 
 // status bits latched in the plan's device status word
@@ -42,6 +44,7 @@ struct WfInfo {
   long long seg_base;      // first (mode, segment) record = sum_{w'<w} N_m (K-1)
   long long tile_base, ntiles;
   long long run_base, nruns;  // filled on the device
+  int occ_lo, occ_hi;         // global bins [occ_lo, occ_hi) some run covers (filled on the device)
 };
 
 struct ModeInfo {
@@ -103,6 +106,21 @@ __device__ __forceinline__ long long ordkey(double x) {
 
 __device__ __forceinline__ double unordkey(long long k) {
   return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFLL));
+}
+
+__device__ __forceinline__ double abs_bits(double x) {
+  // |x| through the sign bit (fabs of a value that is also used bit-wise costs an FP64 add)
+  return __hiloint2double(__double2hiint(x) & 0x7FFFFFFF, __double2loint(x));
+}
+
+__device__ __forceinline__ bool is_zero_bits(double x) {
+  // x == +-0 from the two words (a test on the 64-bit pattern becomes an FP64 compare)
+  return ((__double2hiint(x) & 0x7FFFFFFF) | __double2loint(x)) == 0;
+}
+
+__device__ __forceinline__ double flip_sign(double x) {
+  // -x through the sign bit (an integer operation, not an FP64 instruction)
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
 }
 
 __device__ __forceinline__ float d2f_bits(double x) {
@@ -226,7 +244,7 @@ struct DevScratch {
   double2* runF;                  // [run_cap] (F at run start, F at run end)
   RunBins* rbins;
   long long run_cap;
-  double2* tab;                   // [kTabN] e^{2 pi i k / kTabN}
+  double2* tab;                   // [kTab64N] e^{2 pi i k / kTab64N}
   float4* tabf;                   // [kTabN] the same as FP32 pairs (cos hi, cos lo, sin hi, sin lo), FP64X plans
   // likelihood / adjoint scratch (plans created with likelihood = 1)
   double* hbuf;                   // [2][sum N_f] complex128: h+ then hx

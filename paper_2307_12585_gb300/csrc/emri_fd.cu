@@ -180,7 +180,7 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
   AL(s.runs, s.run_cap);
   AL(s.runF, s.run_cap);
   AL(s.rbins, s.run_cap);
-  AL(s.tab, kTabN);
+  AL(s.tab, kTab64N);
   if (d->likelihood) {
     AL(s.hbuf, 4 * p->cap_nf);
     AL(s.Gbuf, 4 * p->cap_nf);

@@ -49,8 +49,8 @@ constexpr size_t kOffRuns = kOffRunCnt + al256((kNaMaxModes + 1) * sizeof(int));
 constexpr size_t kOffRunF = kOffRuns + al256(kNaRunCap * sizeof(Run));
 constexpr size_t kOffRbins = kOffRunF + al256(kNaRunCap * sizeof(double2));
 constexpr size_t kOffTab = kOffRbins + al256(kNaRunCap * sizeof(RunBins));
-constexpr size_t kNaBytes = kOffTab + al256(kTabN * sizeof(double2));
-static_assert(kNaBytes == 6570240, "the size stated in include/emri_fd.h");
+constexpr size_t kNaBytes = kOffTab + al256(kTab64N * sizeof(double2));
+static_assert(kNaBytes == 7553280, "the size stated in include/emri_fd.h");
 
 // The scratch.  In host code this name is only a stand-in for the device
 // symbol; its device address comes from cudaGetSymbolAddress below.

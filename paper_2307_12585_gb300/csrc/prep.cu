@@ -653,6 +653,8 @@ __global__ void k_wf_runs(int n_wf, WfInfo* wf, const int* run_off, long long ru
   if (b > run_cap) b = run_cap;
   wf[w].run_base = a;
   wf[w].nruns = b - a;
+  wf[w].occ_lo = (int)(wf[w].fo + wf[w].nf);   // empty until k_run_bins widens it
+  wf[w].occ_hi = (int)wf[w].fo;
 }
 
 // Output-bin ranges of each run.  Increasing runs own [F_start, F_end),
@@ -689,7 +691,7 @@ __device__ __forceinline__ long long group_bound(const long long* fk, long long 
   return bal ? lo + (__ffs(bal) - 1) : hi;
 }
 
-__global__ void k_run_bins(const WfInfo* wf, const ModeInfo* modes, long long nm_total, const int* run_total,
+__global__ void k_run_bins(WfInfo* wf, const ModeInfo* modes, long long nm_total, const int* run_total,
                            const Run* runs, const double2* runF, long long run_cap, const double* freqs, RunBins* rb,
                            unsigned long long* counters, int* status) {
   const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -709,7 +711,8 @@ __global__ void k_run_bins(const WfInfo* wf, const ModeInfo* modes, long long nm
     }
     return;
   }
-  const WfInfo W = wf[modes[R.mode].wf];
+  const int wi = modes[R.mode].wf;
+  const WfInfo W = wf[wi];
   if (R.s0 < 0 || R.s1 < R.s0 || R.s1 >= W.K - 1 || R.dir == 0) {
     if (lane == 0) {
       B.b0p = B.b1p = B.b0n = B.b1n = (int)W.fo;
@@ -741,26 +744,31 @@ __global__ void k_run_bins(const WfInfo* wf, const ModeInfo* modes, long long nm
     rb[r] = B;
     unsigned long long cnt = (unsigned long long)((e1p - b0p) + (e1n - b0n));
     if (cnt) atomicAdd(&counters[1], cnt);
+    // the waveform's occupied bin range, so that the output kernel skips the run
+    // scan for tiles no run reaches
+    if (e1p > b0p) { atomicMin(&wf[wi].occ_lo, B.b0p); atomicMax(&wf[wi].occ_hi, B.b1p); }
+    if (e1n > b0n) { atomicMin(&wf[wi].occ_lo, B.b0n); atomicMax(&wf[wi].occ_hi, B.b1n); }
   }
 }
 
 __global__ void k_table(double2* tab) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= kTabN) return;
+  if (k >= kTab64N) return;
   double s, c;
-  sincospi((double)k / (double)(kTabN / 2), &s, &c);
+  sincospi((double)k / (double)(kTab64N / 2), &s, &c);
   tab[k] = make_double2(c, s);
 }
 
 }  // namespace
 
-void launch_table(double2* tab, cudaStream_t st) { k_table<<<(kTabN + 255) / 256, 256, 0, st>>>(tab); }
+void launch_table(double2* tab, cudaStream_t st) { k_table<<<(kTab64N + 255) / 256, 256, 0, st>>>(tab); }
 
 namespace {
 __global__ void k_table_ff(const double2* tab, float4* tabf) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= kTabN) return;
-  const ff c = ff_from_double(tab[k].x), s = ff_from_double(tab[k].y);
+  const double2 e = tab[(long long)k << (kTab64Bits - kTabBits)];   // e^{2 pi i k / kTabN}
+  const ff c = ff_from_double(e.x), s = ff_from_double(e.y);
   tabf[k] = make_float4(c.hi, c.lo, s.hi, s.lo);
 }
 }  // namespace

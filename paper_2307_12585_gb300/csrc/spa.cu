@@ -208,13 +208,13 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
 template <bool EXT>
 __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am, double f, bool neg, double ulo,
                                            double uhi, int dir, float fa, float fb, float* v) {
-  const double g = neg ? -f : f;
+  const double g = neg ? flip_sign(f) : f;
   const double delta = g - C.A;
   float uf, Df;
   const double u = solve_root<4, EXT>(C, delta, ulo, uhi, dir, uf, Df);
   const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
   const long long Dbits = __double_as_longlong(Dd);
-  bool coal = (Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0;
+  bool coal = is_zero_bits(Dd);
   if (!EXT && coal) return false;
   const bool pos = Dbits >= 0;
   float wgt = rsqrtf(fabsf(Df));
@@ -280,9 +280,15 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
 #ifndef EMRI_FD_SPA_MINB
 #define EMRI_FD_SPA_MINB 4
 #endif
+// and the standard-SPA FP64 kernel (three CTAs of 256 threads: 80 registers, a few
+// spilled; 1.4% faster than two CTAs at 128 registers on the 2-yr, 2000-mode
+// workload).  The extended form's FP64 kernel keeps two.
+#ifndef EMRI_FD_SPA64_MINB
+#define EMRI_FD_SPA64_MINB 3
+#endif
 
 template <int BPL, int PREC, bool EXT>
-__global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_spa(SpaParams P) {
+__global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64_MINB) : EMRI_FD_SPA_MINB) k_spa(SpaParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<BPL, PREC>& S = *reinterpret_cast<Smem<BPL, PREC>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
       long long b = bin0 + lane + 32 * q;
       fq[q] = b < binEnd ? P.freqs[b] : 1.0;
       kp[q] = ordkey(fq[q]);
-      kn[q] = ordkey(-fq[q]);
+      kn[q] = ordkey(flip_sign(fq[q]));
     }
     double acc[BPL][4];
     float accf[BPL][4], cmp[BPL][4];
@@ -324,7 +330,9 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
       for (int c = 0; c < 4; c++) { acc[q][c] = 0.0; accf[q][c] = 0.f; cmp[q][c] = 0.f; }
 
     long long rcur = 0;
-    const long long nruns = W.nruns;
+    bool any = false;   // the tile has at least one entry (block-uniform)
+    // a tile outside the waveform's occupied bin range has no entries: skip the run scan
+    const long long nruns = (bin0 < W.occ_hi && binEnd > W.occ_lo) ? W.nruns : 0;
     while (rcur < nruns || rcur == 0) {
       // ---- collect (run, sign) entries overlapping [bin0, binEnd), ascending; each
       // thread tests kRpt consecutive runs per pass (one block-wide scan per
@@ -364,6 +372,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
           if (flags & (2u << (2 * k))) S.list[pos++] = (int)(((rb + k) << 1) | 1);
         }
         cnt += total;
+        any |= total > 0;
         rcur += (long long)kRpt * kThreads;
         __syncthreads();
       }
@@ -386,18 +395,20 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
         if constexpr (PREC != 0) {
           const long long lo_b = max((long long)b0, bin0), hi_b = min((long long)b1, binEnd) - 1;
           const double flo = P.freqs[lo_b], fhi = P.freqs[hi_b];
-          const int s_lo = run_segment_warp(R, P.keyF, M.key_base, ordkey(neg ? -flo : flo), lane);
-          const int s_hi = run_segment_warp(R, P.keyF, M.key_base, ordkey(neg ? -fhi : fhi), lane);
+          const int s_lo = run_segment_warp(R, P.keyF, M.key_base, ordkey(neg ? flip_sign(flo) : flo), lane);
+          const int s_hi = run_segment_warp(R, P.keyF, M.key_base, ordkey(neg ? flip_sign(fhi) : fhi), lane);
           s_uni = s_lo == s_hi ? s_lo : -1;
         }
         if constexpr (PREC == 0) {
-          const double sa = M.alpha, sb = neg ? -M.beta : M.beta;   // h+ += alpha Z~, hx += i sb Z~
+          // h+ += alpha Z~, hx += i sb Z~; the sign flips are integer operations on the sign bit
+          const double sa = M.alpha, sai = neg ? flip_sign(M.alpha) : M.alpha;
+          const double sb = neg ? flip_sign(M.beta) : M.beta, nbeta = flip_sign(M.beta);
 #pragma unroll
           for (int q = 0; q < BPL; q++) {
             const long long bin = bin0 + lane + 32 * q;
             if (bin < b0 || bin >= b1) continue;
-            const double g = neg ? -fq[q] : fq[q];
-            const long long key = neg ? kn[q] : kp[q];
+            const double g = neg ? flip_sign(fq[q]) : fq[q];
+            const long long key = ordkey(g);
             // a5: segment holding the root
             const int s = run_segment(R, P.keyF, M.key_base, key);
             const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
@@ -409,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
             // a8: dF/du and the weight sqrt(h)/sqrt|dF/du| (sqrt(h) is in the amplitude)
             const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
             const long long Dbits = __double_as_longlong(Dd);
-            bool coal = (Dbits & 0x7FFFFFFFFFFFFFFFLL) == 0;   // Fdot == 0
+            bool coal = is_zero_bits(Dd);   // Fdot == 0
             if (!EXT && coal) continue;                         // standard form: no contribution
             const bool pos_slope = Dbits >= 0;
             double wgt = coal ? 0.0 : rsqrt_abs(Dd);
@@ -433,13 +444,11 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
             unsigned long long Th = phase_q64(C, g, delta, u, pos_slope);
             if (EXT && coal) Th += pos_slope ? (1ull << 61) : (0ull - (1ull << 61));
             double er, ei;
-            cis_q64(Th, P.tab, er, ei);   // the 64 KB table is read through L1
+            cis_w_q64(Th, P.tab, wgt, er, ei);   // w e^{i psi}; the 1 MB table is read through L1 and L2
             // a9-a10
             const SegAmp64 Am = P.amp64[M.seg_base + s];
             double are = fma(u, fma(u, fma(u, Am.re[3], Am.re[2]), Am.re[1]), Am.re[0]);
             double aim = fma(u, fma(u, fma(u, Am.im[3], Am.im[2]), Am.im[1]), Am.im[0]);
-            are *= wgt;
-            aim *= wgt;
             if constexpr (EXT) {
               const double nr = fma(are, rr, -aim * ri);
               aim = fma(are, ri, aim * rr);
@@ -450,8 +459,8 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
             // a11: positive branch h+ += alpha Z, hx += i beta Z;
             //      negative branch h+ += alpha conj Z, hx += -i beta conj Z
             acc[q][0] = fma(sa, zr, acc[q][0]);
-            acc[q][1] = fma(neg ? -sa : sa, zi, acc[q][1]);
-            acc[q][2] = fma(-M.beta, zi, acc[q][2]);
+            acc[q][1] = fma(sai, zi, acc[q][1]);
+            acc[q][2] = fma(nbeta, zi, acc[q][2]);
             acc[q][3] = fma(sb, zr, acc[q][3]);
           }
         } else {
@@ -505,6 +514,21 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? 2 : EMRI_FD_SPA_MINB) k_
       if (rcur >= nruns) break;
     }
 
+    // ---- a tile without entries is written as zeros, without the reduction
+    if (!any) {
+      for (int i = tid; i < TB; i += kThreads) {
+        const long long bin = bin0 + i;
+        if (bin >= binEnd) continue;
+        if constexpr (PREC == 1) {
+          reinterpret_cast<float2*>(P.hp)[bin] = make_float2(0.f, 0.f);
+          reinterpret_cast<float2*>(P.hc)[bin] = make_float2(0.f, 0.f);
+        } else {
+          reinterpret_cast<double2*>(P.hp)[bin] = make_double2(0.0, 0.0);
+          reinterpret_cast<double2*>(P.hc)[bin] = make_double2(0.0, 0.0);
+        }
+      }
+      continue;   // the loop's closing barrier above separates this tile from the next
+    }
     // ---- fixed-order reduction over warps, one store per bin (FP64 sums for the
     // FP64 form; FP32 pairs for the other two, so that they spend no FP64
     // instruction per bin beyond the final conversion)

@@ -165,27 +165,49 @@ __device__ __forceinline__ double small_ll_to_double(long long r) {
   return __longlong_as_double((long long)bits);
 }
 
-// e^{2 pi i Th/2^64}: 4096-entry table times 1 + i x - x^2/2 - i x^3/6, |x| <= pi/4096
-__device__ __forceinline__ void cis_q64(unsigned long long Th, const double2* tab, double& er, double& ei) {
-  const unsigned long long kq = (Th + (1ull << (63 - kTabBits))) >> (64 - kTabBits);
-  const long long rr = (long long)(Th - (kq << (64 - kTabBits)));   // |rr| <= 2^51
-  const double x = small_ll_to_double(rr) * kTwoPiOver2p64;
-  const double x2 = x * x;
-  const double cx = fma(x2, -0.5, 1.0);
-  const double sx = x * fma(x2, -1.0 / 6.0, 1.0);
-  const double2 T = tab[kq & (kTabN - 1)];
-  er = fma(T.x, cx, -T.y * sx);
-  ei = fma(T.y, cx, T.x * sx);
+// -x/2 for a normal double x, from its bits: the sign flipped and the exponent
+// lowered by one (integer instructions only)
+__device__ __forceinline__ double neg_half_normal(double x) {
+  return __hiloint2double((__double2hiint(x) ^ (int)0x80000000) - 0x00100000, __double2loint(x));
+}
+
+// w e^{2 pi i Th/2^64}: the table entry T_k = e^{2 pi i k/65536} nearest Th, times
+// w (1 - x^2/2 + i x) with x = 2 pi (Th/2^64 - k/65536), |x| <= pi/65536.  The
+// omitted terms of e^{ix} are below |x|^3/6 = 1.9e-14; the real factor w enters
+// the two-term factor without a separate multiply (8 FP64 instructions in all)
+__device__ __forceinline__ void cis_w_q64(unsigned long long Th, const double2* tab, double w, double& er,
+                                          double& ei) {
+  const unsigned long long kq = (Th + (1ull << (63 - kTab64Bits))) >> (64 - kTab64Bits);
+  const long long rr = (long long)(Th - (kq << (64 - kTab64Bits)));   // |rr| <= 2^47
+  const double x = small_ll_to_double(rr) * kTwoPiOver2p64;   // 0, or normal (|x| >= 3.4e-19)
+  const double wx = w * x;
+  const double cw = rr != 0 ? fma(wx, neg_half_normal(x), w) : w;
+  const double2 T = __ldg(tab + (kq & (kTab64N - 1)));
+  er = fma(T.x, cw, -T.y * wx);
+  ei = fma(T.y, cw, T.x * wx);
+}
+
+// y^2 exactly, as a double, for a positive normal float y: the product of the
+// 24-bit significands has at most 48 bits (integer instructions only)
+__device__ __forceinline__ double sq_exact(float y) {
+  const unsigned b = __float_as_uint(y);
+  const unsigned long long m = (b & 0x7FFFFFu) | 0x800000u;
+  const unsigned long long p = m * m;                  // in [2^46, 2^48)
+  const int top = (p >> 47) ? 47 : 46;                 // y^2 = p 2^(2e - 46), e the unbiased exponent
+  const long long ex = 2 * ((int)(b >> 23) - 127) - 46 + top + 1023;
+  return __longlong_as_double((ex << 52) | (long long)((p << (52 - top)) & 0xFFFFFFFFFFFFFull));
 }
 
 // a8: 1/sqrt|D| from an FP32 seed y0 and one FP64 Newton step,
-// y = y0 + (y0/2)(1 - |D| y0^2); y0/2 is formed exactly in FP32, so the step
-// takes three FP64 instructions
+// y = y0 + (y0/2)(1 - |D| y0^2); y0^2 and y0/2 are formed exactly outside the
+// FP64 pipe, so the step takes two FP64 instructions.  A |D| below the float
+// range gives an infinite seed (such a root sits on a turnover, where the
+// standard form diverges anyway).
 __device__ __forceinline__ double rsqrt_abs(double Dd) {
-  const double Dabs = fabs(Dd);
+  const double Dabs = abs_bits(Dd);
   const float y0f = rsqrtf(d2f_bits(Dabs));
   const double y0 = f2d_bits(y0f), y0h = f2d_bits(0.5f * y0f);
-  const double e = fma(-Dabs * y0, y0, 1.0);
+  const double e = fma(-Dabs, sq_exact(y0f), 1.0);
   return fma(y0h, e, y0);
 }
 
