@@ -34,7 +34,11 @@
  *  - Data pointers may be device memory (the fast path; required while a
  *    stream is being captured into a CUDA graph) or host memory, in which
  *    case the call stages them through plan-owned device buffers and, for
- *    host outputs, synchronises the stream before returning.
+ *    host outputs, synchronises the stream before returning.  The h_plus and
+ *    h_cross outputs of emri_fd_sum_modes are written in place, by the
+ *    kernels, when they are page-locked host memory the device can address
+ *    (cudaHostAlloc / cudaHostRegister; on GB300 over NVLink-C2C), so their
+ *    transfer overlaps the computation; pageable host outputs are staged.
  *  - Ownership: the caller owns every array passed in; the plan owns its
  *    scratch (spline coefficients, branch lists, work counters), sized at plan
  *    creation from the descriptor's maxima and never reallocated by a call on

@@ -282,7 +282,9 @@ constexpr int kLChunks = 512;      // per-waveform chunks of the likelihood's pa
 constexpr int kPrepKernels = 12;   // kernels launched by launch_prep (memsets excluded)
 constexpr int kAdjointKernels = 8; // kernels launched by launch_adjoint
 
-void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st);
+// freqs_ready (optional): an event the kernels that read in.freqs must wait for
+void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st,
+                 cudaEvent_t freqs_ready = nullptr);
 void launch_spa(const CallShape& cs, const DevInputs& in, const DevScratch& s, int num_sms, cudaStream_t st);
 void launch_prep_td(const CallShape& cs, const DevInputs& in, const DevScratch& s, float4* tdamp, cudaStream_t st);
 void launch_td_sum(const CallShape& cs, const DevInputs& in, const DevScratch& s, const float4* tdamp,

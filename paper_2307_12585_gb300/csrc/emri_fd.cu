@@ -20,6 +20,11 @@ struct emri_fd_plan_s {
   DevScratch s{};
   WfInfo* wf_pinned = nullptr;       // host copy uploaded each call
   cudaEvent_t wf_done = nullptr;     // guards reuse of wf_pinned
+  // host frequency grids of emri_fd_sum_modes are copied on a side stream while the
+  // preparation kernels that do not read them run
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_freqs = nullptr;
+  bool freqs_side = false;           // the next run_forward waits for ev_freqs
   unsigned long long* cnt_pinned = nullptr;
   // staging for host-memory inputs / outputs
   void* stage[32] = {};
@@ -107,6 +112,9 @@ void emri_fd_plan_destroy(emri_fd_plan_t p) {
   if (p->wf_pinned) cudaFreeHost(p->wf_pinned);
   if (p->cnt_pinned) cudaFreeHost(p->cnt_pinned);
   if (p->wf_done) cudaEventDestroy(p->wf_done);
+  if (p->side) { cudaStreamSynchronize(p->side); cudaStreamDestroy(p->side); }
+  if (p->ev_main) cudaEventDestroy(p->ev_main);
+  if (p->ev_freqs) cudaEventDestroy(p->ev_freqs);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   for (auto& fp : p->fft_plans) cufftDestroy(fp.second);
   if (p->zbuf) cudaFree(p->zbuf);
@@ -198,7 +206,10 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
 #undef AL
   if (st == EMRI_FD_OK && (cudaMallocHost(&p->wf_pinned, sizeof(WfInfo) * d->max_waveforms) != cudaSuccess ||
                            cudaMallocHost(&p->cnt_pinned, sizeof(unsigned long long) * 8) != cudaSuccess ||
-                           cudaEventCreateWithFlags(&p->wf_done, cudaEventDisableTiming) != cudaSuccess)) {
+                           cudaEventCreateWithFlags(&p->wf_done, cudaEventDisableTiming) != cudaSuccess ||
+                           cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&p->ev_main, cudaEventDisableTiming) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&p->ev_freqs, cudaEventDisableTiming) != cudaSuccess)) {
     cudaGetLastError();
     st = EMRI_FD_ERR_OOM;
   }
@@ -224,7 +235,7 @@ emri_fd_status prepare_call(emri_fd_plan_s* p, int n_wf, const long long* knot_o
                             const long long* freq_off, const double* t, const double* phi_phi, const double* phi_r,
                             const double* omega_phi, const double* omega_r, const int* l, const int* m, const int* n,
                             const double* amp, const double* theta, const double* phi, const double* prefactor,
-                            const double* freqs, CallShape& cs, DevInputs& in) {
+                            const double* freqs, CallShape& cs, DevInputs& in, bool freqs_on_side = false) {
   if (!p || n_wf < 1 || !knot_off || !mode_off || !freq_off) return EMRI_FD_ERR_ARG;
   if (n_wf > p->desc.max_waveforms) return EMRI_FD_ERR_CAPACITY;
   if (knot_off[0] != 0 || mode_off[0] != 0 || freq_off[0] != 0) return EMRI_FD_ERR_ARG;
@@ -290,13 +301,38 @@ emri_fd_status prepare_call(emri_fd_plan_s* p, int n_wf, const long long* knot_o
   STG(9, theta, sizeof(double) * n_wf, theta, const double*);
   STG(10, phi, sizeof(double) * n_wf, phi, const double*);
   STG(11, prefactor, sizeof(double) * n_wf, prefactor, const double*);
-  STG(12, freqs, sizeof(double) * cs.nf_total, freqs, const double*);
+  if (freqs_on_side && cs.nf_total > 0 && !is_device_ptr(freqs)) {
+    // staged on the side stream after the main stream's earlier readers of the buffer
+    const size_t fb = sizeof(double) * cs.nf_total;
+    if (p->stage_sz[12] < fb) {
+      if (p->stage[12]) { cudaStreamSynchronize(p->stream); cudaFree(p->stage[12]); }
+      p->stage[12] = nullptr;
+      p->stage_sz[12] = 0;
+      if (cudaMalloc(&p->stage[12], fb) != cudaSuccess) { cudaGetLastError(); return EMRI_FD_ERR_OOM; }
+      p->stage_sz[12] = fb;
+    }
+    if (cudaEventRecord(p->ev_main, p->stream) != cudaSuccess || cudaStreamWaitEvent(p->side, p->ev_main, 0) != cudaSuccess ||
+        cudaMemcpyAsync(p->stage[12], freqs, fb, cudaMemcpyHostToDevice, p->side) != cudaSuccess ||
+        cudaEventRecord(p->ev_freqs, p->side) != cudaSuccess)
+      return EMRI_FD_ERR_CUDA;
+    in.freqs = static_cast<const double*>(p->stage[12]);
+    p->freqs_side = true;
+  } else {
+    STG(12, freqs, sizeof(double) * cs.nf_total, freqs, const double*);
+  }
 #undef STG
   if (st != EMRI_FD_OK) return st;
   if (cudaMemcpyAsync(p->s.wf, p->wf_pinned, sizeof(WfInfo) * n_wf, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
       cudaEventRecord(p->wf_done, p->stream) != cudaSuccess)
     return EMRI_FD_ERR_CUDA;
   return EMRI_FD_OK;
+}
+
+// the device address of page-locked host memory the device can write in place, else null
+void* mapped_host_ptr(void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 // a device buffer for an output of `bytes` at `dst` (host outputs go to staging slot `slot`)
@@ -326,13 +362,16 @@ void run_forward(emri_fd_plan_s* p, const CallShape& cs, const DevInputs& in, si
     p->ev_used += 3;
     cudaEventRecord(E[0], stm);
   }
+  const cudaEvent_t freqs_ready = p->freqs_side ? p->ev_freqs : nullptr;
+  p->freqs_side = false;
   if (cs.nm_total > 0) {
-    launch_prep(cs, in, p->s, stm);
+    launch_prep(cs, in, p->s, stm, freqs_ready);
     p->launches += kPrepKernels;
   } else {
     // no modes: every run list is empty
     cudaMemsetAsync(p->s.run_cnt, 0, sizeof(int), stm);
   }
+  if (freqs_ready) cudaStreamWaitEvent(stm, freqs_ready, 0);   // (launch_prep has waited already)
   if (cs.nf_total > 0) {
     if (cs.nm_total == 0) {
       cudaMemsetAsync(in.h_plus, 0, ob, stm);
@@ -375,22 +414,25 @@ emri_fd_status emri_fd_sum_modes(emri_fd_plan_t p, int n_wf, const long long* kn
   CallShape cs;
   DevInputs in;
   emri_fd_status st = prepare_call(p, n_wf, knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r, l,
-                                   m, n, amp, theta, phi, prefactor, freqs, cs, in);
+                                   m, n, amp, theta, phi, prefactor, freqs, cs, in, true);
   if (st != EMRI_FD_OK) return st;
   if (cs.nf_total > 0 && (!h_plus || !h_cross)) return EMRI_FD_ERR_ARG;
   const size_t ob = (p->desc.precision == EMRI_FD_MIXED ? 8 : 16) * (size_t)cs.nf_total;
-  bool hp_host = false, hc_host = false;
-  if ((st = stage_out(p, 13, h_plus, ob, &in.h_plus, &hp_host)) != EMRI_FD_OK) return st;
-  if ((st = stage_out(p, 14, h_cross, ob, &in.h_cross, &hc_host)) != EMRI_FD_OK) return st;
+  bool hp_host = false, hc_host = false, in_place = false;
+  // page-locked host outputs: the kernels write them directly (no staging copy after the sum)
+  void* hp_map = (cs.nf_total > 0 && !is_device_ptr(h_plus)) ? mapped_host_ptr(h_plus) : nullptr;
+  void* hc_map = (cs.nf_total > 0 && !is_device_ptr(h_cross)) ? mapped_host_ptr(h_cross) : nullptr;
+  if (hp_map) { in.h_plus = hp_map; in_place = true; }
+  else if ((st = stage_out(p, 13, h_plus, ob, &in.h_plus, &hp_host)) != EMRI_FD_OK) return st;
+  if (hc_map) { in.h_cross = hc_map; in_place = true; }
+  else if ((st = stage_out(p, 14, h_cross, ob, &in.h_cross, &hc_host)) != EMRI_FD_OK) return st;
   run_forward(p, cs, in, ob);
   if (cudaGetLastError() != cudaSuccess) return EMRI_FD_ERR_CUDA;
   cudaStream_t stm = p->stream;
-  if (hp_host || hc_host) {
-    if ((hp_host && cudaMemcpyAsync(h_plus, in.h_plus, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess) ||
-        (hc_host && cudaMemcpyAsync(h_cross, in.h_cross, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess) ||
-        cudaStreamSynchronize(stm) != cudaSuccess)
-      return EMRI_FD_ERR_CUDA;
-  }
+  if ((hp_host && cudaMemcpyAsync(h_plus, in.h_plus, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess) ||
+      (hc_host && cudaMemcpyAsync(h_cross, in.h_cross, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess))
+    return EMRI_FD_ERR_CUDA;
+  if ((hp_host || hc_host || in_place) && cudaStreamSynchronize(stm) != cudaSuccess) return EMRI_FD_ERR_CUDA;
   return EMRI_FD_OK;
 }
 

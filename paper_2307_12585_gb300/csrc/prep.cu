@@ -817,14 +817,10 @@ void launch_prep_td(const CallShape& cs, const DevInputs& in, const DevScratch& 
                                                                    tdamp);
 }
 
-void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st) {
+void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st,
+                 cudaEvent_t freqs_ready) {
   dim3 gk(8, cs.n_wf);
   k_validate_knots<<<gk, 256, 0, st>>>(s.wf, in, s.status);
-  // about one bin per thread per waveform, at most 1216 CTAs (8 per SM of a 152-SM GB300)
-  long long gx = (cs.nf_total / (cs.n_wf > 0 ? cs.n_wf : 1) + 255) / 256;
-  gx = gx < 1 ? 1 : (gx > 1216 ? 1216 : gx);
-  dim3 gf((unsigned)gx, cs.n_wf);
-  k_validate_freqs<<<gf, 256, 0, st>>>(s.wf, in, s.status);
   k_validate_amp<<<256, 256, 0, st>>>(2 * cs.amp_total, in.amp, s.status);
   k_modes<<<(unsigned)((cs.nm_total * 32 + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes,
                                                                        cs.nm_total, s.status);
@@ -842,6 +838,13 @@ void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, 
   k_scan<<<1, 1024, 0, st>>>(s.run_cnt, cs.nm_total);
   k_wf_runs<<<(cs.n_wf + 63) / 64, 64, 0, st>>>(cs.n_wf, s.wf, s.run_cnt, s.run_cap);
   cudaMemsetAsync(s.runs, 0xFF, sizeof(Run) * (size_t)s.run_cap, st);
+  // the frequency grid is first read here (it may still be arriving on another stream)
+  if (freqs_ready) cudaStreamWaitEvent(st, freqs_ready, 0);
+  // about one bin per thread per waveform, at most 1216 CTAs (8 per SM of a 152-SM GB300)
+  long long gx = (cs.nf_total / (cs.n_wf > 0 ? cs.n_wf : 1) + 255) / 256;
+  gx = gx < 1 ? 1 : (gx > 1216 ? 1216 : gx);
+  dim3 gf((unsigned)gx, cs.n_wf);
+  k_validate_freqs<<<gf, 256, 0, st>>>(s.wf, in, s.status);
   k_runs<true><<<wblocks, 256, 0, st>>>(s.wf, s.modes, cs.nm_total, s.core, s.crit, s.keyF, s.run_cnt, s.runs,
                                         s.runF, s.run_cap, nullptr, s.status);
   k_run_bins<<<(unsigned)((s.run_cap * 32 + 255) / 256), 256, 0, st>>>(s.wf, s.modes, cs.nm_total, s.run_cnt + cs.nm_total,

@@ -287,6 +287,8 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
 #define EMRI_FD_SPA64_MINB 3
 #endif
 
+constexpr int kBackPerFront = 8;   // back-of-queue (empty) tiles a CTA may take after each front tile
+
 template <int BPL, int PREC, bool EXT>
 __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64_MINB) : EMRI_FD_SPA_MINB) k_spa(SpaParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -295,11 +297,28 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
   constexpr int TB = 32 * BPL;
   if (*P.status != 0) return;
 
+  // Two-ended tile queue in one 64-bit counter: the low word counts tiles taken from the
+  // front (ascending bins: the heavy low-frequency tiles first), the high word tiles taken
+  // from the back.  After each front tile a CTA takes up to kBackPerFront tiles from the
+  // back while they are empty (beyond every run), so the zero output of the empty tail is
+  // written while the heavy tiles are computed, not in a burst at the end (which matters
+  // when the output is host memory written over the host link).
+  int back = 0;                               // thread 0: back claims left
+  bool prev_back = false, prev_any = true;    // thread 0: how the previous tile was taken / had entries
+  bool started = false;                       // thread 0: a tile has been taken
   for (;;) {
-    if (tid == 0) S.tile = (long long)atomicAdd(&P.counters[0], 1ull);
+    if (tid == 0) {
+      back = !started ? 0 : (prev_back ? (prev_any ? 0 : back - 1) : kBackPerFront);
+      started = true;
+      const bool fb = back > 0;
+      const unsigned long long old = atomicAdd(&P.counters[0], fb ? (1ull << 32) : 1ull);
+      const long long a = (long long)(old & 0xFFFFFFFFull), b = (long long)(old >> 32);
+      S.tile = a + b < P.tiles_total ? (fb ? P.tiles_total - 1 - b : a) : -1;
+      prev_back = fb;
+    }
     __syncthreads();
     const long long tile = S.tile;
-    if (tile >= P.tiles_total) break;
+    if (tile < 0) break;
     int lo = 0, hi = P.n_wf - 1;
     while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (P.wf[mid].tile_base <= tile) lo = mid; else hi = mid - 1; }
     const WfInfo W = P.wf[lo];
@@ -514,6 +533,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
       if (rcur >= nruns) break;
     }
 
+    if (tid == 0) prev_any = any;
     // ---- a tile without entries is written as zeros, without the reduction
     if (!any) {
       for (int i = tid; i < TB; i += kThreads) {

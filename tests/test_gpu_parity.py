@@ -142,6 +142,24 @@ def test_host_pointer_path_equals_device_path():
     plan.close()
 
 
+@pytest.mark.parametrize("prec,window", [("fp64", None), ("mixed", None), ("fp64", "hann")])
+def test_pinned_host_outputs_written_in_place(prec, window):
+    """Page-locked host outputs are written by the kernels directly; the result is
+    bitwise the device-pointer result (also with no modes at all)."""
+    from paper_2307_12585_gb300 import api
+    w = synth.small_config(0, n_bins=5000)
+    for wf in (w, w.with_modes(np.zeros(0, np.int64))):
+        plan = api.Plan(prec, conj_partners=True, max_waveforms=1, max_knots=w.K, max_modes_total=w.n_modes,
+                        max_bins_total=w.n_freqs, window=window)
+        b = synth.concat([wf])
+        dh, dc = plan.sum_modes(plan.upload(b))
+        cdt = torch.complex64 if prec == "mixed" else torch.complex128
+        out = (torch.full((w.n_freqs,), 7.0, dtype=cdt).pin_memory(), torch.full((w.n_freqs,), 7.0, dtype=cdt).pin_memory())
+        plan.sum_modes_host(api.host_batch(b), out=out)
+        assert torch.equal(dh.cpu(), out[0]) and torch.equal(dc.cpu(), out[1])
+        plan.close()
+
+
 def test_degenerate_inputs(oracle):
     w = synth.small_config(0, n_bins=2000)
     # bins where no voice is present
