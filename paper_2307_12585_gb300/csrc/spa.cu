@@ -212,11 +212,19 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
   const double delta = g - C.A;
   float uf, Df;
   const double u = solve_root<4, EXT>(C, delta, ulo, uhi, dir, uf, Df);
-  const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
-  const long long Dbits = __double_as_longlong(Dd);
-  bool coal = is_zero_bits(Dd);
-  if (!EXT && coal) return false;
-  const bool pos = Dbits >= 0;
+  // the standard form needs dF/du only in FP32 (for the weight); its sign is the run's
+  // direction, and a root with Df == 0 sits on a turnover (no contribution)
+  double Dd = 0.0;
+  bool coal, pos;
+  if constexpr (EXT) {
+    Dd = fma(u, fma(u, C.d3, C.c2), C.b);
+    coal = is_zero_bits(Dd);
+    pos = __double_as_longlong(Dd) >= 0;
+  } else {
+    if (Df == 0.f) return false;
+    coal = false;
+    pos = dir > 0;
+  }
   float wgt = rsqrtf(fabsf(Df));
   float rr = 1.f, ri = 0.f;
   if constexpr (EXT) {
