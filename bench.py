@@ -33,6 +33,8 @@ WORKLOAD = ("paper-shaped FP64 single waveform: T=2 yr, K=200 knots, 2000 modes 
 FP64_OPS_PER_MODE_BIN = 34      # 26 DFMA + 8 DMUL/DADD per mode-bin in k_spa<*, 0, 0> (counted from the source)
 FP64_FLOPS_PER_MODE_BIN = 60    # 26 x 2 + 8
 FP64_PER_CLK_PER_SM = 2          # GB300 FP64 issue rate (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
+MIXED_FP64_OPS_PER_MODE_BIN = 9  # the mixed form's FP64 left per mode-bin: difference 1, root polish 4, phase 4
+ADJ_FP64_OPS_PER_MODE_BIN = 76   # k_adjoint per mode-bin: the forward's 30 (with dA/du) + 46 for the derivatives
 
 
 def parse():
@@ -392,7 +394,28 @@ def run_paper(args, rank, world, local):
                torch.linalg.vector_norm(oout[1].to(torch.complex128) - outs[0][1]) ** 2)
         den = torch.linalg.vector_norm(outs[0][0]) ** 2 + torch.linalg.vector_norm(outs[0][1]) ** 2
         oplan.close()
+        ospa_s = ost["spa_ns"] * 1e-9 / max(1, ost["timed_calls"])
+        if prec == "mixed" and spa == "standard":
+            # its FP64 (root polish, phase) against the FP64 pipe's peak; the ALU pipe
+            # (integer phase and keys) is about as busy
+            ach = MIXED_FP64_OPS_PER_MODE_BIN * mb_per_launch / ospa_s
+            pk = FP64_PER_CLK_PER_SM * n_sms * clk_hz
+            roof = {"bound": "fp64+alu", "achieved": ach / 1e12, "peak": pk / 1e12, "unit": "T FP64 inst/s",
+                    "frac": ach / pk, "note": "%d FP64 instructions per mode-bin (root polish, in-segment phase) "
+                    "against 2 FP64 instructions/clk/SM at the median SM clock; the rest is FP32 and integer work"
+                    % MIXED_FP64_OPS_PER_MODE_BIN}
+        elif prec == "fp64x" and spa == "standard":
+            # no FP64 per mode-bin: the FP64 form's 60 flops of FP64-accurate arithmetic per
+            # mode-bin, done in FP32 pairs, against the FP64 pipe's peak
+            ach = FP64_FLOPS_PER_MODE_BIN * mb_per_launch / ospa_s
+            roof = {"bound": "issue", "fp64_equivalent_achieved": ach / 1e12, "peak": peak_tflops,
+                    "unit": "TFLOP/s", "frac_of_fp64_peak": ach / (peak_tflops * 1e12),
+                    "note": "FP64-accurate work (the FP64 form's 60 flops per mode-bin) in FP32 pairs and "
+                    "integers, against the FP64 pipe's nominal peak; instruction issue is the limit"}
+        else:
+            roof = None
         return {"value": world * args.steps / (oms * 1e-3), "unit": "waveforms/s", "ms_per_step": oms / args.steps,
+                "roofline": roof,
                 "spa_kernel_ms": ost["spa_ns"] * 1e-6 / max(1, ost["timed_calls"]),
                 "prep_ms": ost["prep_ns"] * 1e-6 / max(1, ost["timed_calls"]),
                 "mode_bin_evals_per_s": world * mb / (oms * 1e-3),
@@ -562,6 +585,20 @@ def run_batched(args, rank, world, local, mixed):
     extra = {"mode_bin_evals_per_s": world * mb * args.steps / sec, "mode_bins_per_batch": mb,
              "waveforms_per_step": nb, "bins_per_batch": nf, "autotune": tune, "cuda_graph": True,
              "gpu_launches": plan.stats()["launches"], "clocks": clocks}
+    # the whole replay (preparation included) against the FP64 pipe: the FP64 form's 34
+    # FP64 instructions per mode-bin, the mixed form's 9; FP64X has none per mode-bin and
+    # is reported as FP64-accurate flops against the FP64 peak
+    clk_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
+    pk = FP64_PER_CLK_PER_SM * torch.cuda.get_device_properties(local).multi_processor_count * clk_hz
+    mbs = mb * args.steps / sec
+    if prec == "fp64x":
+        extra["roofline"] = {"bound": "issue", "fp64_equivalent_achieved": FP64_FLOPS_PER_MODE_BIN * mbs / 1e12,
+                             "peak": 2 * pk / 1e12, "unit": "TFLOP/s", "frac_of_fp64_peak": FP64_FLOPS_PER_MODE_BIN * mbs / (2 * pk)}
+    else:
+        ops = MIXED_FP64_OPS_PER_MODE_BIN if prec == "mixed" else FP64_OPS_PER_MODE_BIN
+        extra["roofline"] = {"bound": "fp64+alu" if prec == "mixed" else "alu", "achieved": ops * mbs / 1e12,
+                             "peak": pk / 1e12, "unit": "T FP64 inst/s", "frac": ops * mbs / pk,
+                             "note": "%d FP64 instructions per mode-bin, whole replay (preparation included)" % ops}
     if mixed:
         # speed-up over the FP64 single-waveform form on the same GPU and waveform shape
         p64 = api.Plan("fp64", max_waveforms=1, max_knots=200, max_modes_total=2000, max_bins_total=wfs[0].n_freqs)
@@ -631,12 +668,23 @@ def run_likelihood(args, rank, world, local):
                      args.steps)
     plan.sync()
     ms = max_over_ranks(ms, world)
+    mb = plan.stats()["mode_bins"]
+    # the gradient path (adjoint kernel, then the per-segment sums and the transposed spline
+    # solves) is the difference of the two timings; its FP64 work is the adjoint's
+    grad_s = max(ms - lms, 1e-6) * 1e-3 / args.steps
+    clk_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
+    pk = FP64_PER_CLK_PER_SM * torch.cuda.get_device_properties(local).multi_processor_count * clk_hz
+    ach = ADJ_FP64_OPS_PER_MODE_BIN * mb / grad_s
+    roof = {"bound": "fp64", "kernel": "k_adjoint (timed with the rest of the gradient path)", "achieved": ach / 1e12,
+            "peak": pk / 1e12, "unit": "T FP64 inst/s", "frac": ach / pk, "mode_bins": mb,
+            "note": "%d FP64 instructions per mode-bin against 2 FP64 instructions/clk/SM at the median SM clock"
+            % ADJ_FP64_OPS_PER_MODE_BIN}
     if rank == 0:
         line = base_line(args, world, "likelihood+gradient evaluations/s", world * args.steps / (ms * 1e-3),
                          "evaluations/s", ms,
                          "Whittle likelihood + knot gradient: T=1 yr, 500 modes, K=150, 1,577,880 bins, SNR 78",
-                         {"loglike_only_per_s": world * args.steps / (lms * 1e-3),
-                          "n_gradients": 4 * w.K + 2 * w.n_modes * w.K, "clocks": clocks})
+                         {"loglike_only_per_s": world * args.steps / (lms * 1e-3), "gradient_path_ms": grad_s * 1e3,
+                          "roofline": roof, "n_gradients": 4 * w.K + 2 * w.n_modes * w.K, "clocks": clocks})
         print(json.dumps(line), flush=True)
     plan.close()
 

@@ -160,6 +160,22 @@ def test_pinned_host_outputs_written_in_place(prec, window):
         plan.close()
 
 
+def test_pinned_host_outputs_batch():
+    """A batch of three waveforms (different grids) with page-locked outputs and pageable
+    inputs equals the device-pointer call bitwise."""
+    from paper_2307_12585_gb300 import api
+    from tests.gpu_util import plan_for
+    wfs = [synth.small_config(0, n_bins=3001), synth.small_config(1, n_bins=777), synth.small_config(2, n_bins=4096)]
+    plan = plan_for(wfs)
+    b = synth.concat(wfs)
+    dh, dc = plan.sum_modes(plan.upload(b))
+    nf = sum(w.n_freqs for w in wfs)
+    out = (torch.empty(nf, dtype=torch.complex128).pin_memory(), torch.empty(nf, dtype=torch.complex128).pin_memory())
+    plan.sum_modes_host(api.host_batch(b), out=out)
+    assert torch.equal(dh.cpu(), out[0]) and torch.equal(dc.cpu(), out[1])
+    plan.close()
+
+
 def test_degenerate_inputs(oracle):
     w = synth.small_config(0, n_bins=2000)
     # bins where no voice is present
