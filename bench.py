@@ -471,6 +471,7 @@ def run_paper(args, rank, world, local):
         v, cores, sample = cpu_oracle_rate(wfs[0])
         cpu = {"value": v, "unit": "waveforms/s", "cores": cores, "kind": "oracle", "sample": sample}
 
+    hbm_peak = measured_peaks().get("hbm_gbs")
     if rank == 0:
         line = base_line(args, world, "waveforms/s", value, "waveforms/s", ms, WORKLOAD, {
             "mode_bin_evals_per_s": world * mb / sec,
@@ -480,6 +481,10 @@ def run_paper(args, rank, world, local):
                           "frac": achieved / peak_tflops,
                           "traffic": TRAFFIC_FP64_SPA if args.tile_bins == 128 else None,
                           "issue_frac": issue,
+                          # the same launch against HBM: far from that roof (compute-bound)
+                          "hbm": ({"achieved_GBs": TRAFFIC_FP64_SPA / spa_s / 1e9, "peak_GBs": hbm_peak,
+                                   "frac": TRAFFIC_FP64_SPA / spa_s / 1e9 / hbm_peak}
+                                  if args.tile_bins == 128 and hbm_peak else None),
                           "note": "FP64 pipe: %d FP64 flops (%d FP64 instructions) per mode-bin; peak = %d FP64 FMA/clk/SM x 2 x SMs x median SM clock; traffic = DRAM bytes per launch from one ncu capture" % (
                               FP64_FLOPS_PER_MODE_BIN, FP64_OPS_PER_MODE_BIN, FP64_PER_CLK_PER_SM)}
                          if headline else None),
