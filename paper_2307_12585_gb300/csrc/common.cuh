@@ -279,7 +279,7 @@ struct CallShape {
 };
 
 constexpr int kLChunks = 512;      // per-waveform chunks of the likelihood's partial sums
-constexpr int kPrepKernels = 12;   // kernels launched by launch_prep (memsets excluded)
+constexpr int kPrepKernels = 11;   // kernels launched by launch_prep (memsets excluded)
 constexpr int kAdjointKernels = 8; // kernels launched by launch_adjoint
 
 // freqs_ready (optional): an event the kernels that read in.freqs must wait for

@@ -45,6 +45,7 @@ __global__ void k_validate_freqs(const WfInfo* wf, DevInputs in, int* status) {
   const WfInfo W = wf[blockIdx.y];
   int bad = 0;
   const long long* fb = reinterpret_cast<const long long*>(in.freqs) + W.fo;
+#pragma unroll 4
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < W.nf; k += (long long)gridDim.x * blockDim.x) {
     const long long u = fb[k];
     if (!(u > 0 && u < 0x7FF0000000000000LL)) bad |= ST_FREQ;
@@ -95,10 +96,8 @@ __device__ double swsh_theta_warp(int l, int m, double ch, double sh, int lane) 
 
 // one warp per mode (the Wigner-d sums are short dependent FP64 chains: spread
 // over lanes they overlap instead of running back to back in one thread)
-__global__ void k_modes(int n_wf, const WfInfo* wf, DevInputs in, int conj, ModeInfo* modes,
-                        long long nm_total, int* status) {
-  const long long j = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void modes_warp(long long j, int lane, int n_wf, const WfInfo* wf, const DevInputs& in,
+                                           int conj, ModeInfo* modes, long long nm_total, int* status) {
   if (j >= nm_total) return;
   int lo = 0, hi = n_wf - 1;     // waveform holding mode j: last w with mo <= j
   while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (wf[mid].mo <= j) lo = mid; else hi = mid - 1; }
@@ -216,8 +215,8 @@ __device__ __forceinline__ M22 m22_shfl_up(const M22& X, int o) {
 // of the reduced system, and 1/h_k.  With v_i = (N_i, D_i) = M_i v_{i-1},
 // M_i = [[0, c_i], [-a_i, b_i]], v_0 = (0, 1): c'_i = N_i / D_i and
 // m_i = b_i - a_i c'_{i-1} = D_i / D_{i-1}.
-__global__ void k_spline_factor(int n_wf, const WfInfo* wf, const double* tall, dbl4* fac, double* ih) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void factor_warp(int w, int lane, int n_wf, const WfInfo* wf, const double* tall, dbl4* fac,
+                                            double* ih) {
   if (w >= n_wf) return;
   const WfInfo W = wf[w];
   const double* t = tall + W.ko;
@@ -255,6 +254,19 @@ __global__ void k_spline_factor(int n_wf, const WfInfo* wf, const double* tall, 
     N = Nn * scl;
     D = Dn * scl;
   }
+}
+
+// one launch for the two independent first steps of the preparation: the spline
+// factorisation (first fblocks blocks, a warp per waveform) and the per-mode records
+// (a warp per mode)
+__global__ void k_modes_factor(int n_wf, const WfInfo* wf, DevInputs in, int conj, ModeInfo* modes,
+                               long long nm_total, int* status, dbl4* fac, double* ih, int fblocks) {
+  const int lane = threadIdx.x & 31;
+  if ((int)blockIdx.x < fblocks)
+    factor_warp((int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane, n_wf, wf, in.t, fac, ih);
+  else
+    modes_warp(((blockIdx.x - fblocks) * (long long)blockDim.x + threadIdx.x) >> 5, lane, n_wf, wf, in, conj, modes,
+               nm_total, status);
 }
 
 // affine map x -> p x + q; compose(g, f) = g after f
@@ -411,7 +423,7 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
   // theta0 = frac((m Phi_phi_s + n Phi_r_s - m phi)/2pi): integer combination of
   // the Q0.64 knot phases (wraps modulo one turn)
   C.theta0 = (unsigned long long)(long long)m * (Fs.q[0] - Fs.q[2]) + (unsigned long long)(long long)n * Fs.q[1];
-  C.bf = (float)C.b; C.cf = (float)C.c; C.df = (float)C.d; C.pad = 0.f;
+  C.bf = d2f_bits(C.b); C.cf = d2f_bits(C.c); C.df = d2f_bits(C.d); C.pad = 0.f;   // truncated: start values only
   core[r] = C;
   if (yk) yk[r] = 0.47746482927568600731 / h;   // 3/(2 pi h), extended SPA
 
@@ -450,7 +462,7 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
   // (margins of 1e-3 relative cover the FP32 rounding); otherwise solve exactly
   bool maybe = true;
   {
-    const float fb = (float)C.b, fc2 = (float)C.c2, fd3 = (float)C.d3;
+    const float fb = d2f_bits(C.b), fc2 = d2f_bits(C.c2), fd3 = d2f_bits(C.d3);
     const float D0 = fb, D1 = fb + fc2 + fd3;
     const float scl = fabsf(fb) + fabsf(fc2) + fabsf(fd3);
     if (D0 * D1 > 1e-3f * scl * scl) {
@@ -803,13 +815,18 @@ __global__ void k_td_amp(int n_wf, const WfInfo* wf, const ModeInfo* modes, DevI
   tdamp[2 * r + 1] = make_float4((float)cim[0], (float)cim[1], (float)cim[2], (float)cim[3]);
 }
 
+static void launch_modes_factor(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st) {
+  const int fblocks = (cs.n_wf * 32 + 255) / 256;
+  const long long mblocks = (cs.nm_total * 32 + 255) / 256;
+  k_modes_factor<<<(unsigned)(fblocks + mblocks), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes, cs.nm_total,
+                                                                s.status, s.spl_fac, s.spl_ih, fblocks);
+}
+
 void launch_prep_td(const CallShape& cs, const DevInputs& in, const DevScratch& s, float4* tdamp, cudaStream_t st) {
   dim3 gk(8, cs.n_wf);
   k_validate_knots<<<gk, 256, 0, st>>>(s.wf, in, s.status);
   k_validate_amp<<<256, 256, 0, st>>>(2 * cs.amp_total, in.amp, s.status);
-  k_modes<<<(unsigned)((cs.nm_total * 32 + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes,
-                                                                       cs.nm_total, s.status);
-  k_spline_factor<<<(cs.n_wf * 32 + 127) / 128, 128, 0, st>>>(cs.n_wf, s.wf, in.t, s.spl_fac, s.spl_ih);
+  launch_modes_factor(cs, in, s, st);
   long long nser = 4LL * cs.n_wf + 2 * cs.nm_total;
   k_spline_solve<<<(unsigned)((nser * 32 + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, s.modes, cs.nm_total, in, s.spl_fac,
                                                                  s.spl_ih, s.fundM, cs.K_total, s.ampM, s.fund);
@@ -822,9 +839,7 @@ void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, 
   dim3 gk(8, cs.n_wf);
   k_validate_knots<<<gk, 256, 0, st>>>(s.wf, in, s.status);
   k_validate_amp<<<256, 256, 0, st>>>(2 * cs.amp_total, in.amp, s.status);
-  k_modes<<<(unsigned)((cs.nm_total * 32 + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, in, cs.conj, s.modes,
-                                                                       cs.nm_total, s.status);
-  k_spline_factor<<<(cs.n_wf * 32 + 127) / 128, 128, 0, st>>>(cs.n_wf, s.wf, in.t, s.spl_fac, s.spl_ih);
+  launch_modes_factor(cs, in, s, st);
   long long nser = 4LL * cs.n_wf + 2 * cs.nm_total;
   k_spline_solve<<<(unsigned)((nser * 32 + 255) / 256), 256, 0, st>>>(cs.n_wf, s.wf, s.modes, cs.nm_total, in, s.spl_fac,
                                                                  s.spl_ih, s.fundM, cs.K_total, s.ampM, s.fund);
