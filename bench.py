@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -124,20 +125,24 @@ def oracle_setup_s(w, threads):
     return time.perf_counter() - t0
 
 
-def cpu_oracle_rate(w, budget_s=15.0):
+def cpu_oracle_rate(w, budget_s=15.0, threads=None):
     """The CPU oracle on a strided sample of the waveform's bins.  Bins are
     independent, so the per-bin part extrapolates; the per-waveform set-up is
     timed on its own and counted once.  Returns waveforms/s, threads, sample text."""
     from oracle import oracle as O
     O.build()
-    threads = O.default_threads()
+    threads = threads or O.default_threads()
     setup = oracle_setup_s(w, threads)
-    stride = 256
+    # calibration sample (large enough that the set-up's timing noise does not matter),
+    # then a sample sized to the budget
+    stride = 256 if threads > 1 else 512
     sel = w.freqs[::stride]
     t0 = time.perf_counter()
     O.sum_modes(w, freqs=sel, nthreads=threads)
     dt = time.perf_counter() - t0
-    stride = int(min(64, max(1, stride * max(dt - setup, 1e-3) / budget_s)))
+    per_bin = max(dt - setup, 1e-3) / sel.shape[0]
+    target = max(1.0, (budget_s - setup) / per_bin)
+    stride = int(min(1024, max(1, math.ceil(w.n_freqs / target))))
     sel = w.freqs[::stride]
     t0 = time.perf_counter()
     O.sum_modes(w, freqs=sel, nthreads=threads)
@@ -470,6 +475,8 @@ def run_paper(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, sample = cpu_oracle_rate(wfs[0])
         cpu = {"value": v, "unit": "waveforms/s", "cores": cores, "kind": "oracle", "sample": sample}
+        v1, _, sample1 = cpu_oracle_rate(wfs[0], budget_s=6.0, threads=1)
+        cpu["one_core"] = {"value": v1, "cores": 1, "sample": sample1}
 
     hbm_peak = measured_peaks().get("hbm_gbs")
     if rank == 0:
