@@ -25,7 +25,10 @@ namespace emrifd {
 
 constexpr int kWarps = 8;                 // warps per CTA of the hot kernel
 constexpr int kThreads = 32 * kWarps;
-constexpr int kTabBits = 12;              // FP32-pair table e^{2 pi i k / 4096} (FP64X form)
+#ifndef EMRI_FD_TABFF_BITS
+#define EMRI_FD_TABFF_BITS 16
+#endif
+constexpr int kTabBits = EMRI_FD_TABFF_BITS;   // FP32-pair table e^{2 pi i k / 2^kTabBits} (FP64X form)
 constexpr int kTabN = 1 << kTabBits;
 constexpr int kTab64Bits = 16;            // FP64 table e^{2 pi i k / 65536} (FP64 form, adjoint)
 constexpr int kTab64N = 1 << kTab64Bits;

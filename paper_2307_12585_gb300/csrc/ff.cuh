@@ -44,6 +44,14 @@ __device__ __forceinline__ ff ff_add(ff x, ff y) {
 
 __device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
 
+// running sum acc += y without renormalising: the high words by TwoSum, their error and
+// the low words added into acc.lo (renormalise with fast_two_sum before other use);
+// |acc.lo| stays a few hundred ulps of acc.hi over the few hundred terms of a tile
+__device__ __forceinline__ ff ff_acc(ff acc, ff y) {
+  const ff s = two_sum(acc.hi, y.hi);
+  return ff_make(s.hi, __fadd_rn(acc.lo, __fadd_rn(s.lo, y.lo)));
+}
+
 // ff + float
 __device__ __forceinline__ ff ff_add_f(ff x, float y) {
   const ff s = two_sum(x.hi, y);

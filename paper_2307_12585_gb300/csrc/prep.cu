@@ -779,6 +779,7 @@ namespace {
 __global__ void k_table_ff(const double2* tab, float4* tabf) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= kTabN) return;
+  static_assert(kTabBits <= kTab64Bits, "the FP32-pair table samples the FP64 table");
   const double2 e = tab[(long long)k << (kTab64Bits - kTabBits)];   // e^{2 pi i k / kTabN}
   const ff c = ff_from_double(e.x), s = ff_from_double(e.y);
   tabf[k] = make_float4(c.hi, c.lo, s.hi, s.lo);

@@ -143,9 +143,12 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
     if (m0 == 0.0) return false;
     wgt = ff_from_double(m0);
   } else {
+    // one Newton step y0 (1 + e/2), e = 1 - |D| y0^2 (|e| ~ 1e-7): y0^2 exactly as a pair,
+    // the leading product of e by an FMA, its small cross terms in FP32
     const float y0 = rsqrtf(Da.hi);
-    const ff ee = ff_mul_f(ff_mul_f(Da, y0), y0);
-    wgt = ff_mul_f(ff_add_f(ff_mul_f(ee, -0.5f), 1.5f), y0);
+    const ff t2 = two_prod(y0, y0);
+    const float e = __fsub_rn(__fmaf_rn(-Da.hi, t2.hi, 1.f), __fmaf_rn(Da.hi, t2.lo, __fmul_rn(Da.lo, t2.hi)));
+    wgt = fast_two_sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), e));
   }
   // a7: phase, Q0.64 turns
   const ff dh = ff_mul(dl, ff_make(X.h[0], X.h[1]));
@@ -155,18 +158,29 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
   const unsigned long long ft = q64_mul(f, C.ts);           // f t_s; the branch sign is applied here
   unsigned long long Th = (neg ? 0ull - ft : ft) - C.theta0 + q64_of_float(inseg.hi) + q64_of_float(inseg.lo);
   if (!coal) Th += pos ? (0ull - (1ull << 61)) : (1ull << 61);
-  // e^{2 pi i Th/2^64}: table entry times (1 - x^2/2) + i (x - x^3/6), |x| <= pi/4096
+  // e^{2 pi i Th/2^64}: table entry times (1 - x^2/2) + i x (and - i x^3/6 with the
+  // coarse table), |x| <= pi/2^kTabBits
   const unsigned long long kq = (Th + (1ull << (63 - kTabBits))) >> (64 - kTabBits);
   const long long rr = (long long)(Th - (kq << (64 - kTabBits))) >> 8;   // units of 2^-56 turn
   const ff xt = two_sum(small_int_to_float((int)(rr >> 22)) * 5.820766091346741e-11f,        // 2^-34
                         small_int_to_float((int)(rr & 0x3FFFFF)) * 1.3877787807814457e-17f);  // 2^-56
   const ff xr = ff_mul(xt, ff_make(6.2831854820251465f, -1.7484555314695172e-07f));
   const float qx = 0.5f * xr.hi * xr.hi;
-  const ff sx = ff_add_f(xr, -xr.hi * xr.hi * xr.hi * (1.f / 6.f));
   const float4 T = __ldg(tabf + (kq & (kTabN - 1)));
   const ff Tc = ff_make(T.x, T.y), Ts = ff_make(T.z, T.w);
-  const ff er = ff_add_f(ff_sub(Tc, ff_mul(Ts, sx)), -T.x * qx);
-  const ff ei = ff_add_f(ff_add(Ts, ff_mul(Tc, sx)), -T.z * qx);
+  ff er, ei;
+  if constexpr (kTabBits >= 16) {
+    // |x| <= 4.8e-5: x^3/6 < 2e-14 is dropped; x^2/2 < 1.2e-9 times the entry lies below
+    // the pair's low word and is added into it
+    er = ff_sub(Tc, ff_mul(Ts, xr));
+    ei = ff_add(Ts, ff_mul(Tc, xr));
+    er.lo = __fmaf_rn(-T.x, qx, er.lo);
+    ei.lo = __fmaf_rn(-T.z, qx, ei.lo);
+  } else {
+    const ff sx = ff_add_f(xr, -xr.hi * xr.hi * xr.hi * (1.f / 6.f));
+    er = ff_add_f(ff_sub(Tc, ff_mul(Ts, sx)), -T.x * qx);
+    ei = ff_add_f(ff_add(Ts, ff_mul(Tc, sx)), -T.z * qx);
+  }
   // a9-a10
   ff ar = ff_make(X.are[3][0], X.are[3][1]), ai = ff_make(X.aim[3][0], X.aim[3][1]);
 #pragma unroll
@@ -523,7 +537,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
               if (qq != q) continue;
               if constexpr (PREC == 2) {
 #pragma unroll
-                for (int c = 0; c < 4; c++) accx[qq][c] = ff_add(accx[qq][c], ff_make(v[2 * c], v[2 * c + 1]));
+                for (int c = 0; c < 4; c++) accx[qq][c] = ff_acc(accx[qq][c], ff_make(v[2 * c], v[2 * c + 1]));
               } else {
 #pragma unroll
                 for (int c = 0; c < 4; c++) {   // Kahan-compensated accumulation
@@ -571,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
       for (int q = 0; q < BPL; q++)
 #pragma unroll
         for (int c = 0; c < 4; c++) {
-          const ff v = PREC == 2 ? accx[q][c] : fast_two_sum(accf[q][c], -cmp[q][c]);
+          const ff v = PREC == 2 ? fast_two_sum(accx[q][c].hi, accx[q][c].lo) : fast_two_sum(accf[q][c], -cmp[q][c]);
           redf[warp][lane + 32 * q][c] = make_float2(v.hi, v.lo);
         }
     }
