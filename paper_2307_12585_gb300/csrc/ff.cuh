@@ -74,9 +74,6 @@ __device__ __forceinline__ ff ff_mul_f(ff x, float y) {
   return fast_two_sum(p, e);
 }
 
-// x * y + z
-__device__ __forceinline__ ff ff_fma(ff x, ff y, ff z) { return ff_add(ff_mul(x, y), z); }
-
 // ff from a double (prep time only: uses the FP64 pipe)
 __device__ __forceinline__ ff ff_from_double(double x) {
   const float hi = __double2float_rn(x);

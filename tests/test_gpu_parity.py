@@ -176,6 +176,37 @@ def test_pinned_host_outputs_batch():
     plan.close()
 
 
+def test_host_inputs_device_outputs_back_to_back():
+    """Page-locked host inputs (the frequency grid staged on the side stream) with device
+    outputs, two calls in a row without a sync in between and with different grids:
+    each equals its device-input result bitwise (the second staging waits for the
+    first call's readers)."""
+    from paper_2307_12585_gb300 import api
+    from tests.gpu_util import plan_for
+    w1 = synth.small_config(0, n_bins=6000)
+    w2 = synth.small_config(1, n_bins=6000).with_freqs(np.linspace(2e-4, 1.5e-2, 6000))
+    plan = plan_for([w1])
+    refs = []
+    for w in (w1, w2):
+        hp, hc = plan.sum_modes(plan.upload(synth.concat([w])))
+        refs.append((hp.cpu(), hc.cpu()))
+    hbs = []
+    for w in (w1, w2):
+        hb = api.host_batch(synth.concat([w]))
+        for k in list(hb):
+            if isinstance(hb[k], np.ndarray) and k not in ("knot_off", "mode_off", "freq_off"):
+                hb[k] = torch.from_numpy(hb[k]).pin_memory()
+        hbs.append(hb)
+    outs = [(torch.empty(6000, dtype=torch.complex128, device="cuda"), torch.empty(6000, dtype=torch.complex128, device="cuda"))
+            for _ in range(2)]
+    for i in range(2):
+        plan.sum_modes(hbs[i], out=outs[i], check=False)
+    plan.sync()
+    for i in range(2):
+        assert torch.equal(outs[i][0].cpu(), refs[i][0]) and torch.equal(outs[i][1].cpu(), refs[i][1])
+    plan.close()
+
+
 def test_degenerate_inputs(oracle):
     w = synth.small_config(0, n_bins=2000)
     # bins where no voice is present
