@@ -225,6 +225,27 @@ def test_degenerate_inputs(oracle):
     _cmp(run(t4), oracle.sum_modes(t4), TOL64)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp64x", "mixed"])
+def test_batch_with_empty_members(prec):
+    """A batch whose members include a waveform with no bins and one with no modes, between
+    ordinary ones: every member equals its single-waveform call bitwise, the no-mode member
+    is zero, and the zero-bin member takes no output."""
+    a = synth.small_config(0, n_bins=3001)
+    nob = synth.small_config(1, n_bins=5).with_freqs(np.zeros(0))
+    nom = synth.small_config(2, n_bins=777).with_modes(np.zeros(0, np.int64))
+    b = synth.small_config(3, n_bins=4096)
+    wfs = [a, nob, nom, b]
+    hp, hc = run(wfs, precision=prec)
+    off = np.concatenate([[0], np.cumsum([w.n_freqs for w in wfs])])
+    assert hp.shape[0] == off[-1]
+    for i, w in enumerate(wfs):
+        if w.n_freqs == 0:
+            continue
+        sp, sc = run(w, precision=prec)
+        assert np.array_equal(hp[off[i]:off[i + 1]], sp) and np.array_equal(hc[off[i]:off[i + 1]], sc)
+    assert np.all(hp[off[2]:off[3]] == 0) and np.all(hc[off[2]:off[3]] == 0)
+
+
 def test_mixed_precision_small(oracle):
     w = synth.small_config(0)
     _cmp(run(w, precision="mixed"), oracle.sum_modes(w), TOL32)
