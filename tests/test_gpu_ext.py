@@ -62,7 +62,7 @@ def test_paper_dense_sampled(oracle, prec):
     """Full 3,155,760-bin grid on the GPU; 3000 sampled bins (2000 of them where
     some voice contributes) through the oracle."""
     w = synth.paper_config(3)
-    hp, hc = run(w, precision=prec, spa="extended")
+    hp, hc = run(w, precision=prec, spa="extended", tile_bins={"fp64": 128, "fp64x": 64}[prec])   # the bench's tiles
     rng = np.random.default_rng(7)
     occ = np.nonzero(np.abs(hp) > 0)[0]
     sel = np.unique(np.concatenate([rng.choice(w.n_freqs, 1000, replace=False), rng.choice(occ, 2000, replace=False)]))

@@ -34,6 +34,7 @@ def _cmp(got, ref, tol):
 
 
 PRECS = ["fp64", "fp64x"]   # both must meet the FP64 tolerance
+BENCH_TILE = {"fp64": 128, "fp64x": 64, "mixed": 64}   # the tile sizes bench.py times each form at
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -109,7 +110,7 @@ def test_paper_config_sampled(oracle, seed, prec):
     """Full-size 2 yr waveform (2000 modes, 3,155,760 bins) in the bench's launch
     configuration; the oracle evaluates ~4000 sampled bins (bins are independent)."""
     w = synth.paper_config(seed)
-    hp, hc = run(w, precision=prec)
+    hp, hc = run(w, precision=prec, tile_bins=BENCH_TILE[prec])
     rng = np.random.default_rng(seed)
     occupied = np.nonzero(np.abs(hp) > 0)[0]
     sel = np.unique(np.concatenate([rng.choice(w.n_freqs, 1000, replace=False),
@@ -253,7 +254,7 @@ def test_mixed_precision_small(oracle):
 
 def test_mixed_precision_paper_sampled(oracle):
     w = synth.paper_config(4)
-    hp, hc = run(w, precision="mixed")
+    hp, hc = run(w, precision="mixed", tile_bins=BENCH_TILE["mixed"])
     rng = np.random.default_rng(4)
     occupied = np.nonzero(np.abs(hp) > 0)[0]
     sel = np.unique(rng.choice(occupied, 3000, replace=False))
