@@ -110,7 +110,7 @@ struct AdjParams {
   const dbl4* G;
   const int* item_off;     // exclusive scan of items per run, total at [run_cap]
   long long run_cap;
-  const double2* tab;
+  const double2* tab;      // e^{2 pi i k/65536}
   double* slots;           // [3 * seg_total][16]
   const int* status;
 };

@@ -75,7 +75,7 @@ bool on_device(const void* p) {
 }
 
 // once per device, with that device current: the scratch's device address and
-// the e^{2 pi i k/4096} table the output kernel reads
+// the e^{2 pi i k/65536} table the output kernel reads
 emri_fd_status setup(int dev, cudaStream_t st, unsigned char** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (g_dev_ptr[dev]) { *out = g_dev_ptr[dev]; return EMRI_FD_OK; }

@@ -52,7 +52,7 @@ struct SpaParams {
   const double* freqs;
   void* hp;
   void* hc;
-  const double2* tab;
+  const double2* tab;      // e^{2 pi i k/65536}
   const float4* tabf;
   const double* prefactor;
   const double* yk;                 // [segments] 3/(2 pi h), extended plans
