@@ -304,17 +304,21 @@ def paper_aux(args, w, fd_ms_per_wf):
                                   "FP64 rate (12 FP64 operations per bin), not HBM; peak = measured copy bandwidth"}
     # the same waveform on a sparse grid of 1e4 log-spaced bins (the paper's downsampled FD, Sec. 3.3)
     ws = synth.paper_config(1, grid="sparse")
-    best = None
-    for tb in (32, 64, 128):      # few bins: the tile size sets how many SMs take part
+    best, unsplit = None, None
+    # few bins: the tile size, and how many CTAs (a cluster) share a tile, set how many SMs take part
+    for tb, split in ((32, 1), (64, 1), (128, 1), (32, 2), (32, 4), (64, 2), (64, 4)):
         plan = api.Plan("fp64", max_waveforms=1, max_knots=ws.K, max_modes_total=ws.n_modes,
-                        max_bins_total=ws.n_freqs, tile_bins=tb)
+                        max_bins_total=ws.n_freqs, tile_bins=tb, tile_split=split)
         b = plan.upload(synth.concat([ws]))
         o = plan.sum_modes(b)
         t = timed(plan.stream, lambda: plan.sum_modes(b, out=o, check=False), reps)
         plan.close()
         if best is None or t < best[0]:
-            best = (t, tb)
-    out["sparse_grid"] = {"bins": ws.n_freqs, "fp64_ms": best[0], "tile_bins": best[1]}
+            best = (t, tb, split)
+        if split == 1 and (unsplit is None or t < unsplit):
+            unsplit = t
+    out["sparse_grid"] = {"bins": ws.n_freqs, "fp64_ms": best[0], "tile_bins": best[1], "tile_split": best[2],
+                          "fp64_ms_unsplit": unsplit}
     # mode selection on the full pool
     pool = synth.paper_config(1, n_modes=3294, grid="sparse", n_sparse=16)
     plan = api.Plan("fp64", max_waveforms=1, max_knots=pool.K, max_modes_total=pool.n_modes, max_bins_total=16)

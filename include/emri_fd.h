@@ -135,7 +135,13 @@ typedef struct {
   int time_domain;          /* 1: also allocate the scratch of the time-domain comparator
                                (emri_fd_td_sum, emri_fd_td_spectrum); 0: those return
                                EMRI_FD_ERR_ARG */
-  int reserved[3];          /* must be zero */
+  int tile_split;           /* CTAs sharing each output tile: 0 or 1 = one CTA per tile;
+                               2 or 4 = the tile's branch list split over a thread-block
+                               cluster of that many CTAs, whose partial sums are combined
+                               in rank order through distributed shared memory.  For grids
+                               with few tiles (sparse grids); tile_bins must be 32 or 64.
+                               The summation grouping, hence the last bits, depend on it. */
+  int reserved[2];          /* must be zero */
 } emri_fd_desc;
 
 /*
@@ -332,8 +338,15 @@ emri_fd_status emri_fd_sum_modes_noalloc(int conj_partners, long long n_knots, l
 /*
  * Change the output-tile width of a plan (32, 64 or 128 bins) for later calls.
  * Results may change in the last bits (the in-tile summation grouping changes).
+ * EMRI_FD_ERR_ARG for 128 while the plan's tile split is above 1.
  */
 emri_fd_status emri_fd_set_tile(emri_fd_plan_t plan, int tile_bins);
+
+/*
+ * Change the tile split (see emri_fd_desc.tile_split: 0, 1, 2 or 4) for later calls.
+ * EMRI_FD_ERR_ARG for other values, or for a split above 1 with 128-bin tiles.
+ */
+emri_fd_status emri_fd_set_tile_split(emri_fd_plan_t plan, int tile_split);
 
 /*
  * CUDA-graph capture of one emri_fd_sum_modes call (batches included): the

@@ -20,7 +20,7 @@ STATUS = {0: "EMRI_FD_OK", 1: "EMRI_FD_ERR_ARG", 2: "EMRI_FD_ERR_KNOTS", 3: "EMR
           7: "EMRI_FD_ERR_CUDA", 8: "EMRI_FD_ERR_OOM", 9: "EMRI_FD_ERR_TIMEOUT"}
 EXPORTS = ("emri_fd_plan", "emri_fd_sum_modes", "emri_fd_loglike_and_grad", "emri_fd_sync", "emri_fd_stats",
            "emri_fd_profile", "emri_fd_plan_destroy", "emri_fd_strerror", "emri_fd_sum_modes_noalloc",
-           "emri_fd_set_tile", "emri_fd_capture", "emri_fd_replay", "emri_fd_graph_destroy",
+           "emri_fd_set_tile", "emri_fd_set_tile_split", "emri_fd_capture", "emri_fd_replay", "emri_fd_graph_destroy",
            "emri_fd_select_modes", "emri_fd_td_sum", "emri_fd_td_spectrum")
 
 
@@ -34,7 +34,8 @@ class emri_fd_desc(C.Structure):
     _fields_ = [("precision", C.c_int), ("conj_partners", C.c_int), ("max_waveforms", C.c_int),
                 ("max_knots", C.c_int), ("max_knots_total", C.c_longlong), ("max_modes_total", C.c_longlong),
                 ("max_bins_total", C.c_longlong), ("tile_bins", C.c_int), ("likelihood", C.c_int),
-                ("spa_form", C.c_int), ("window", C.c_int), ("time_domain", C.c_int), ("reserved", C.c_int * 3)]
+                ("spa_form", C.c_int), ("window", C.c_int), ("time_domain", C.c_int), ("tile_split", C.c_int),
+                ("reserved", C.c_int * 2)]
 
 SPA_FORMS = {"standard": 0, "extended": 1}
 WINDOWS = {None: 0, "none": 0, "hann": 1}
@@ -71,6 +72,8 @@ def lib():
         L.emri_fd_select_modes.restype = C.c_int
         L.emri_fd_set_tile.argtypes = [vp, C.c_int]
         L.emri_fd_set_tile.restype = C.c_int
+        L.emri_fd_set_tile_split.argtypes = [vp, C.c_int]
+        L.emri_fd_set_tile_split.restype = C.c_int
         L.emri_fd_capture.argtypes = [vp, C.c_int, vp, vp, vp] + [dp] * 5 + [ip] * 3 + [dp] * 5 + [vp, vp,
                                                                                           C.POINTER(C.c_void_p)]
         L.emri_fd_capture.restype = C.c_int
@@ -146,6 +149,10 @@ def emri_fd_sum_modes_noalloc(conj_partners, n_knots, n_modes, n_freqs, t, phi_p
 
 def emri_fd_set_tile(plan, tile_bins) -> int:
     return lib().emri_fd_set_tile(C.c_void_p(plan), int(tile_bins))
+
+
+def emri_fd_set_tile_split(plan, tile_split) -> int:
+    return lib().emri_fd_set_tile_split(C.c_void_p(plan), int(tile_split))
 
 
 def emri_fd_capture(plan, n_waveforms, knot_off, mode_off, freq_off, t, phi_phi, phi_r, omega_phi, omega_r,
@@ -230,11 +237,14 @@ class Plan:
     precision: "fp64" or "fp64x" (complex128 outputs) or "mixed" (complex64 outputs).
     spa: "standard" (Fresnel integral per root) or "extended" (Eq. 10 per root).
     window: None or "hann" (the window's three-term convolution on a uniform grid).
+    tile_split: 0/1, 2 or 4 CTAs (a thread-block cluster) per output tile (32- or 64-bin
+    tiles; for grids with few tiles).
     Batches are dicts in the layout of synth.concat (numpy or torch)."""
 
     def __init__(self, precision="fp64", conj_partners=True, max_waveforms=1, max_knots=200,
                  max_modes_total=4096, max_bins_total=1 << 22, max_knots_total=0, tile_bins=0,
-                 likelihood=False, device=None, stream=None, spa="standard", window=None, time_domain=False):
+                 likelihood=False, device=None, stream=None, spa="standard", window=None, time_domain=False,
+                 tile_split=0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -253,6 +263,7 @@ class Plan:
         d.spa_form = SPA_FORMS[spa]
         d.window = WINDOWS[window]
         d.time_domain = int(bool(time_domain))
+        d.tile_split = int(tile_split)
         self.spa = spa
         self.window = window
         self.desc = d
@@ -415,6 +426,9 @@ class Plan:
 
     def set_tile(self, tile_bins):
         _check(emri_fd_set_tile(self.handle, tile_bins), "emri_fd_set_tile")
+
+    def set_tile_split(self, tile_split):
+        _check(emri_fd_set_tile_split(self.handle, tile_split), "emri_fd_set_tile_split")
 
     def capture(self, b, out):
         """Capture emri_fd_sum_modes(b) -> out into a CUDA graph; returns a Graph."""

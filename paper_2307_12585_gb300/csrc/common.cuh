@@ -275,6 +275,7 @@ struct CallShape {
   long long K_total, nm_total, nf_total, seg_total, tiles_total, amp_total;
   int max_K;
   int tile_bins;
+  int tile_split;   // CTAs (a thread-block cluster) sharing each tile: 1, 2 or 4
   int conj;
   int precision;
   int ext;          // 1: extended SPA (Eq. 10)

@@ -130,7 +130,9 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
       d->max_bins_total > 2000000000LL || d->max_knots_total < 0 ||
       !(d->tile_bins == 0 || d->tile_bins == 32 || d->tile_bins == 64 || d->tile_bins == 128))
     return EMRI_FD_ERR_ARG;
-  for (int i = 0; i < 3; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
+  for (int i = 0; i < 2; i++) if (d->reserved[i] != 0) return EMRI_FD_ERR_ARG;
+  if (!(d->tile_split == 0 || d->tile_split == 1 || d->tile_split == 2 || d->tile_split == 4)) return EMRI_FD_ERR_ARG;
+  if (d->tile_split > 1 && !(d->tile_bins == 32 || d->tile_bins == 64)) return EMRI_FD_ERR_ARG;
   if (d->time_domain != 0 && d->time_domain != 1) return EMRI_FD_ERR_ARG;
   if (d->window != EMRI_FD_WINDOW_NONE && d->window != EMRI_FD_WINDOW_HANN) return EMRI_FD_ERR_ARG;
   if (d->window != EMRI_FD_WINDOW_NONE && d->likelihood) return EMRI_FD_ERR_ARG;
@@ -245,6 +247,7 @@ emri_fd_status prepare_call(emri_fd_plan_s* p, int n_wf, const long long* knot_o
   cs = CallShape{};
   cs.n_wf = n_wf;
   cs.tile_bins = TB;
+  cs.tile_split = p->desc.tile_split > 1 ? p->desc.tile_split : 1;
   cs.conj = p->desc.conj_partners;
   cs.precision = p->desc.precision;
   cs.ext = p->desc.spa_form;
@@ -775,7 +778,15 @@ struct emri_fd_graph_s {
 
 emri_fd_status emri_fd_set_tile(emri_fd_plan_t p, int tile_bins) {
   if (!p || !(tile_bins == 32 || tile_bins == 64 || tile_bins == 128)) return EMRI_FD_ERR_ARG;
+  if (tile_bins == 128 && p->desc.tile_split > 1) return EMRI_FD_ERR_ARG;
   p->desc.tile_bins = tile_bins;
+  return EMRI_FD_OK;
+}
+
+emri_fd_status emri_fd_set_tile_split(emri_fd_plan_t p, int tile_split) {
+  if (!p || !(tile_split == 0 || tile_split == 1 || tile_split == 2 || tile_split == 4)) return EMRI_FD_ERR_ARG;
+  if (tile_split > 1 && p->desc.tile_bins == 128) return EMRI_FD_ERR_ARG;
+  p->desc.tile_split = tile_split;
   return EMRI_FD_OK;
 }
 

@@ -25,6 +25,7 @@
 #include "spa_math.cuh"
 #include "ff.cuh"
 #include "ext_spa.cuh"
+#include <cooperative_groups.h>
 
 namespace emrifd {
 namespace {
@@ -66,6 +67,7 @@ struct Smem {
   int list[kListCap];
   int wsum[kWarps + 1];
   long long tile;
+  int anyv[4];     // cluster members' "has entries" flags (tile split)
   float2 pf;       // the waveform's prefactor as an FP32 pair (FP64X)
   double red[kWarps][32 * BPL][4];   // FP64 partials, or FP32-pair partials in the same bytes
 };
@@ -309,14 +311,45 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
 #define EMRI_FD_SPA64_MINB 3
 #endif
 
+// store one bin of the FP32-pair forms: FP64X applies mu/d_L (an FP32 pair) and writes
+// doubles; the mixed form writes floats
+template <int PREC>
+__device__ __forceinline__ void store_bin(const SpaParams& P, float2 pf2, long long bin, const ff (&v)[4]) {
+  if constexpr (PREC == 2) {
+    const ff pf = ff_make(pf2.x, pf2.y);
+    double o[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const ff r = ff_mul(v[c], pf);
+      o[c] = f2d_bits(r.hi) + f2d_bits(r.lo);
+    }
+    reinterpret_cast<double2*>(P.hp)[bin] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2*>(P.hc)[bin] = make_double2(o[2], o[3]);
+  } else {
+    reinterpret_cast<float2*>(P.hp)[bin] = make_float2(v[0].hi + v[0].lo, v[1].hi + v[1].lo);
+    reinterpret_cast<float2*>(P.hc)[bin] = make_float2(v[2].hi + v[2].lo, v[3].hi + v[3].lo);
+  }
+}
+
 constexpr int kBackPerFront = 8;   // back-of-queue (empty) tiles a CTA may take after each front tile
 
-template <int BPL, int PREC, bool EXT>
+// CL > 1: a thread-block cluster of CL CTAs shares each tile.  Rank 0 takes the tile
+// and writes it into every member's shared memory; member r scans every CL-th chunk of
+// kRpt runs (chunk index = r mod CL), evaluates the entries it found and sums its warps'
+// partials; the members' "has entries" flags are exchanged; after a cluster barrier,
+// member r sums bins i = r (mod CL) over the members' partials in rank order
+// (distributed shared memory) and stores them.  The order of every sum is fixed, so
+// results do not depend on scheduling.  Every cluster barrier is reached by all threads
+// of all members the same number of times: the tile and the exchanged flags are the
+// same for all members.
+template <int BPL, int PREC, bool EXT, int CL>
 __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64_MINB) : EMRI_FD_SPA_MINB) k_spa(SpaParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<BPL, PREC>& S = *reinterpret_cast<Smem<BPL, PREC>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int TB = 32 * BPL;
+  static_assert(CL == 1 || CL == 2 || CL == 4, "cluster of 1, 2 or 4 CTAs");
+  const int crank = CL > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
   if (*P.status != 0) return;
 
   // Two-ended tile queue in one 64-bit counter: the low word counts tiles taken from the
@@ -329,17 +362,24 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
   bool prev_back = false, prev_any = true;    // thread 0: how the previous tile was taken / had entries
   bool started = false;                       // thread 0: a tile has been taken
   for (;;) {
-    if (tid == 0) {
+    if (tid == 0 && crank == 0) {
       back = !started ? 0 : (prev_back ? (prev_any ? 0 : back - 1) : kBackPerFront);
       started = true;
       const bool fb = back > 0;
       const unsigned long long old = atomicAdd(&P.counters[0], fb ? (1ull << 32) : 1ull);
       const long long a = (long long)(old & 0xFFFFFFFFull), b = (long long)(old >> 32);
-      S.tile = a + b < P.tiles_total ? (fb ? P.tiles_total - 1 - b : a) : -1;
+      const long long tv = a + b < P.tiles_total ? (fb ? P.tiles_total - 1 - b : a) : -1;
+      if constexpr (CL > 1) {
+        cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+        for (int r = 0; r < CL; r++) *cl.map_shared_rank(&S.tile, r) = tv;
+      } else {
+        S.tile = tv;
+      }
       prev_back = fb;
     }
-    __syncthreads();
-    const long long tile = S.tile;
+    if constexpr (CL > 1) cooperative_groups::this_cluster().sync();
+    else __syncthreads();
+    const long long tile = S.tile;   // every member reads its own copy
     if (tile < 0) break;
     int lo = 0, hi = P.n_wf - 1;
     while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (P.wf[mid].tile_base <= tile) lo = mid; else hi = mid - 1; }
@@ -380,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
       // kRpt * kThreads runs), so the list order is the run order as before
       int cnt = 0;
       while (rcur < nruns && cnt + 2 * kRpt * kThreads <= kListCap) {
-        const long long rb = rcur + (long long)tid * kRpt;
+        const long long rb = rcur + ((long long)tid * CL + crank) * kRpt;
         unsigned flags = 0u;   // bit 2k: run rb + k covers the tile for +f, bit 2k + 1: for -f
 #pragma unroll
         for (int k = 0; k < kRpt; k++) {
@@ -414,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
         }
         cnt += total;
         any |= total > 0;
-        rcur += (long long)kRpt * kThreads;
+        rcur += (long long)kRpt * kThreads * CL;
         __syncthreads();
       }
       if (rcur == 0) rcur = 1;   // no runs at all: leave the loop after this pass
@@ -555,12 +595,23 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
       if (rcur >= nruns) break;
     }
 
+    if constexpr (CL > 1) {
+      // the cluster has entries if any member has: every member gets every flag (this
+      // barrier also orders rank 0's next tile broadcast after every member's read)
+      cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+      if (tid == 0)
+        for (int r = 0; r < CL; r++) *cl.map_shared_rank(&S.anyv[crank], r) = any ? 1 : 0;
+      cl.sync();
+      any = false;
+#pragma unroll
+      for (int r = 0; r < CL; r++) any |= S.anyv[r] != 0;
+    }
     if (tid == 0) prev_any = any;
     // ---- a tile without entries is written as zeros, without the reduction
     if (!any) {
       for (int i = tid; i < TB; i += kThreads) {
         const long long bin = bin0 + i;
-        if (bin >= binEnd) continue;
+        if (bin >= binEnd || i % CL != crank) continue;
         if constexpr (PREC == 1) {
           reinterpret_cast<float2*>(P.hp)[bin] = make_float2(0.f, 0.f);
           reinterpret_cast<float2*>(P.hc)[bin] = make_float2(0.f, 0.f);
@@ -569,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
           reinterpret_cast<double2*>(P.hc)[bin] = make_double2(0.0, 0.0);
         }
       }
-      continue;   // the loop's closing barrier above separates this tile from the next
+      continue;   // the loop's closing barrier above (and, for CL > 1, the flag exchange) separates the tiles
     }
     // ---- fixed-order reduction over warps, one store per bin (FP64 sums for the
     // FP64 form; FP32 pairs for the other two, so that they spend no FP64
@@ -594,72 +645,146 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
       S.pf = make_float2(pf.hi, pf.lo);
     }
     __syncthreads();
-    for (int i = tid; i < TB; i += kThreads) {
-      const long long bin = bin0 + i;
-      if (bin >= binEnd) continue;
-      if constexpr (PREC == 0) {
-        double v[4] = {S.red[0][i][0], S.red[0][i][1], S.red[0][i][2], S.red[0][i][3]};
-        for (int w2 = 1; w2 < kWarps; w2++)
+    if constexpr (CL == 1) {
+      for (int i = tid; i < TB; i += kThreads) {
+        const long long bin = bin0 + i;
+        if (bin >= binEnd) continue;
+        if constexpr (PREC == 0) {
+          double v[4] = {S.red[0][i][0], S.red[0][i][1], S.red[0][i][2], S.red[0][i][3]};
+          for (int w2 = 1; w2 < kWarps; w2++)
 #pragma unroll
-          for (int c = 0; c < 4; c++) v[c] += S.red[w2][i][c];
-        reinterpret_cast<double2*>(P.hp)[bin] = make_double2(v[0], v[1]);
-        reinterpret_cast<double2*>(P.hc)[bin] = make_double2(v[2], v[3]);
-      } else {
-        const float2(&redf)[kWarps][32 * BPL][4] =
-            *reinterpret_cast<const float2(*)[kWarps][32 * BPL][4]>(&S.red[0][0][0]);
-        ff v[4];
-#pragma unroll
-        for (int c = 0; c < 4; c++) v[c] = ff_make(0.f, 0.f);
-        for (int w2 = 0; w2 < kWarps; w2++)
-#pragma unroll
-          for (int c = 0; c < 4; c++) v[c] = ff_add(v[c], ff_make(redf[w2][i][c].x, redf[w2][i][c].y));
-        if constexpr (PREC == 2) {
-          const ff pf = ff_make(S.pf.x, S.pf.y);
-          double o[4];
-#pragma unroll
-          for (int c = 0; c < 4; c++) {
-            const ff r = ff_mul(v[c], pf);
-            o[c] = f2d_bits(r.hi) + f2d_bits(r.lo);
-          }
-          reinterpret_cast<double2*>(P.hp)[bin] = make_double2(o[0], o[1]);
-          reinterpret_cast<double2*>(P.hc)[bin] = make_double2(o[2], o[3]);
+            for (int c = 0; c < 4; c++) v[c] += S.red[w2][i][c];
+          reinterpret_cast<double2*>(P.hp)[bin] = make_double2(v[0], v[1]);
+          reinterpret_cast<double2*>(P.hc)[bin] = make_double2(v[2], v[3]);
         } else {
-          reinterpret_cast<float2*>(P.hp)[bin] = make_float2(v[0].hi + v[0].lo, v[1].hi + v[1].lo);
-          reinterpret_cast<float2*>(P.hc)[bin] = make_float2(v[2].hi + v[2].lo, v[3].hi + v[3].lo);
+          const float2(&redf)[kWarps][32 * BPL][4] =
+              *reinterpret_cast<const float2(*)[kWarps][32 * BPL][4]>(&S.red[0][0][0]);
+          ff v[4];
+#pragma unroll
+          for (int c = 0; c < 4; c++) v[c] = ff_make(0.f, 0.f);
+          for (int w2 = 0; w2 < kWarps; w2++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) v[c] = ff_add(v[c], ff_make(redf[w2][i][c].x, redf[w2][i][c].y));
+          store_bin<PREC>(P, S.pf, bin, v);
         }
       }
+      __syncthreads();
+    } else {
+      // this member's partial of each bin, in warp order, into warp 0's slot
+      for (int i = tid; i < TB; i += kThreads) {
+        if constexpr (PREC == 0) {
+          double v[4] = {S.red[0][i][0], S.red[0][i][1], S.red[0][i][2], S.red[0][i][3]};
+          for (int w2 = 1; w2 < kWarps; w2++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) v[c] += S.red[w2][i][c];
+#pragma unroll
+          for (int c = 0; c < 4; c++) S.red[0][i][c] = v[c];
+        } else {
+          float2(&redf)[kWarps][32 * BPL][4] = *reinterpret_cast<float2(*)[kWarps][32 * BPL][4]>(&S.red[0][0][0]);
+          ff v[4];
+#pragma unroll
+          for (int c = 0; c < 4; c++) v[c] = ff_make(0.f, 0.f);
+          for (int w2 = 0; w2 < kWarps; w2++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) v[c] = ff_add(v[c], ff_make(redf[w2][i][c].x, redf[w2][i][c].y));
+#pragma unroll
+          for (int c = 0; c < 4; c++) redf[0][i][c] = make_float2(v[c].hi, v[c].lo);
+        }
+      }
+      cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+      cl.sync();
+      // member r stores bins i = r (mod CL): the members' partials summed in rank order
+      for (int i = tid; i < TB; i += kThreads) {
+        const long long bin = bin0 + i;
+        if (bin >= binEnd || i % CL != crank) continue;
+        if constexpr (PREC == 0) {
+          double v[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+          for (int r = 0; r < CL; r++) {
+            const double* src = cl.map_shared_rank(&S.red[0][i][0], r);
+#pragma unroll
+            for (int c = 0; c < 4; c++) v[c] = r == 0 ? src[c] : v[c] + src[c];
+          }
+          reinterpret_cast<double2*>(P.hp)[bin] = make_double2(v[0], v[1]);
+          reinterpret_cast<double2*>(P.hc)[bin] = make_double2(v[2], v[3]);
+        } else {
+          ff v[4];
+#pragma unroll
+          for (int c = 0; c < 4; c++) v[c] = ff_make(0.f, 0.f);
+#pragma unroll
+          for (int r = 0; r < CL; r++) {
+            const float2* src = cl.map_shared_rank(reinterpret_cast<const float2*>(&S.red[0][0][0]) + 4 * i, r);
+#pragma unroll
+            for (int c = 0; c < 4; c++) v[c] = ff_add(v[c], ff_make(src[c].x, src[c].y));
+          }
+          store_bin<PREC>(P, S.pf, bin, v);
+        }
+      }
+      cl.sync();   // the partials are read before any member overwrites them or exits
     }
-    __syncthreads();
   }
 }
 
-template <int BPL, int PREC, bool EXT>
+template <int BPL, int PREC, bool EXT, int CL>
 void launch_one(const SpaParams& p, int num_sms, cudaStream_t st) {
   size_t sm = sizeof(Smem<BPL, PREC>);
-  cudaFuncSetAttribute(k_spa<BPL, PREC, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_spa<BPL, PREC, EXT, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spa<BPL, PREC, EXT>, kThreads, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spa<BPL, PREC, EXT, CL>, kThreads, sm);
   if (per_sm < 1) per_sm = 1;
-  long long grid = (long long)num_sms * per_sm;
-  if (grid > p.tiles_total) grid = p.tiles_total > 0 ? p.tiles_total : 1;
-  k_spa<BPL, PREC, EXT><<<(unsigned)grid, kThreads, sm, st>>>(p);
+  if constexpr (CL == 1) {
+    long long grid = (long long)num_sms * per_sm;
+    if (grid > p.tiles_total) grid = p.tiles_total > 0 ? p.tiles_total : 1;
+    k_spa<BPL, PREC, EXT, 1><<<(unsigned)grid, kThreads, sm, st>>>(p);
+  } else {
+    // clusters of CL CTAs: as many as can be resident, at most one per tile
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    long long grid = ((long long)num_sms * per_sm / CL) * CL;
+    if (grid < CL) grid = CL;
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_spa<BPL, PREC, EXT, CL>, &cfg) == cudaSuccess && nclusters > 0)
+      grid = (long long)nclusters * CL;
+    else
+      cudaGetLastError();
+    const long long need = (p.tiles_total > 0 ? p.tiles_total : 1) * CL;
+    if (grid > need) grid = need;
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cudaLaunchKernelEx(&cfg, k_spa<BPL, PREC, EXT, CL>, p);
+  }
+}
+
+template <int PREC, bool EXT>
+void launch_tile(const SpaParams& p, int bpl, int split, int num_sms, cudaStream_t st) {
+  // tile splitting is built for the small tiles (sparse grids have few tiles)
+  if (bpl == 1) {
+    if (split == 4) launch_one<1, PREC, EXT, 4>(p, num_sms, st);
+    else if (split == 2) launch_one<1, PREC, EXT, 2>(p, num_sms, st);
+    else launch_one<1, PREC, EXT, 1>(p, num_sms, st);
+  } else if (bpl == 2) {
+    if (split == 4) launch_one<2, PREC, EXT, 4>(p, num_sms, st);
+    else if (split == 2) launch_one<2, PREC, EXT, 2>(p, num_sms, st);
+    else launch_one<2, PREC, EXT, 1>(p, num_sms, st);
+  } else {
+    launch_one<4, PREC, EXT, 1>(p, num_sms, st);
+  }
 }
 
 template <bool EXT>
-void launch_prec(const SpaParams& p, int bpl, int precision, int num_sms, cudaStream_t st) {
-  if (precision == 0) {
-    if (bpl == 1) launch_one<1, 0, EXT>(p, num_sms, st);
-    else if (bpl == 4) launch_one<4, 0, EXT>(p, num_sms, st);
-    else launch_one<2, 0, EXT>(p, num_sms, st);
-  } else if (precision == 2) {
-    if (bpl == 1) launch_one<1, 2, EXT>(p, num_sms, st);
-    else if (bpl == 4) launch_one<4, 2, EXT>(p, num_sms, st);
-    else launch_one<2, 2, EXT>(p, num_sms, st);
-  } else {
-    if (bpl == 1) launch_one<1, 1, EXT>(p, num_sms, st);
-    else if (bpl == 4) launch_one<4, 1, EXT>(p, num_sms, st);
-    else launch_one<2, 1, EXT>(p, num_sms, st);
-  }
+void launch_prec(const SpaParams& p, int bpl, int split, int precision, int num_sms, cudaStream_t st) {
+  if (precision == 0) launch_tile<0, EXT>(p, bpl, split, num_sms, st);
+  else if (precision == 2) launch_tile<2, EXT>(p, bpl, split, num_sms, st);
+  else launch_tile<1, EXT>(p, bpl, split, num_sms, st);
 }
 
 }  // namespace
@@ -672,8 +797,8 @@ void launch_spa(const CallShape& cs, const DevInputs& in, const DevScratch& s, i
   p.segff = s.segff; p.tabf = s.tabf; p.prefactor = in.prefactor; p.yk = s.yk;
   cudaMemsetAsync(s.counters, 0, sizeof(unsigned long long), st);
   const int bpl = cs.tile_bins / 32;
-  if (cs.ext) launch_prec<true>(p, bpl, cs.precision, num_sms, st);
-  else launch_prec<false>(p, bpl, cs.precision, num_sms, st);
+  if (cs.ext) launch_prec<true>(p, bpl, cs.tile_split, cs.precision, num_sms, st);
+  else launch_prec<false>(p, bpl, cs.tile_split, cs.precision, num_sms, st);
 }
 
 }  // namespace emrifd

@@ -50,6 +50,54 @@ def test_tile_shapes(oracle, tb):
     _cmp(run(w, tile_bins=tb), oracle.sum_modes(w), TOL64)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp64x", TOL64), ("mixed", TOL32)])
+@pytest.mark.parametrize("tb,split", [(32, 2), (32, 4), (64, 4)])
+def test_tile_split_clusters(oracle, prec, tol, tb, split):
+    """Tiles shared by a thread-block cluster of 2 or 4 CTAs (partials combined through
+    distributed shared memory): the small config and the sparse paper grid against the
+    oracle, and close to the unsplit call (only the grouping of the sums differs: 1e-14
+    for FP64, 1e-13 for the FP32-pair form, whose unit roundoff is 2^-48)."""
+    regroup = {"fp64": 1e-14, "fp64x": 1e-13}
+    for w in (synth.small_config(0, n_bins=3001), synth.paper_config(1, grid="sparse")):
+        got = run(w, precision=prec, tile_bins=tb, tile_split=split)
+        _cmp(got, oracle.sum_modes(w), tol)
+        if prec != "mixed":
+            ref = run(w, precision=prec, tile_bins=tb)
+            for x, y in zip(got, ref):
+                assert rel_l2(x, y) < regroup[prec]
+
+
+@pytest.mark.parametrize("split", [2, 4])
+def test_tile_split_batch_extended_graph(oracle, split):
+    """With a split: batch = singles bitwise, the extended form against its oracle, and
+    graph replay = direct call; a split with 128-bin tiles is refused."""
+    from paper_2307_12585_gb300 import api
+    from tests.gpu_util import plan_for
+    wfs = [synth.small_config(0, n_bins=3001), synth.paper_config(3, n_modes=300, T_years=0.5, grid="sparse", n_sparse=4000)]
+    bh, bc = run(wfs, tile_bins=64, tile_split=split)
+    off = 0
+    for w in wfs:
+        sh, sc = run(w, tile_bins=64, tile_split=split)
+        assert np.array_equal(bh[off:off + w.n_freqs], sh) and np.array_equal(bc[off:off + w.n_freqs], sc)
+        off += w.n_freqs
+    w = synth.paper_config(2, grid="sparse")
+    _cmp(run(w, spa="extended", tile_bins=32, tile_split=split), oracle.sum_modes(w, spa="extended"), TOL64)
+    plan = plan_for(wfs, tile_bins=32, tile_split=split)
+    b = plan.upload(synth.concat(wfs))
+    direct = [x.clone() for x in plan.sum_modes(b)]
+    out = (torch.zeros_like(direct[0]), torch.zeros_like(direct[1]))
+    g = plan.capture(b, out)
+    g.replay()
+    plan.sync()
+    assert torch.equal(out[0], direct[0]) and torch.equal(out[1], direct[1])
+    g.close()
+    with pytest.raises(api.EmriFdError):
+        plan.set_tile(128)
+    plan.close()
+    with pytest.raises(api.EmriFdError):
+        api.Plan("fp64", max_waveforms=1, max_knots=100, max_modes_total=10, max_bins_total=10, tile_split=2)
+
+
 def test_tile_shapes_agree():
     w = synth.small_config(0, n_bins=3001)
     a = run(w, tile_bins=32)
@@ -296,8 +344,15 @@ def test_autotuner(tmp_path, monkeypatch):
     out = plan.sum_modes(b)
     r1 = autotune.tune(plan, b, out)
     assert r1["tile_bins"] in (32, 64, 128) and not r1["cached"]
+    # 20000 bins are few tiles: the split candidates were timed too
+    assert "32x4" in r1["ms"] and r1["tile_split"] in (1, 2, 4)
     r2 = autotune.tune(plan, b, out)
-    assert r2["cached"] and r2["tile_bins"] == r1["tile_bins"]
+    assert r2["cached"] and r2["tile_bins"] == r1["tile_bins"] and r2["tile_split"] == r1["tile_split"]
+    # the tuned plan still matches the oracle's result within the FP64 bar
+    got = tuple(x.cpu().numpy() for x in plan.sum_modes(b))
+    ref = run(w)
+    for x, y in zip(got, ref):
+        assert rel_l2(x, y) < 1e-14
     plan.close()
 
 
