@@ -225,7 +225,7 @@ FORM_TILE = {"fp64x": 64, "mixed": 64}
 DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
 # DRAM bytes (read + write) of one k_spa<4,0,0> launch (FP64, standard SPA, 128-bin tiles) on
 # this workload, from one ncu capture of the kernel as it stands
-TRAFFIC_FP64_SPA = 101.924096e6 + 67.682816e6
+TRAFFIC_FP64_SPA = 102.650880e6 + 67.815936e6
 
 
 def base_line(args, world, metric, value, unit, ms, workload, extra=None):
