@@ -274,6 +274,30 @@ def test_degenerate_inputs(oracle):
     _cmp(run(t4), oracle.sum_modes(t4), TOL64)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_batched_workload_sampled(oracle, prec):
+    """The batched workload's recipe (N_m ~ U{50..3000}, T ~ U(0.5, 4) yr, N_f log-uniform in
+    [1e4, 6e6], uniform or log grids) for 24 waveforms (17.6e6 bins) in one call at the
+    tile size the autotuner picks: 8 of the waveforms against the oracle on 300 sampled
+    bins each (bins are independent)."""
+    from paper_2307_12585_gb300 import autotune
+    from tests.gpu_util import plan_for
+    wfs = synth.batch_config(24)
+    plan = plan_for(wfs, precision=prec)
+    b = plan.upload(synth.concat(wfs))
+    out = plan.sum_modes(b)
+    autotune.tune(plan, b, out, use_cache=False)
+    hp, hc = (x.cpu().numpy() for x in plan.sum_modes(b, out=out))
+    plan.close()
+    off = np.concatenate([[0], np.cumsum([w.n_freqs for w in wfs])])
+    rng = np.random.default_rng(24)
+    for i in rng.choice(len(wfs), 8, replace=False):
+        w = wfs[i]
+        idx = np.sort(rng.choice(w.n_freqs, min(300, w.n_freqs), replace=False))
+        rp, rc = oracle.sum_modes(w, freqs=w.freqs[idx])
+        _cmp((hp[off[i]:off[i + 1]][idx], hc[off[i]:off[i + 1]][idx]), (rp, rc), TOL64)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp64x", "mixed"])
 def test_batch_with_empty_members(prec):
     """A batch whose members include a waveform with no bins and one with no modes, between
