@@ -34,7 +34,9 @@
  *  - Data pointers may be device memory (the fast path; required while a
  *    stream is being captured into a CUDA graph) or host memory, in which
  *    case the call stages them through plan-owned device buffers and, for
- *    host outputs, synchronises the stream before returning.  The h_plus and
+ *    host outputs, synchronises the stream before returning (emri_fd_sum_modes
+ *    then also returns the device-detected errors, reading and resetting the
+ *    status word as emri_fd_sync does).  The h_plus and
  *    h_cross outputs of emri_fd_sum_modes are written in place, by the
  *    kernels, when they are page-locked host memory the device can address
  *    (cudaHostAlloc / cudaHostRegister; on GB300 over NVLink-C2C), so their

@@ -332,8 +332,9 @@ class Plan:
                                  *[_addr(b[k]) for k in ("t", "phi_phi", "phi_r", "omega_phi", "omega_r", "l", "m",
                                                          "n", "amp", "theta", "phi", "prefactor", "freqs")],
                                  _addr(out[0]), _addr(out[1]))
-        _check(code, "emri_fd_sum_modes")
-        _check(emri_fd_sync(self.handle), "emri_fd_sum_modes (device checks)")
+        _check(code, "emri_fd_sum_modes")   # host outputs: the call has synchronised and checked
+        if any(getattr(x, "is_cuda", False) for x in out):
+            _check(emri_fd_sync(self.handle), "emri_fd_sum_modes (device checks)")
         return out
 
     def td_sum(self, b, dt, n_samples, check=True):

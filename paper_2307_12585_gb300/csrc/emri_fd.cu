@@ -26,6 +26,7 @@ struct emri_fd_plan_s {
   cudaEvent_t ev_main = nullptr, ev_freqs = nullptr;
   bool freqs_side = false;           // the next run_forward waits for ev_freqs
   unsigned long long* cnt_pinned = nullptr;
+  int* st_pinned = nullptr;          // the status word read back by synchronising calls
   // staging for host-memory inputs / outputs
   void* stage[32] = {};
   size_t stage_sz[32] = {};
@@ -111,6 +112,7 @@ void emri_fd_plan_destroy(emri_fd_plan_t p) {
   for (int i = 0; i < 32; i++) if (p->stage[i]) cudaFree(p->stage[i]);
   if (p->wf_pinned) cudaFreeHost(p->wf_pinned);
   if (p->cnt_pinned) cudaFreeHost(p->cnt_pinned);
+  if (p->st_pinned) cudaFreeHost(p->st_pinned);
   if (p->wf_done) cudaEventDestroy(p->wf_done);
   if (p->side) { cudaStreamSynchronize(p->side); cudaStreamDestroy(p->side); }
   if (p->ev_main) cudaEventDestroy(p->ev_main);
@@ -208,6 +210,7 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
 #undef AL
   if (st == EMRI_FD_OK && (cudaMallocHost(&p->wf_pinned, sizeof(WfInfo) * d->max_waveforms) != cudaSuccess ||
                            cudaMallocHost(&p->cnt_pinned, sizeof(unsigned long long) * 8) != cudaSuccess ||
+                           cudaMallocHost(&p->st_pinned, sizeof(int)) != cudaSuccess ||
                            cudaEventCreateWithFlags(&p->wf_done, cudaEventDisableTiming) != cudaSuccess ||
                            cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
                            cudaEventCreateWithFlags(&p->ev_main, cudaEventDisableTiming) != cudaSuccess ||
@@ -355,6 +358,25 @@ emri_fd_status stage_out(emri_fd_plan_s* p, int slot, void* dst, size_t bytes, v
   return EMRI_FD_OK;
 }
 
+// read the status word back (pinned), reset it and synchronise once; the first latched
+// device-detected error, in a fixed order of precedence
+emri_fd_status sync_status(emri_fd_plan_s* p) {
+  if (cudaMemcpyAsync(p->st_pinned, p->s.status, sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+      cudaMemsetAsync(p->s.status, 0, sizeof(int), p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return EMRI_FD_ERR_CUDA;
+  }
+  const int hs = *p->st_pinned;
+  if (hs & ST_KNOTS) return EMRI_FD_ERR_KNOTS;
+  if (hs & ST_FREQ) return EMRI_FD_ERR_FREQ;
+  if (hs & ST_MODE) return EMRI_FD_ERR_MODE;
+  if (hs & ST_NONFINITE) return EMRI_FD_ERR_NONFINITE;
+  if (hs & ST_CAPACITY) return EMRI_FD_ERR_CAPACITY;
+  if (hs & ST_TIMEOUT) return EMRI_FD_ERR_TIMEOUT;
+  return EMRI_FD_OK;
+}
+
 // preparation kernels and the output kernel, with optional event timing
 void run_forward(emri_fd_plan_s* p, const CallShape& cs, const DevInputs& in, size_t ob) {
   cudaStream_t stm = p->stream;
@@ -435,7 +457,8 @@ emri_fd_status emri_fd_sum_modes(emri_fd_plan_t p, int n_wf, const long long* kn
   if ((hp_host && cudaMemcpyAsync(h_plus, in.h_plus, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess) ||
       (hc_host && cudaMemcpyAsync(h_cross, in.h_cross, ob, cudaMemcpyDeviceToHost, stm) != cudaSuccess))
     return EMRI_FD_ERR_CUDA;
-  if ((hp_host || hc_host || in_place) && cudaStreamSynchronize(stm) != cudaSuccess) return EMRI_FD_ERR_CUDA;
+  // host outputs: the call synchronises, so it also returns its device-detected errors
+  if (hp_host || hc_host || in_place) return sync_status(p);
   return EMRI_FD_OK;
 }
 
@@ -718,21 +741,7 @@ emri_fd_status emri_fd_loglike_and_grad(emri_fd_plan_t p, int n_wf, const long l
 
 emri_fd_status emri_fd_sync(emri_fd_plan_t p) {
   if (!p) return EMRI_FD_ERR_ARG;
-  int hs = 0;
-  if (cudaMemcpyAsync(&hs, p->s.status, sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
-      cudaStreamSynchronize(p->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return EMRI_FD_ERR_CUDA;
-  }
-  cudaMemsetAsync(p->s.status, 0, sizeof(int), p->stream);
-  cudaStreamSynchronize(p->stream);
-  if (hs & ST_KNOTS) return EMRI_FD_ERR_KNOTS;
-  if (hs & ST_FREQ) return EMRI_FD_ERR_FREQ;
-  if (hs & ST_MODE) return EMRI_FD_ERR_MODE;
-  if (hs & ST_NONFINITE) return EMRI_FD_ERR_NONFINITE;
-  if (hs & ST_CAPACITY) return EMRI_FD_ERR_CAPACITY;
-  if (hs & ST_TIMEOUT) return EMRI_FD_ERR_TIMEOUT;
-  return EMRI_FD_OK;
+  return sync_status(p);
 }
 
 emri_fd_status emri_fd_stats(emri_fd_plan_t p, long long* out, int nout) {

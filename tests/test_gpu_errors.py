@@ -1,5 +1,6 @@
 """Error behaviour of the C ABI on a device: host-side shape checks return at
-once; value checks run on the device and are reported by emri_fd_sync.  The
+once; value checks run on the device and are reported by emri_fd_sync (or by the
+call itself when its outputs are host memory, since it then synchronises).  The
 invalid inputs here are all rejected by those checks (nothing out of bounds
 is ever read or written)."""
 import numpy as np
@@ -89,4 +90,26 @@ def test_host_side_shape_errors():
     with pytest.raises(api.EmriFdError) as e:
         plan.sum_modes(big)
     assert e.value.code == 6
+    plan.close()
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_host_outputs_report_device_errors(pinned):
+    """With host outputs the call synchronises, so it returns its own device-detected
+    error (here: frequencies out of order, staged on the side stream), and the plan
+    stays usable."""
+    w = synth.small_config(0, n_bins=800)
+    plan = plan_for([w])
+    hb = api.host_batch(synth.concat([w]))
+    hb["freqs"] = hb["freqs"].copy()
+    hb["freqs"][100] = hb["freqs"][50]
+    out = None
+    if pinned:
+        out = (torch.empty(800, dtype=torch.complex128).pin_memory(), torch.empty(800, dtype=torch.complex128).pin_memory())
+    with pytest.raises(api.EmriFdError) as e:
+        plan.sum_modes_host(hb, out=out)
+    assert e.value.code == 3
+    good = api.host_batch(synth.concat([w]))
+    hp, hc = plan.sum_modes_host(good, out=out)
+    assert np.all(np.isfinite(np.asarray(hp))) and np.any(np.asarray(hp) != 0)
     plan.close()
