@@ -65,13 +65,17 @@ def linear_chirp_expected(w, p, f):
     return out
 
 
-def quadratic_voice(K=41, seed=1, nb=5000):
+def quadratic_voice(K=41, seed=1, nb=5000, uniform=False):
     """F(t) = Fs - kappa (t - ts)^2 / 2 with its maximum inside [0, T];
-    Phi = 2 pi [Fs (t - ts) - kappa (t - ts)^3 / 6] + Ps."""
+    Phi = 2 pi [Fs (t - ts) - kappa (t - ts)^3 / 6] + Ps.  Knots random (seeded), or
+    uniform (K = 40 puts the maximum mid-segment, at 21.45 segment widths)."""
     rng = np.random.default_rng(seed)
     T, ts, Fs, Ps = 1e6, 0.55e6, 2e-3, -1.2
     kappa = 1e-3 / (0.55e6) ** 2
-    t = np.concatenate([[0.0], np.sort(rng.uniform(0, T, K - 2)), [T]])
+    if uniform:
+        t = np.linspace(0.0, T, K)
+    else:
+        t = np.concatenate([[0.0], np.sort(rng.uniform(0, T, K - 2)), [T]])
     freqs = np.linspace(1.3e-3, 2.1e-3, nb)
     w = single_voice(t, lambda x: 2 * math.pi * (Fs * (x - ts) - kappa * (x - ts) ** 3 / 6) + Ps,
                      lambda x: 2 * math.pi * (Fs - 0.5 * kappa * (x - ts) ** 2), amp=0.5 + 0.9j, freqs=freqs)

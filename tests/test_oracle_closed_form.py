@@ -33,8 +33,56 @@ def test_linear_chirp(oracle):
     assert err.max() < TOL
 
 
-def test_quadratic_turning_point(oracle):
-    w, p = AN.quadratic_voice()
+def test_linear_chirp_from_two_series(oracle):
+    """A voice with m = 2, n = -1 whose fundamental phases are both quadratic:
+    Phi_V = m Phi_phi + n Phi_r is a linear chirp's phase with f0 = m p1 + n q1 and
+    Fdot = m p2 + n q2, so the closed form holds with the n Omega_r term of the
+    frequency track and the n Phi_r term of the phase at full weight (the other
+    closed forms have n = 0)."""
+    import mpmath as mp
+    from scipy.interpolate import CubicSpline
+    from paper_2307_12585_gb300.synth import Waveform
+    rng = np.random.default_rng(3)
+    K, T = 41, 1e6
+    t = np.concatenate([[0.0], np.sort(rng.uniform(0, T, K - 2)), [T]])
+    m, n = 2, -1
+    p1, p2, c1 = 0.8e-3, 0.7e-9, 0.2      # Phi_phi = 2 pi (p1 t + p2 t^2/2) + c1
+    q1, q2, c2 = 0.6e-3, 0.4e-9, -0.1     # Phi_r   = 2 pi (q1 t + q2 t^2/2) + c2
+    tp = 2 * math.pi
+    pp, pr = tp * (p1 * t + p2 * t * t / 2) + c1, tp * (q1 * t + q2 * t * t / 2) + c2
+    amp = 0.7 + 0.4j
+    freqs = np.linspace(0.8e-3, 2.2e-3, 3000)
+    w = Waveform(t, pp, pr, tp * (p1 + p2 * t), tp * (q1 + q2 * t), np.array([3], np.int32), np.array([m], np.int32),
+                 np.array([n], np.int32), np.full((1, K), amp, np.complex128), 0.9, 0.4, 1.0, freqs)
+    got = _voice(oracle, w) / amp
+    # expected: the chirp's transform, with the spline of the combined phase knots' rounding
+    mp.mp.dps = 40
+    P = [mp.mpf(x) for x in (p1, p2, c1, q1, q2, c2)]
+    f0, fd = m * P[0] + n * P[3], m * P[1] + n * P[4]
+    P0 = m * P[2] + n * P[5]
+    exact = lambda x: 2 * mp.pi * (f0 * x + fd * x * x / 2) + P0
+    d = np.array([float(m * mp.mpf(float(pp[k])) + n * mp.mpf(float(pr[k])) - exact(mp.mpf(float(t[k])))) for k in range(K)])
+    corr = CubicSpline(t, d, bc_type="not-a-knot")
+    exp = np.zeros(freqs.shape, np.complex128)
+    for i, fi in enumerate(freqs):
+        x = mp.mpf(fi) - f0
+        if not (0 <= x < fd * T):
+            continue
+        psi = mp.pi * x * x / fd - P0 - mp.pi / 4 - float(corr(float(x / fd)))
+        exp[i] = complex(mp.cos(psi), mp.sin(psi)) / math.sqrt(float(fd))
+    assert np.count_nonzero(exp) > 1000
+    assert np.array_equal(got != 0, exp != 0)
+    err = np.abs(got - exp) / np.abs(exp).max()
+    assert err.max() < TOL
+
+
+@pytest.mark.parametrize("uniform", [False, True])
+def test_quadratic_turning_point(oracle, uniform):
+    w, p = AN.quadratic_voice(K=40, uniform=True) if uniform else AN.quadratic_voice()
+    # plus a dense cluster just below the turnover frequency; with uniform knots the
+    # turnover is mid-segment, so both roots of these bins fall in the segment that
+    # holds it (its split into monotone pieces is exercised)
+    w = w.with_freqs(np.unique(np.concatenate([w.freqs, p["Fs"] * (1 - np.logspace(-5.9, -3.3, 160))])))
     got = _voice(oracle, w) / w.amp[0, 0]
     exp = AN.quadratic_voice_expected(w, p, w.freqs)
     # Near the turnover F*, the FP64 rounding of F(t) - f (~1e-16 |F|) moves
