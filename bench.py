@@ -31,8 +31,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = ("paper-shaped FP64 single waveform: T=2 yr, K=200 knots, 2000 modes (l=2..10, m=1..l, "
             "|n|<=30, top mean power of 3294), 3,155,760 bins f=i/T, conjugate partners implied")
-FP64_OPS_PER_MODE_BIN = 34      # 26 DFMA + 8 DMUL/DADD per mode-bin in k_spa<*, 0, 0> (counted from the source)
-FP64_FLOPS_PER_MODE_BIN = 60    # 26 x 2 + 8
+FP64_OPS_PER_MODE_BIN = 31      # 25 DFMA + 6 DMUL/DADD per mode-bin in k_spa<*, 0, 0> (counted from the source)
+FP64_FLOPS_PER_MODE_BIN = 56    # 25 x 2 + 6
 FP64_PER_CLK_PER_SM = 2          # GB300 FP64 issue rate (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
 MIXED_FP64_OPS_PER_MODE_BIN = 9  # the mixed form's FP64 left per mode-bin: difference 1, root polish 4, phase 4
 ADJ_FP64_OPS_PER_MODE_BIN = 76   # k_adjoint per mode-bin: the forward's 30 (with dA/du) + 46 for the derivatives
@@ -225,7 +225,7 @@ FORM_TILE = {"fp64x": 64, "mixed": 64}
 DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
 # DRAM bytes (read + write) of one k_spa<4,0,0> launch (FP64, standard SPA, 128-bin tiles) on
 # this workload, from one ncu capture of the kernel as it stands
-TRAFFIC_FP64_SPA = 102.650880e6 + 67.815936e6
+TRAFFIC_FP64_SPA = 102.923264e6 + 67.747840e6
 
 
 def base_line(args, world, metric, value, unit, ms, workload, extra=None):
@@ -414,13 +414,14 @@ def run_paper(args, rank, world, local):
                     "against 2 FP64 instructions/clk/SM at the median SM clock; the rest is FP32 and integer work"
                     % MIXED_FP64_OPS_PER_MODE_BIN}
         elif prec == "fp64x" and spa == "standard":
-            # no FP64 per mode-bin: the FP64 form's 60 flops of FP64-accurate arithmetic per
+            # no FP64 per mode-bin: the FP64 form's flops of FP64-accurate arithmetic per
             # mode-bin, done in FP32 pairs, against the FP64 pipe's peak
             ach = FP64_FLOPS_PER_MODE_BIN * mb_per_launch / ospa_s
             roof = {"bound": "issue", "fp64_equivalent_achieved": ach / 1e12, "peak": peak_tflops,
                     "unit": "TFLOP/s", "frac_of_fp64_peak": ach / (peak_tflops * 1e12),
-                    "note": "FP64-accurate work (the FP64 form's 60 flops per mode-bin) in FP32 pairs and "
-                    "integers, against the FP64 pipe's nominal peak; instruction issue is the limit"}
+                    "note": "FP64-accurate work (the FP64 form's %d flops per mode-bin) in FP32 pairs and "
+                    "integers, against the FP64 pipe's nominal peak; instruction issue is the limit"
+                    % FP64_FLOPS_PER_MODE_BIN}
         else:
             roof = None
         return {"value": world * args.steps / (oms * 1e-3), "unit": "waveforms/s", "ms_per_step": oms / args.steps,
@@ -495,7 +496,7 @@ def run_paper(args, rank, world, local):
                           # the same launch against HBM: far from that roof (compute-bound)
                           "hbm": ({"achieved_GBs": TRAFFIC_FP64_SPA / spa_s / 1e9, "peak_GBs": hbm_peak,
                                    "frac": TRAFFIC_FP64_SPA / spa_s / 1e9 / hbm_peak}
-                                  if args.tile_bins == 128 and hbm_peak else None),
+                                  if args.tile_bins == 128 and hbm_peak and TRAFFIC_FP64_SPA else None),
                           "note": "FP64 pipe: %d FP64 flops (%d FP64 instructions) per mode-bin; peak = %d FP64 FMA/clk/SM x 2 x SMs x median SM clock; traffic = DRAM bytes per launch from one ncu capture" % (
                               FP64_FLOPS_PER_MODE_BIN, FP64_OPS_PER_MODE_BIN, FP64_PER_CLK_PER_SM)}
                          if headline else None),

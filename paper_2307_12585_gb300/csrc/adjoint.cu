@@ -144,7 +144,11 @@ __global__ void __launch_bounds__(256, 2) k_adjoint(AdjParams P) {
     const ModeInfo M = P.modes[R.mode];
     const WfInfo W = P.wf[M.wf];
     const SegCore C = P.core[M.seg_base + s];
-    const SegAmp64 Am = P.amp64[M.seg_base + s];
+    const SegAmp64 Am = P.amp64[M.seg_base + s];   // times M.scale
+    // alpha, beta over the record's scale (one is 1); the amplitude sums are multiplied
+    // back by the scale in k_seg_sum
+    const bool amaj = alpha_major(M.alpha, M.beta);
+    const double ap = amaj ? 1.0 : M.rho, bp = amaj ? M.rho : 1.0;
     const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
     // per-segment constants of dA/du, d2F/du2 and dPhi_V/du
     const double a3r = 3.0 * Am.re[3], a2r = 2.0 * Am.re[2], a3i = 3.0 * Am.im[3], a2i = 2.0 * Am.im[2];
@@ -194,8 +198,8 @@ __global__ void __launch_bounds__(256, 2) k_adjoint(AdjParams P) {
         const double dAi = fma(u, fma(u, a3i, a2i), Am.im[1]);
         const dbl4 Gb = P.G[b];
         double Qr, Qi;
-        if (!neg) { Qr = M.alpha * Gb.x + M.beta * Gb.w; Qi = -M.alpha * Gb.y + M.beta * Gb.z; }
-        else { Qr = M.alpha * Gb.x - M.beta * Gb.w; Qi = M.alpha * Gb.y + M.beta * Gb.z; }
+        if (!neg) { Qr = ap * Gb.x + bp * Gb.w; Qi = -ap * Gb.y + bp * Gb.z; }
+        else { Qr = ap * Gb.x - bp * Gb.w; Qi = ap * Gb.y + bp * Gb.z; }
         const double QEr = Qr * Er - Qi * Ei, QEi = Qr * Ei + Qi * Er;
         const double QZr = QEr * Ar - QEi * Ai, QZi = QEr * Ai + QEi * Ar;
         const double Dp = fma(d2c, u, C.c2);                  // d^2F/du^2
@@ -261,7 +265,8 @@ __global__ void __launch_bounds__(256, 2) k_adjoint(AdjParams P) {
 
 // per (mode, segment): sum the sub-piece slots into slot 0 and scale the
 // amplitude part to the unscaled spline coefficients (the record holds
-// prefactor sqrt(h) times them)
+// prefactor sqrt(h) scale times them, and the sums were formed with alpha and
+// beta over the mode's scale)
 __global__ void k_seg_sum(long long seg_total, const WfInfo* wf, const ModeInfo* modes, int n_wf, const SegCore* core,
                           const double* pref, double* slots) {
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -269,7 +274,9 @@ __global__ void k_seg_sum(long long seg_total, const WfInfo* wf, const ModeInfo*
   int lo = 0, hi = n_wf - 1;
   while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (wf[mid].seg_base <= r) lo = mid; else hi = mid - 1; }
   double* a = slots + r * 3 * 16;
-  const double sc = pref[lo] * sqrt(core[r].h);
+  const WfInfo W = wf[lo];
+  const ModeInfo& M = modes[W.mo + (r - W.seg_base) / (W.K - 1)];
+  const double sc = pref[lo] * sqrt(core[r].h) * M.scale;
   for (int q = 0; q < 16; q++) {
     double v = a[q] + a[16 + q] + a[32 + q];
     a[q] = q >= 8 ? v * sc : v;

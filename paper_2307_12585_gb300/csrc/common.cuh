@@ -56,7 +56,12 @@ struct ModeInfo {
   long long key_base;      // first knot key / amplitude knot of this mode
   double alpha, beta;      // h+ += alpha Z, hx += i beta Z (positive branch), see spa.cu
   float af[2], bf[2];      // alpha, beta as FP32 pairs (hi, lo)
+  // FP64 records: the amplitude is stored times scale, the one of alpha, beta of larger
+  // magnitude (alpha_major), and rho = the other over it (0 when both are 0), so that
+  // alpha Z and beta Z take one multiply by rho instead of two by alpha and beta
+  double scale, rho;
 };
+static_assert(sizeof(ModeInfo) == 80, "ModeInfo layout");
 
 struct __align__(16) SegCore {
   double A;                // F_V(t_s), knot expression (m*Om_phi_s + n*Om_r_s)/(2 pi)  [Hz]
@@ -124,6 +129,12 @@ __device__ __forceinline__ bool is_zero_bits(double x) {
 __device__ __forceinline__ double flip_sign(double x) {
   // -x through the sign bit (an integer operation, not an FP64 instruction)
   return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+
+// |alpha| >= |beta|, compared through the bits of the magnitudes (integer order is
+// numeric order for non-negative doubles); the same test wherever ModeInfo.scale is used
+__device__ __forceinline__ bool alpha_major(double alpha, double beta) {
+  return (__double_as_longlong(alpha) & 0x7FFFFFFFFFFFFFFFll) >= (__double_as_longlong(beta) & 0x7FFFFFFFFFFFFFFFll);
 }
 
 __device__ __forceinline__ float d2f_bits(double x) {

@@ -50,7 +50,7 @@ constexpr size_t kOffRunF = kOffRuns + al256(kNaRunCap * sizeof(Run));
 constexpr size_t kOffRbins = kOffRunF + al256(kNaRunCap * sizeof(double2));
 constexpr size_t kOffTab = kOffRbins + al256(kNaRunCap * sizeof(RunBins));
 constexpr size_t kNaBytes = kOffTab + al256(kTab64N * sizeof(double2));
-static_assert(kNaBytes == 7553280, "the size stated in include/emri_fd.h");
+static_assert(kNaBytes == 7555328, "the size stated in include/emri_fd.h");
 
 // The scratch.  In host code this name is only a stand-in for the device
 // symbol; its device address comes from cudaGetSymbolAddress below.

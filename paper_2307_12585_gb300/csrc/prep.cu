@@ -130,6 +130,9 @@ __device__ __forceinline__ void modes_warp(long long j, int lane, int n_wf, cons
   if (lane == 0) {
     const ff a = ff_from_double(M.alpha), b = ff_from_double(M.beta);
     M.af[0] = a.hi; M.af[1] = a.lo; M.bf[0] = b.hi; M.bf[1] = b.lo;
+    const bool amaj = alpha_major(M.alpha, M.beta);
+    M.scale = amaj ? M.alpha : M.beta;
+    M.rho = M.scale != 0.0 ? (amaj ? M.beta : M.alpha) / M.scale : 0.0;   // |rho| <= 1
     modes[j] = M;
   }
 }
@@ -434,9 +437,10 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
   double cre[4], cim[4];
   ucoef(ay[0], ay[2], am[0], am[2], h2, cre);
   ucoef(ay[1], ay[3], am[1], am[3], h2, cim);
-  if (amp64) {
+  if (amp64) {   // FP64 records also carry the mode's polarisation scale
     SegAmp64 A;
-    for (int q = 0; q < 4; q++) { A.re[q] = sc * cre[q]; A.im[q] = sc * cim[q]; }
+    const double sc64 = sc * Mi.scale;
+    for (int q = 0; q < 4; q++) { A.re[q] = sc64 * cre[q]; A.im[q] = sc64 * cim[q]; }
     amp64[r] = A;
   }
   if (amp32) {

@@ -481,9 +481,12 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
           s_uni = s_lo == s_hi ? s_lo : -1;
         }
         if constexpr (PREC == 0) {
-          // h+ += alpha Z~, hx += i sb Z~; the sign flips are integer operations on the sign bit
-          const double sa = M.alpha, sai = neg ? flip_sign(M.alpha) : M.alpha;
-          const double sb = neg ? flip_sign(M.beta) : M.beta, nbeta = flip_sign(M.beta);
+          // h+ += alpha Z~, hx += i beta Z~ (conjugates on the negative branch).  The
+          // amplitude record carries the factor scale (alpha or beta, the larger in
+          // magnitude), so the two multipliers are 1 and rho in some order: with the
+          // weight, cw and rho cw.  Sign flips are integer operations on the sign bit.
+          const bool amaj = alpha_major(M.alpha, M.beta);
+          const double rho = M.rho;
 #pragma unroll
           for (int q = 0; q < BPL; q++) {
             const long long bin = bin0 + lane + 32 * q;
@@ -498,16 +501,35 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
             const double delta = g - C.A;
             float uf, Df;
             const double u = solve_root<6, EXT>(C, delta, ulo, uhi, R.dir, uf, Df);
-            // a8: dF/du and the weight sqrt(h)/sqrt|dF/du| (sqrt(h) is in the amplitude)
+            // a8: dF/du
             const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
             const long long Dbits = __double_as_longlong(Dd);
             bool coal = is_zero_bits(Dd);   // Fdot == 0
             if (!EXT && coal) continue;                         // standard form: no contribution
             const bool pos_slope = Dbits >= 0;
-            double wgt = coal ? 0.0 : rsqrt_abs(Dd);
-            double rr = 1.0, ri = 0.0;
-            if constexpr (EXT) {
+            const SegAmp64 Am = P.amp64[M.seg_base + s];
+            double zr, zi, mp, mx;   // h+ += mp Z, hx += i mx Z (Z without the weight's factor)
+            if constexpr (!EXT) {
+              // a7: phase in Q0.64 turns; e^{i psi} = T_k (1 - q)(1 + i x')
+              const unsigned long long Th = phase_q64(C, g, delta, u, pos_slope);
+              double2 T;
+              double xp, c1;
+              cis_split_q64(Th, P.tab, T, xp, c1);   // the 1 MB table is read through L1 and L2
+              // a8: the weight (1 - q)/sqrt|dF/du| (sqrt(h) is in the amplitude)
+              const double cw = rsqrt_abs(Dd, c1);
+              // a9-a10: Z = (A T)(1 + i x'), the multipliers cw and rho cw
+              const double are = fma(u, fma(u, fma(u, Am.re[3], Am.re[2]), Am.re[1]), Am.re[0]);
+              const double aim = fma(u, fma(u, fma(u, Am.im[3], Am.im[2]), Am.im[1]), Am.im[0]);
+              const double atr = fma(are, T.x, -aim * T.y), ati = fma(are, T.y, aim * T.x);
+              zr = fma(-xp, ati, atr);
+              zi = fma(xp, atr, ati);
+              const double t = rho * cw;
+              mp = amaj ? cw : t;
+              mx = amaj ? t : cw;
+            } else {
               // extended form: R(X) from y = 1/X = 3 (d2F/du2)^2 / (2 pi h (dF/du)^3)
+              double wgt = coal ? 0.0 : rsqrt_abs(Dd);
+              double rr = 1.0, ri = 0.0;
               const double D2 = fma(2.0 * C.d3, u, C.c2);
               if (!coal) {
                 const double w2 = wgt * wgt;
@@ -520,29 +542,28 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
                 wgt = ext_coalesced(D2, C.h);
                 if (wgt == 0.0) continue;
               }
-            }
-            // a7: phase in Q0.64 turns (a double root of the extended form has no pi/4 shift)
-            unsigned long long Th = phase_q64(C, g, delta, u, pos_slope);
-            if (EXT && coal) Th += pos_slope ? (1ull << 61) : (0ull - (1ull << 61));
-            double er, ei;
-            cis_w_q64(Th, P.tab, wgt, er, ei);   // w e^{i psi}; the 1 MB table is read through L1 and L2
-            // a9-a10
-            const SegAmp64 Am = P.amp64[M.seg_base + s];
-            double are = fma(u, fma(u, fma(u, Am.re[3], Am.re[2]), Am.re[1]), Am.re[0]);
-            double aim = fma(u, fma(u, fma(u, Am.im[3], Am.im[2]), Am.im[1]), Am.im[0]);
-            if constexpr (EXT) {
+              // a7: phase in Q0.64 turns (a double root has no pi/4 shift)
+              unsigned long long Th = phase_q64(C, g, delta, u, pos_slope);
+              if (coal) Th += pos_slope ? (1ull << 61) : (0ull - (1ull << 61));
+              double er, ei;
+              cis_w_q64(Th, P.tab, wgt, er, ei);   // w e^{i psi}
+              // a9-a10
+              double are = fma(u, fma(u, fma(u, Am.re[3], Am.re[2]), Am.re[1]), Am.re[0]);
+              double aim = fma(u, fma(u, fma(u, Am.im[3], Am.im[2]), Am.im[1]), Am.im[0]);
               const double nr = fma(are, rr, -aim * ri);
               aim = fma(are, ri, aim * rr);
               are = nr;
+              zr = fma(are, er, -aim * ei);
+              zi = fma(are, ei, aim * er);
+              mp = amaj ? 1.0 : rho;
+              mx = amaj ? rho : 1.0;
             }
-            const double zr = fma(are, er, -aim * ei);
-            const double zi = fma(are, ei, aim * er);
             // a11: positive branch h+ += alpha Z, hx += i beta Z;
             //      negative branch h+ += alpha conj Z, hx += -i beta conj Z
-            acc[q][0] = fma(sa, zr, acc[q][0]);
-            acc[q][1] = fma(sai, zi, acc[q][1]);
-            acc[q][2] = fma(nbeta, zi, acc[q][2]);
-            acc[q][3] = fma(sb, zr, acc[q][3]);
+            acc[q][0] = fma(mp, zr, acc[q][0]);
+            acc[q][1] = fma(neg ? flip_sign(mp) : mp, zi, acc[q][1]);
+            acc[q][2] = fma(flip_sign(mx), zi, acc[q][2]);
+            acc[q][3] = fma(neg ? flip_sign(mx) : mx, zr, acc[q][3]);
           }
         } else {
           // FP64X and mixed: one copy of the per-bin body (rolled loop over the

@@ -187,6 +187,33 @@ __device__ __forceinline__ void cis_w_q64(unsigned long long Th, const double2* 
   ei = fma(T.y, cw, T.x * wx);
 }
 
+// The parts of e^{2 pi i Th/2^64} used by the standard FP64 form: the table entry
+// T_k = e^{2 pi i k/65536} nearest Th, and with x = 2 pi (Th/2^64 - k/65536),
+// |x| <= pi/65536, the factor e^{ix} = (1 - x^2/2)(1 + i x') + O(x^4) where
+// x' = x (1 + x^2/3) (so that (1 - x^2/2) x' = x - x^3/6 + O(x^5)).  q = x^2/2 is a
+// correction below 1.2e-9 and is formed in FP32 (its error is below 5e-16 of the
+// result); it is returned as c1 = 1 - 2q, the double that folds it into the
+// weight's Newton step.  x' is formed from the integer remainder, corrected in the
+// integer domain, times 2 pi/2^64: one FP64 instruction in all.
+__device__ __forceinline__ void cis_split_q64(unsigned long long Th, const double2* tab, double2& T, double& xp,
+                                              double& c1) {
+  const unsigned long long kq = (Th + (1ull << (63 - kTab64Bits))) >> (64 - kTab64Bits);
+  const long long rr = (long long)(Th - (kq << (64 - kTab64Bits)));   // |rr| <= 2^47
+  // x in FP32 from the top bits of rr (rr/2^25 rounded, |.| <= 2^22)
+  const float rrf = small_int_to_float((int)((rr + (1ll << 24)) >> 25));
+  const float xf = rrf * 1.1429048e-11f;                  // 2 pi 2^25/2^64
+  const float qf = 0.5f * xf * xf;                        // <= 1.15e-9
+  // rr x^2/3 = rr (2q/3) = (rr/2^25)(q 2^26/3), |.| <= 1.1e5, rounded to an integer
+  const float corr = __fmul_rn(rrf, __fmul_rn(qf, 22369621.3f));
+  const long long ci = (long long)(__float_as_int(__fadd_rn(corr, 12582912.0f)) - 0x4B400000);
+  xp = small_ll_to_double(rr + ci) * kTwoPiOver2p64;
+  // 2q in units of 2^-50 (q 2^51 <= 2.6e6 < 2^22); 1 - n 2^-53 has the bits of 1.0 minus n
+  const long long qi =
+      (long long)(__float_as_int(__fadd_rn(__fmul_rn(qf, 2251799813685248.0f), 12582912.0f)) - 0x4B400000);
+  c1 = __longlong_as_double(0x3FF0000000000000ll - (qi << 3));
+  T = __ldg(tab + (kq & (kTab64N - 1)));
+}
+
 // y^2 exactly, as a double, for a positive normal float y: the product of the
 // 24-bit significands has at most 48 bits (integer instructions only)
 __device__ __forceinline__ double sq_exact(float y) {
@@ -203,11 +230,13 @@ __device__ __forceinline__ double sq_exact(float y) {
 // FP64 pipe, so the step takes two FP64 instructions.  A |D| below the float
 // range gives an infinite seed (such a root sits on a turnover, where the
 // standard form diverges anyway).
-__device__ __forceinline__ double rsqrt_abs(double Dd) {
+// With c1 = 1 - 2q in place of 1 the step returns (1 - q)/sqrt|D| to within
+// |e| q/2 (below 2e-16), the weight already times a real factor 1 - q.
+__device__ __forceinline__ double rsqrt_abs(double Dd, double c1 = 1.0) {
   const double Dabs = abs_bits(Dd);
   const float y0f = rsqrtf(d2f_bits(Dabs));
   const double y0 = f2d_bits(y0f), y0h = f2d_bits(0.5f * y0f);
-  const double e = fma(-Dabs, sq_exact(y0f), 1.0);
+  const double e = fma(-Dabs, sq_exact(y0f), c1);
   return fma(y0h, e, y0);
 }
 
