@@ -31,11 +31,11 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = ("paper-shaped FP64 single waveform: T=2 yr, K=200 knots, 2000 modes (l=2..10, m=1..l, "
             "|n|<=30, top mean power of 3294), 3,155,760 bins f=i/T, conjugate partners implied")
-FP64_OPS_PER_MODE_BIN = 31      # 25 DFMA + 6 DMUL/DADD per mode-bin in k_spa<*, 0, 0> (counted from the source)
-FP64_FLOPS_PER_MODE_BIN = 56    # 25 x 2 + 6
+FP64_OPS_PER_MODE_BIN = 30      # 25 DFMA + 5 DMUL/DADD per mode-bin in k_spa<*, 0, 0> (counted from the source)
+FP64_FLOPS_PER_MODE_BIN = 55    # 25 x 2 + 5
 FP64_PER_CLK_PER_SM = 2          # GB300 FP64 issue rate (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
 MIXED_FP64_OPS_PER_MODE_BIN = 9  # the mixed form's FP64 left per mode-bin: difference 1, root polish 4, phase 4
-ADJ_FP64_OPS_PER_MODE_BIN = 76   # k_adjoint per mode-bin: the forward's 30 (with dA/du) + 46 for the derivatives
+ADJ_FP64_OPS_PER_MODE_BIN = 75   # k_adjoint per mode-bin: the forward's 29 (with dA/du) + 46 for the derivatives
 
 
 def parse():
@@ -225,7 +225,7 @@ FORM_TILE = {"fp64x": 64, "mixed": 64}
 DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
 # DRAM bytes (read + write) of one k_spa<4,0,0> launch (FP64, standard SPA, 128-bin tiles) on
 # this workload, from one ncu capture of the kernel as it stands
-TRAFFIC_FP64_SPA = 102.923264e6 + 67.747840e6
+TRAFFIC_FP64_SPA = 102.095104e6 + 72.666368e6
 
 
 def base_line(args, world, metric, value, unit, ms, workload, extra=None):

@@ -277,7 +277,7 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
       }
     }
   }
-  unsigned long long Th = phase_q64(C, g, delta, u, pos);
+  unsigned long long Th = phase_q64<false>(C, g, delta, u, pos);
   if (coal) Th += pos ? (1ull << 61) : (0ull - (1ull << 61));
   // half-turns in [-1, 1) from the top 46 bits of Th, without conversion instructions
   const long long ts_ = (long long)Th;

@@ -145,12 +145,18 @@ __device__ __forceinline__ double solve_root(const SegCore& C, double delta, dou
   return u;
 }
 
-// a7: Q0.64 phase (turns) of 2 pi g t - Phi_V(t) + m phi - sgn(Fdot) pi/4
+// a7: Q0.64 phase (turns) of 2 pi g t - Phi_V(t) + m phi - sgn(Fdot) pi/4.  g t_s is
+// reduced modulo one turn from its exact integer mantissa product.  With INT_INSEG the
+// in-segment product u (delta h - Q1 - ...) is too, in place of an FP64 multiply (one
+// FP64 instruction fewer for FP64-bound kernels; the mixed form, which is bound by its
+// integer work as much, keeps the multiply).
+template <bool INT_INSEG = true>
 __device__ __forceinline__ unsigned long long phase_q64(const SegCore& C, double g, double delta, double u,
                                                         bool pos_slope) {
   const double inner = fma(u, fma(u, C.P3, C.P2), C.Q1);
-  const double inseg = u * (delta * C.h - inner);
-  unsigned long long Th = q64_mul(g, C.ts) - C.theta0 + q64_of(inseg);
+  unsigned long long Th = q64_mul(g, C.ts) - C.theta0;
+  if constexpr (INT_INSEG) Th += q64_mul(u, fma(delta, C.h, -inner));
+  else Th += q64_of(u * (delta * C.h - inner));
   Th += pos_slope ? (0ull - (1ull << 61)) : (1ull << 61);
   return Th;
 }
