@@ -31,8 +31,8 @@ def test_three_term_form_is_exact_on_dft(oracle):
         assert err < 1e-11
 
 
-def test_hann_fd_definition():
-    from oracle import oracle as O
+def test_hann_fd_definition(oracle):
+    O = oracle
     h = np.array([1 + 2j, -3.0, 0.5j, 4.0])
     got = O.hann_fd(h)
     exp = np.array([0.5 * h[0] - 0.25 * h[1], 0.5 * h[1] - 0.25 * (h[0] + h[2]),
