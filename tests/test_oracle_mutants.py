@@ -13,6 +13,7 @@ import pytest
 from tests import test_oracle_closed_form as CF
 from tests import test_oracle_ext as EXT
 from tests import test_oracle_fft as FFT
+from tests import test_oracle_grad as GRAD
 from tests import test_oracle_invariants as INV
 from tests import test_oracle_select as SEL
 from tests import test_oracle_spline as SPL
@@ -73,6 +74,19 @@ MUTANTS = [
      "hin += w.prefactor * ((-1) ** l) * np.conj(A) * Yp * np.exp(1j * (m * Pp + n * Pr))",
      "hin += w.prefactor * ((-1) ** l) * np.conj(A) * Yp * np.exp(-1j * (m * Pp + n * Pr))"),
     ("TD h_x sign", "py", "td", "return tj, h.real.copy(), -h.imag", "return tj, h.real.copy(), h.imag"),
+    # Whittle likelihood and its knot gradient (Eq. 13-14)
+    ("likelihood -2 df -> -df", "c", "grad", "L += -2.0 * df * (rpr * rpr + rpi * rpi + rcr * rcr + rci * rci) / psd[i];",
+     "L += -1.0 * df * (rpr * rpr + rpi * rpi + rcr * rcr + rci * rci) / psd[i];"),
+    ("residual weight 4 df -> 2 df", "c", "grad", "double s = 4.0 * df / psd[i];", "double s = 2.0 * df / psd[i];"),
+    ("d^2F/dt^2 term of the weight dropped", "c", "grad", "- 0.5 * Xr * Fdd / Fd - Xi", "- 0.0 * Xr * Fdd / Fd - Xi"),
+    ("dFdot/dc_j without its factor j", "c", "grad", "double dfdot = (j == 0) ? 0.0 : j * xp[j - 1];",
+     "double dfdot = (j == 0) ? 0.0 : xp[j - 1];"),
+    ("partner amplitude gradient sign", "c", "grad", "ga[sc + 4 * k + q] += -sgn * a[12 + q]; }",
+     "ga[sc + 4 * k + q] += sgn * a[12 + q]; }"),
+    ("negative-branch residual weight", "c", "grad", "else { Wr = 0.5 * (Gb[0] - Gb[3]); Wi = 0.5 * (Gb[1] + Gb[2]); }",
+     "else { Wr = 0.5 * (Gb[0] + Gb[3]); Wi = 0.5 * (Gb[1] + Gb[2]); }"),
+    ("Phi_r chain rule uses m", "c", "grad", "gcf[1 * sc + 4 * k + q] += (double)V->n * a[4 + q];",
+     "gcf[1 * sc + 4 * k + q] += (double)V->m * a[4 + q];"),
 ]
 
 # the pins run on each mutant: (group, name, call)
@@ -96,6 +110,12 @@ BATTERY = [
     ("window", "three-term form on the DFT", lambda O: WIN.test_three_term_form_is_exact_on_dft(O)),
     ("window", "FD definition", lambda O: WIN.test_hann_fd_definition(O)),
     ("td", "linear chirp samples", lambda O: TD.test_linear_chirp_samples(O)),
+    ("grad", "likelihood definition", lambda O: GRAD.test_loglike_definition(O)),
+    ("grad", "Euler identity", lambda O: GRAD.test_euler_identity_amplitudes(O)),
+    ("grad", "phase offset identities", lambda O: [GRAD.test_phase_offset_identity(O, x) for x in ("phi_phi", "phi_r")]),
+    ("grad", "central differences", lambda O: [GRAD.test_central_differences(O, x, h) for x, h in
+                                               (("phi_phi", 3e-5), ("phi_r", 3e-5), ("omega_phi", 1e-8),
+                                                ("omega_r", 1e-8), ("amp", 1e-4))]),
 ]
 
 
