@@ -237,7 +237,8 @@ __device__ __forceinline__ double sq_exact(float y) {
 // range gives an infinite seed (such a root sits on a turnover, where the
 // standard form diverges anyway).
 // With c1 = 1 - 2q in place of 1 the step returns (1 - q)/sqrt|D| to within
-// |e| q/2 (below 2e-16), the weight already times a real factor 1 - q.
+// |e| q/2 (below 3e-16 for a seed within 2 ulp), the weight already times a real
+// factor 1 - q.
 __device__ __forceinline__ double rsqrt_abs(double Dd, double c1 = 1.0) {
   const double Dabs = abs_bits(Dd);
   const float y0f = rsqrtf(d2f_bits(Dabs));
