@@ -64,9 +64,9 @@ __global__ void k_validate_amp(long long n2, const double* amp, int* status) {
 // ---------------------------------------------------- spin-weighted harmonic
 // -2Y_lm(theta, phi) = S_lm(theta) e^{i m phi} with
 // S_lm = (-1)^s sqrt((2l+1)/4pi) d^l_{m,-s}(theta), s = -2, and the Wigner
-// small-d sum (1/k! from a table of exact-as-possible constants, k <= 40)  d^l_{a,b}(x) = sum_k (-1)^{a-b+k} sqrt((l+a)!(l-a)!(l+b)!(l-b)!)
+// small-d sum (1/k! from a table of the nearest doubles, k <= 40)  d^l_{a,b}(x) = sum_k (-1)^{a-b+k} sqrt((l+a)!(l-a)!(l+b)!(l-b)!)
 //   / ((l+b-k)! k! (a-b+k)! (l-a-k)!) cos^{2l+b-a-2k}(x/2) sin^{a-b+2k}(x/2).
-__constant__ double c_invfact[41] = {1.0, 1.0, 0.5, 0.16666666666666666, 0.041666666666666664, 0.008333333333333333, 0.001388888888888889, 0.0001984126984126984, 2.48015873015873e-05, 2.7557319223985893e-06, 2.755731922398589e-07, 2.505210838544172e-08, 2.08767569878681e-09, 1.6059043836821613e-10, 1.1470745597729725e-11, 7.647163731819816e-13, 4.779477332387385e-14, 2.8114572543455206e-15, 1.5619206968586225e-16, 8.22063524662433e-18, 4.110317623312165e-19, 1.9572941063391263e-20, 8.896791392450574e-22, 3.8681701706306835e-23, 1.6117375710961184e-24, 6.446950284384474e-26, 2.4795962632247972e-27, 9.183689863795546e-29, 3.279889237069838e-30, 1.1309962886447718e-31, 3.7699876288159054e-33, 1.2161250415535181e-34, 3.800390754854744e-36, 1.151633562077195e-37, 3.387157535521162e-39, 9.67759295863189e-41, 2.688220266286636e-42, 7.265460179153071e-44, 1.911963205040282e-45, 4.902469756513544e-47, 1.225617439128386e-48};
+__constant__ double c_invfact[41] = {1.0, 1.0, 0.5, 0.16666666666666666, 0.041666666666666664, 0.008333333333333333, 0.001388888888888889, 0.0001984126984126984, 2.48015873015873e-05, 2.7557319223985893e-06, 2.755731922398589e-07, 2.505210838544172e-08, 2.08767569878681e-09, 1.6059043836821613e-10, 1.1470745597729725e-11, 7.647163731819816e-13, 4.779477332387385e-14, 2.8114572543455206e-15, 1.5619206968586225e-16, 8.22063524662433e-18, 4.110317623312165e-19, 1.9572941063391263e-20, 8.896791392450574e-22, 3.868170170630684e-23, 1.6117375710961184e-24, 6.446950284384474e-26, 2.4795962632247976e-27, 9.183689863795546e-29, 3.279889237069838e-30, 1.1309962886447716e-31, 3.7699876288159054e-33, 1.216125041553518e-34, 3.8003907548547434e-36, 1.151633562077195e-37, 3.387157535521162e-39, 9.67759295863189e-41, 2.6882202662866363e-42, 7.265460179153071e-44, 1.911963205040282e-45, 4.902469756513544e-47, 1.2256174391283858e-48};
 
 __device__ __forceinline__ double ipow(double x, int n) {
   double r = 1.0;
