@@ -58,7 +58,7 @@
 #endif
 
 #define OR_TWO_PI_HI 6.283185307179586232
-#define OR_TWO_PI_LO 2.449293598294706e-16
+#define OR_TWO_PI_LO 2.4492935982947064e-16
 #define OR_QPI_HI 0.7853981633974483096
 #define OR_QPI_LO 3.061616997868383e-17
 #define OR_PI 3.14159265358979323846

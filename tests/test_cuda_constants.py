@@ -101,3 +101,17 @@ def test_reciprocal_factorials():
     assert len(vals) == 41
     for k, v in enumerate(vals):
         assert v == float(1 / mp.factorial(k)), k
+
+
+def test_oracle_constants():
+    """The oracle's double-double 2 pi and pi/4 (its phase is carried to ~1e-32 of a
+    turn before reduction) and pi; an error in a low word would sit far below its pins."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    with open(os.path.join(os.path.dirname(CSRC), "..", "oracle", "oracle.c")) as fh:
+        src = fh.read()
+    d = {k: float(v) for k, v in re.findall(r"#define (OR_[A-Z_]+) ([-0-9.e+]+)", src)}
+    for name, value in (("TWO_PI", 2 * mp.pi), ("QPI", mp.pi / 4)):
+        hi, lo = d["OR_%s_HI" % name], d["OR_%s_LO" % name]
+        assert hi == float(value) and lo == float(value - mp.mpf(hi)), name
+    assert d["OR_PI"] == float(mp.pi)
