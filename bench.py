@@ -11,7 +11,9 @@ working set (~200 MB) exceeds the 129 MB L2.
 Metric: waveforms/s (whole job; with N ranks each rank sums its own
 waveforms, weak scaling), plus mode-bin evaluations/s.
 `--impl reference` times the CPU oracle instead (bounded samples of the
-same workload, extrapolated).  See the design doc for the roofline arithmetic.
+same workload, extrapolated).  Roofline: the headline kernel's algorithmic FP64
+work (FP64_FLOPS_PER_MODE_BIN per mode-bin) over its event-timed duration, against
+2 FP64 FMA/clk/SM x 2 flops x SMs x the median sampled SM clock.
 """
 from __future__ import annotations
 
