@@ -180,7 +180,8 @@ __device__ __forceinline__ double neg_half_normal(double x) {
 // w e^{2 pi i Th/2^64}: the table entry T_k = e^{2 pi i k/65536} nearest Th, times
 // w (1 - x^2/2 + i x) with x = 2 pi (Th/2^64 - k/65536), |x| <= pi/65536.  The
 // omitted terms of e^{ix} are below |x|^3/6 = 1.9e-14; the real factor w enters
-// the two-term factor without a separate multiply (8 FP64 instructions in all)
+// the two-term factor without a separate multiply (7 FP64 instructions in all).
+// The extended form and the adjoint use it: both need w apart from the factor.
 __device__ __forceinline__ void cis_w_q64(unsigned long long Th, const double2* tab, double w, double& er,
                                           double& ei) {
   const unsigned long long kq = (Th + (1ull << (63 - kTab64Bits))) >> (64 - kTab64Bits);
