@@ -310,7 +310,7 @@ emri_fd_status emri_fd_profile(emri_fd_plan_t plan, int enable);
  * synchronise the device), and plug-ins or callbacks that must not call the
  * allocator.  It calls no cudaMalloc, cudaFree or other allocating routine:
  * all scratch lives in one file-scope __device__ array of 7,555,328 bytes
- * (6.2 MiB), which every GPU that loads the library holds until the process
+ * (7.2 MiB), which every GPU that loads the library holds until the process
  * exits.
  *   Limits: n_knots in [4, EMRI_FD_NOALLOC_MAX_KNOTS], n_modes in
  *   [1, EMRI_FD_NOALLOC_MAX_MODES], n_freqs in [1, EMRI_FD_NOALLOC_MAX_BINS];
