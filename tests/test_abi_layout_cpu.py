@@ -1,7 +1,8 @@
-"""The ctypes binding agrees with include/emri_fd.h: a small C program compiled
+"""The ctypes binding agrees with include/emri_fd.h.  A small C program compiled
 against the header prints the descriptor's size and field offsets and the values
 of the status, precision, SPA-form and window enums, and the binding's
-definitions must match them.  CPU only (gcc, no CUDA)."""
+definitions must match them; and every prototype, parsed from the preprocessed
+header, matches the binding's argtypes and restype.  CPU only (gcc, no CUDA)."""
 import ctypes as C
 import os
 import shutil
@@ -63,3 +64,59 @@ def test_enum_values(header_values):
     assert header_values["EMRI_FD_SPA_EXTENDED"] == api.SPA_FORMS["extended"]
     assert header_values["EMRI_FD_WINDOW_NONE"] == api.WINDOWS[None]
     assert header_values["EMRI_FD_WINDOW_HANN"] == api.WINDOWS["hann"]
+
+
+def _c_kind(node):
+    """Class of a pycparser type node: "ptr", "int", "ll", "double", "void"."""
+    from pycparser import c_ast
+    if isinstance(node, c_ast.PtrDecl):
+        return "ptr"
+    if isinstance(node, c_ast.TypeDecl) and isinstance(node.type, c_ast.IdentifierType):
+        names = node.type.names
+        if names in (["emri_fd_plan_t"], ["emri_fd_graph_t"]):
+            return "ptr"   # typedefs of pointers
+        if names in (["int"], ["emri_fd_status"]):
+            return "int"
+        if names == ["long", "long"]:
+            return "ll"
+        if names == ["double"]:
+            return "double"
+        if names == ["void"]:
+            return "void"
+    raise AssertionError("unhandled type %r" % node)
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return "void"
+    if t in (C.c_void_p, C.c_char_p) or (isinstance(t, type) and issubclass(t, C._Pointer)):
+        return "ptr"
+    return {C.c_int: "int", C.c_longlong: "ll", C.c_double: "double"}[t]
+
+
+def test_function_signatures_match_argtypes():
+    """Every exported prototype in the header against the binding's argtypes and
+    restype, parameter by parameter (pointer / int / long long / double)."""
+    pycparser = pytest.importorskip("pycparser")
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    try:
+        L = api.lib()
+    except (OSError, RuntimeError) as e:
+        pytest.skip("library not built: %s" % e)
+    text = subprocess.check_output(["gcc", "-E", "-P", "-std=c11", os.path.join(ROOT, "include", "emri_fd.h")],
+                                   text=True)
+    ast = pycparser.CParser().parse(text)
+    protos = {}
+    for ext in ast.ext:
+        if type(ext).__name__ == "Decl" and type(ext.type).__name__ == "FuncDecl":
+            f = ext.type
+            params = [] if f.args is None else [p.type for p in f.args.params]
+            if len(params) == 1 and _c_kind(params[0]) == "void":
+                params = []
+            protos[ext.name] = (_c_kind(f.type), [_c_kind(p) for p in params])
+    assert set(protos) == set(api.EXPORTS)
+    for name, (ret, params) in protos.items():
+        fn = getattr(L, name)
+        assert [_ctypes_kind(t) for t in fn.argtypes] == params, name
+        assert _ctypes_kind(fn.restype) == ret, name
