@@ -379,6 +379,24 @@ void emri_fd_plan_destroy(emri_fd_plan_t plan);
 /* Static, human-readable name of a status code. */
 const char* emri_fd_strerror(emri_fd_status status);
 
+/*
+ * Peak-rate probe of the fused multiply-add pipes (a measurement utility; the
+ * paper has no counterpart).  It gives the denominator against which the SPA
+ * kernels' FP64 and FP32 roofline fractions are quoted.  Launches one kernel
+ * on `stream` (a cudaStream_t on the current device; NULL = legacy default
+ * stream) in which every thread of blocks_per_sm x SMs blocks of 256 threads
+ * runs 8 independent FMA chains of iters x 16 steps each; the caller times the
+ * launch (e.g. with CUDA events on that stream).
+ *   precision: 0 = FP64 (DFMA), 1 = FP32 (FFMA);
+ *   iters >= 1; blocks_per_sm in [1, 64];
+ *   fma_per_launch: if not NULL, receives the FMAs one launch executes
+ *     (blocks x 256 x iters x 128), each 2 flops.
+ * Allocates nothing.  EMRI_FD_ERR_ARG for bad arguments, EMRI_FD_ERR_CUDA if
+ * the launch fails.
+ */
+emri_fd_status emri_fd_fma_probe(int precision, int iters, int blocks_per_sm, void* stream,
+                                 long long* fma_per_launch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ STATUS = {0: "EMRI_FD_OK", 1: "EMRI_FD_ERR_ARG", 2: "EMRI_FD_ERR_KNOTS", 3: "EMR
 EXPORTS = ("emri_fd_plan", "emri_fd_sum_modes", "emri_fd_loglike_and_grad", "emri_fd_sync", "emri_fd_stats",
            "emri_fd_profile", "emri_fd_plan_destroy", "emri_fd_strerror", "emri_fd_sum_modes_noalloc",
            "emri_fd_set_tile", "emri_fd_set_tile_split", "emri_fd_capture", "emri_fd_replay", "emri_fd_graph_destroy",
-           "emri_fd_select_modes", "emri_fd_td_sum", "emri_fd_td_spectrum")
+           "emri_fd_select_modes", "emri_fd_td_sum", "emri_fd_td_spectrum", "emri_fd_fma_probe")
 
 
 class EmriFdError(RuntimeError):
@@ -94,6 +94,8 @@ def lib():
         L.emri_fd_plan_destroy.restype = None
         L.emri_fd_strerror.argtypes = [C.c_int]
         L.emri_fd_strerror.restype = C.c_char_p
+        L.emri_fd_fma_probe.argtypes = [C.c_int, C.c_int, C.c_int, vp, C.POINTER(C.c_longlong)]
+        L.emri_fd_fma_probe.restype = C.c_int
         _lib = L
     return _lib
 
@@ -216,6 +218,15 @@ def emri_fd_td_spectrum(plan, n_waveforms, sample_off, t0, dt, window, h_plus, h
 
 def emri_fd_plan_destroy(plan) -> None:
     lib().emri_fd_plan_destroy(C.c_void_p(plan))
+
+
+def emri_fd_fma_probe(precision, iters, blocks_per_sm, stream=0):
+    """Launch the FMA peak probe (precision 0 = FP64, 1 = FP32) on a raw stream
+    handle; returns the FMAs the launch executes.  The caller times it."""
+    n = C.c_longlong(0)
+    _check(lib().emri_fd_fma_probe(int(precision), int(iters), int(blocks_per_sm), C.c_void_p(int(stream)),
+                                   C.byref(n)), "emri_fd_fma_probe")
+    return n.value
 
 
 # ---------------------------------------------------------------- wrapper

@@ -17,8 +17,10 @@ Units: seconds, rad, rad/s, Hz.  Every random draw comes from
 """
 from __future__ import annotations
 
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 import math
+import os
 
 import numpy as np
 
@@ -233,17 +235,31 @@ def batch_config(n_waveforms: int = 256, seed0: int = 100, max_bins: float = 6e6
     """Batched workload: waveform i uses seed seed0 + i.  Per waveform, draw order:
     N_m ~ U{mode_range}, T ~ U(T_range) yr, N_f = round(exp(U(ln min_bins, ln max_bins))),
     grid kind ~ Bernoulli(1/2) (uniform or log-spaced over [1/T, 0.05]);
-    then ``paper_config``'s draws with its own generator seeded seed0 + i."""
-    out = []
-    for i in range(n_waveforms):
+    then ``paper_config``'s draws with its own generator seeded seed0 + i.
+    Waveforms are made on a thread pool; each uses only its own generators, so the
+    result does not depend on the pool."""
+    def one(i):
         r = np.random.default_rng(seed0 + i)
         nm = int(r.integers(mode_range[0], mode_range[1] + 1))
         Ty = float(r.uniform(*T_range))
         nf = int(round(math.exp(r.uniform(math.log(min_bins), math.log(max_bins)))))
         kind = "uniform" if r.uniform() < 0.5 else "sparse"
-        w = paper_config(seed0 + i, n_modes=nm, T_years=Ty, K=K, grid=kind, n_sparse=nf, n_bins=nf)
-        out.append(w)
-    return out
+        return paper_config(seed0 + i, n_modes=nm, T_years=Ty, K=K, grid=kind, n_sparse=nf, n_bins=nf)
+    return _pool_map(one, range(n_waveforms))
+
+
+def paper_configs(seeds, **kw):
+    """``paper_config(s, **kw)`` for every seed, made on a thread pool (numpy releases
+    the GIL in its array loops); identical to the serial list."""
+    return _pool_map(lambda s: paper_config(s, **kw), seeds)
+
+
+def _pool_map(fn, items):
+    items = list(items)
+    if len(items) <= 1:
+        return [fn(i) for i in items]
+    with ThreadPoolExecutor(max_workers=min(len(items), os.cpu_count() or 1, 16)) as ex:
+        return list(ex.map(fn, items))
 
 
 def psd(f):
