@@ -76,7 +76,11 @@ typedef enum {
   EMRI_FD_ERR_CAPACITY = 6,   /* a size above the plan's maxima, or branch storage exhausted */
   EMRI_FD_ERR_CUDA = 7,       /* a CUDA runtime call failed */
   EMRI_FD_ERR_OOM = 8,        /* device allocation failed */
-  EMRI_FD_ERR_TIMEOUT = 9     /* a bounded device wait ran out */
+  EMRI_FD_ERR_TIMEOUT = 9     /* reserved for a bounded device wait that runs out.  No kernel of
+                                 this version waits on a flag, a peer or another CTA's progress
+                                 (work is claimed with atomics, and thread-block cluster barriers
+                                 are reached by every member the same number of times), so no
+                                 call returns it. */
 } emri_fd_status;
 
 enum { EMRI_FD_FP64 = 0, EMRI_FD_MIXED = 1, EMRI_FD_FP64X = 2 };
@@ -321,7 +325,10 @@ emri_fd_status emri_fd_profile(emri_fd_plan_t plan, int enable);
  *   EMRI_FD_ERR_ARG).  stream: a cudaStream_t on the current device.
  *   Set-up: the first call on a device (with that device current) looks up the
  *   array's device address and fills a sin/cos table in it; make that first
- *   call before any stream capture.
+ *   call before any stream capture.  The set-up is kept per device ordinal for
+ *   the life of the process: it does not survive cudaDeviceReset (or any other
+ *   teardown of the device's primary context), after which this entry point
+ *   must not be called again in that process.
  *   The call waits for its stream and returns the status of the device-side
  *   checks.  Every call uses the same array and overwrites the previous
  *   call's contents; calls whose GPU work overlaps in time (e.g. from two host

@@ -515,12 +515,19 @@ def _autograd_function():
             bb.update(phi_phi=phi_phi.detach(), phi_r=phi_r.detach(), omega_phi=omega_phi.detach(),
                       omega_r=omega_r.detach(), amp=amp.detach())
             L, _ = plan.loglike_and_grad(bb, data_plus, data_cross, psd, df, grad=False)
-            ctx.plan, ctx.b, ctx.data = plan, bb, (data_plus, data_cross, psd, df)
+            # the knot tensors go through save_for_backward, so that autograd's version
+            # counters reject a backward after any of them was modified in place
+            ctx.save_for_backward(phi_phi, phi_r, omega_phi, omega_r, amp)
+            ctx.plan, ctx.b, ctx.data = plan, b, (data_plus, data_cross, psd, df)
             return L.sum()
 
         @staticmethod
         def backward(ctx, gL):
-            _, g = ctx.plan.loglike_and_grad(ctx.b, *ctx.data, grad=True)
+            phi_phi, phi_r, omega_phi, omega_r, amp = ctx.saved_tensors
+            bb = dict(ctx.b)
+            bb.update(phi_phi=phi_phi.detach(), phi_r=phi_r.detach(), omega_phi=omega_phi.detach(),
+                      omega_r=omega_r.detach(), amp=amp.detach())
+            _, g = ctx.plan.loglike_and_grad(bb, *ctx.data, grad=True)
             ga = torch.view_as_real(g["amp"]).reshape(-1)
             return (None, None, None, None, None, None, gL * g["phi_phi"], gL * g["phi_r"], gL * g["omega_phi"],
                     gL * g["omega_r"], gL * ga)

@@ -34,9 +34,10 @@ constexpr int kTab64Bits = 16;            // FP64 table e^{2 pi i k / 65536} (FP
 constexpr int kTab64N = 1 << kTab64Bits;
 constexpr int kListCap = 2048;            // (run, sign) entries buffered per tile pass
 
-// status bits latched in the plan's device status word
+// status bits latched in the plan's device status word (no kernel of this library
+// waits on a flag, a peer or a barrier it does not own, so none has a timeout bit)
 enum : int {
-  ST_KNOTS = 1, ST_FREQ = 2, ST_MODE = 4, ST_NONFINITE = 8, ST_CAPACITY = 16, ST_TIMEOUT = 32
+  ST_KNOTS = 1, ST_FREQ = 2, ST_MODE = 4, ST_NONFINITE = 8, ST_CAPACITY = 16
 };
 
 struct WfInfo {

@@ -142,3 +142,24 @@ def test_autograd_function(oracle):
         assert torch.equal(b[k].grad, 2.5 * g[k])
     assert torch.equal(b["amp"].grad, 2.5 * torch.view_as_real(g["amp"]).reshape(-1))
     plan.close()
+
+
+def test_autograd_rejects_knots_changed_in_place(oracle):
+    """The knot tensors are saved for backward: changing one in place between the forward
+    and backward passes makes autograd raise instead of returning a stale gradient."""
+    w, d = _case(oracle, synth.small_config(0, n_bins=2048))
+    plan = api.Plan("fp64", max_waveforms=1, max_knots=w.K, max_modes_total=w.n_modes, max_bins_total=w.n_freqs,
+                    likelihood=True)
+    b = plan.upload(synth.concat([w]))
+    for k in ("phi_phi", "phi_r", "omega_phi", "omega_r", "amp"):
+        b[k].requires_grad_(True)
+    dev = plan.device
+    dp, dc = (torch.as_tensor(x).to(dev) for x in d[:2])
+    S = torch.as_tensor(d[2]).to(dev)
+    df = torch.tensor([d[3]], dtype=torch.float64, device=dev)
+    L = api.whittle_loglike(plan, b, dp, dc, S, df)
+    with torch.no_grad():
+        b["omega_r"].mul_(1.0 + 1e-9)
+    with pytest.raises(RuntimeError):
+        L.backward()
+    plan.close()

@@ -14,6 +14,7 @@ from tests import test_oracle_closed_form as CF
 from tests import test_oracle_ext as EXT
 from tests import test_oracle_fft as FFT
 from tests import test_oracle_grad as GRAD
+from tests import test_oracle_mismatch as MM
 from tests import test_oracle_invariants as INV
 from tests import test_oracle_select as SEL
 from tests import test_oracle_spline as SPL
@@ -87,6 +88,10 @@ MUTANTS = [
      "else { Wr = 0.5 * (Gb[0] + Gb[3]); Wi = 0.5 * (Gb[1] + Gb[2]); }"),
     ("Phi_r chain rule uses m", "c", "grad", "gcf[1 * sc + 4 * k + q] += (double)V->n * a[4 + q];",
      "gcf[1 * sc + 4 * k + q] += (double)V->m * a[4 + q];"),
+    # inner product and mismatch (Eq. 12-13)
+    ("inner product multiplies by the PSD", "py", "mismatch", "np.sum(np.conj(a) * b / psd)", "np.sum(np.conj(a) * b * psd)"),
+    ("inner product without the conjugate", "py", "mismatch", "np.sum(np.conj(a) * b / psd)", "np.sum(a * b / psd)"),
+    ("mismatch summed over the channels", "py", "mismatch", "return 1.0 - out / len(a_pair)", "return 1.0 - out"),
 ]
 
 # the pins run on each mutant: (group, name, call)
@@ -113,6 +118,10 @@ BATTERY = [
     ("grad", "likelihood definition", lambda O: GRAD.test_loglike_definition(O)),
     ("grad", "Euler identity", lambda O: GRAD.test_euler_identity_amplitudes(O)),
     ("grad", "phase offset identities", lambda O: [GRAD.test_phase_offset_identity(O, x) for x in ("phi_phi", "phi_r")]),
+    ("mismatch", "inner product", lambda O: MM.test_inner_is_4_df_re_sum_over_psd(O)),
+    ("mismatch", "phase rotation", lambda O: [MM.test_phase_rotation(O, x) for x in (0.4, 2.0)]),
+    ("mismatch", "PSD weighting", lambda O: MM.test_psd_weighting(O, 4.0)),
+    ("mismatch", "identical signals", lambda O: MM.test_identical_and_scaled(O)),
     ("grad", "central differences", lambda O: [GRAD.test_central_differences(O, x, h) for x, h in
                                                (("phi_phi", 3e-5), ("phi_r", 3e-5), ("omega_phi", 1e-8),
                                                 ("omega_r", 1e-8), ("amp", 1e-4))]),

@@ -6,8 +6,9 @@ keeps its scratch in a fixed file-scope device array instead of a plan.  This
 test calls it through the C ABI twice in a row, on two different waveforms (so
 the second call starts from the first call's leftovers in the shared array),
 and compares each result with the plan-based emri_fd_sum_modes, within the
-FP64 parity tolerance (relative L2 1e-10).  It also checks the size limit.
-The file name makes pytest collect it last."""
+FP64 parity tolerance (relative L2 1e-10).  It also checks the size limit and
+that a call leaves the device's free memory unchanged.  The file name makes
+pytest collect it last."""
 import numpy as np
 import pytest
 
@@ -28,20 +29,33 @@ def _gpu():
     build.build()
 
 
-def _noalloc(w, conj=True):
+def _inputs(w):
+    """Device copies of the waveform's arrays and the two outputs (made by torch, before
+    the entry point is called)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     d = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a, dt)).to(dev)
-    t, pp, pr, op, orr = (d(getattr(w, k), np.float64) for k in ("t", "phi_phi", "phi_r", "omega_phi", "omega_r"))
-    l, m, n = (d(getattr(w, k), np.int32) for k in ("l", "m", "n"))
-    amp = d(np.ascontiguousarray(w.amp, np.complex128).view(np.float64), np.float64)
-    f = d(w.freqs, np.float64)
+    arrs = [d(getattr(w, k), np.float64) for k in ("t", "phi_phi", "phi_r", "omega_phi", "omega_r")]
+    arrs += [d(getattr(w, k), np.int32) for k in ("l", "m", "n")]
+    arrs.append(d(np.ascontiguousarray(w.amp, np.complex128).view(np.float64), np.float64))
+    arrs.append(d(w.freqs, np.float64))
     hp = torch.empty(w.n_freqs, dtype=torch.complex128, device=dev)
     hc = torch.empty(w.n_freqs, dtype=torch.complex128, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    code = api.emri_fd_sum_modes_noalloc(int(conj), w.K, w.n_modes, w.n_freqs, t.data_ptr(), pp.data_ptr(),
+    return arrs, hp, hc
+
+
+def _call(w, arrs, hp, hc, conj=True):
+    """One call of the entry point through the C ABI; returns its status."""
+    t, pp, pr, op, orr, l, m, n, amp, f = arrs
+    stream = torch.cuda.current_stream(hp.device)
+    return api.emri_fd_sum_modes_noalloc(int(conj), w.K, w.n_modes, w.n_freqs, t.data_ptr(), pp.data_ptr(),
                                          pr.data_ptr(), op.data_ptr(), orr.data_ptr(), l.data_ptr(), m.data_ptr(),
                                          n.data_ptr(), amp.data_ptr(), w.theta, w.phi, w.prefactor, f.data_ptr(),
                                          hp.data_ptr(), hc.data_ptr(), stream.cuda_stream)
+
+
+def _noalloc(w, conj=True):
+    arrs, hp, hc = _inputs(w)
+    code = _call(w, arrs, hp, hc, conj)
     return code, hp.cpu().numpy(), hc.cpu().numpy()
 
 
@@ -60,3 +74,22 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     w = synth.paper_config(7, n_modes=129, T_years=0.5, grid="sparse", n_sparse=1000)
     code, _, _ = _noalloc(w)
     assert code == 6   # EMRI_FD_ERR_CAPACITY
+
+
+def test_noalloc_allocates_no_device_memory():
+    """The property the entry point exists for: once its first call on the device has
+    done the set-up, a call leaves the device's free memory (cudaMemGetInfo) unchanged.
+    The inputs and outputs are made beforehand, and the call is repeated once first so
+    that every kernel it launches has been loaded."""
+    w = synth.paper_config(8, n_modes=100, T_years=0.5, grid="uniform", n_bins=40000)
+    arrs, hp, hc = _inputs(w)
+    assert _call(w, arrs, hp, hc) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    code = _call(w, arrs, hp, hc)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert code == 0, api.emri_fd_strerror(code)
+    assert free1 == free0, (free0, free1)
+    rp, rc = run(w)
+    assert rel_l2(hp.cpu().numpy(), rp) <= TOL64 and rel_l2(hc.cpu().numpy(), rc) <= TOL64
