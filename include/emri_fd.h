@@ -204,6 +204,11 @@ emri_fd_status emri_fd_sum_modes(emri_fd_plan_t plan, int n_waveforms,
  * at the input's (L is only piecewise smooth in the frequency knots: a bin
  * changes segment when a knot frequency crosses it).  Roots t(f) are
  * recomputed in the adjoint pass, with the same arithmetic as the forward pass.
+ * Every sum has a fixed order, so a call is repeatable bit for bit.  loglike is
+ * summed per waveform and equals the single-waveform call bitwise; the
+ * gradient's bins are spread evenly over the GPU's lanes by their position in
+ * the whole call, so a waveform's gradient in a batch differs from its
+ * single-waveform value in the last bits.
  * Needs an FP64 plan created with likelihood = 1 (else EMRI_FD_ERR_ARG).
  * Pointers may be device or host memory (host: staged, and the call syncs).
  */

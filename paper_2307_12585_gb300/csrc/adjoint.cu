@@ -97,6 +97,16 @@ __device__ __forceinline__ long long first_true(long long lo, long long hi, P pr
   return lo;
 }
 
+// One adjoint item: a (run, segment) pair, with the bins of both branch signs that it
+// covers and per-segment constants of its derivatives
+struct __align__(16) AdjItem {
+  int run, s, piece, pad;
+  int lo_p, hi_p, lo_n, hi_n;            // global bins [lo, hi) of the positive / negative branch
+  double a3r, a2r, a3i, a2i;             // 3 re_3, 2 re_2, 3 im_3, 2 im_2 of the amplitude record (dA/du)
+  double d2c, p2c, p3c, pad2;            // 2 (3d) = d^2F/du^2 slope, 2 P2, 3 P3 (dPhi_V/du)
+};
+static_assert(sizeof(AdjItem) == 96, "AdjItem layout");
+
 struct AdjParams {
   const WfInfo* wf;
   const ModeInfo* modes;
@@ -110,60 +120,50 @@ struct AdjParams {
   const dbl4* G;
   const int* item_off;     // exclusive scan of items per run, total at [run_cap]
   long long run_cap;
+  AdjItem* items;          // [item_cap]
+  long long* adj_off;      // [item_cap + 1] exclusive scan of the items' bin counts (the bin stream)
+  long long item_cap;
+  double* bnd;             // [warps][2][16]
+  int* bnd_id;             // [warps][2]
   const double2* tab;      // e^{2 pi i k/65536}
   double* slots;           // [3 * seg_total][16]
   const int* status;
 };
 
-// last r in [0, n) with off[r] <= it, for ascending off with off[0] <= it: one warp,
-// all lanes with the same it, 32 probes per round (the probes that pass are a prefix)
-__device__ __forceinline__ long long last_le_warp(const int* off, long long n, long long it, int lane) {
-  long long base = 0, len = n;   // answer in [base, base + len); off[base] <= it
-  while (len > 1) {
-    const long long step = (len + 31) >> 5;
-    const long long p = base + lane * step;
-    const bool ok = p < base + len && off[p] <= it;
-    const int c = 31 - __clz(__ballot_sync(0xffffffffu, ok));   // lane 0 probes base, so c >= 0
-    base += c * step;
-    len = min(step, len - c * step);
+// last r in [0, n) with off[r] <= it, for ascending off with off[0] <= it (one thread)
+template <typename T>
+__device__ __forceinline__ long long last_le(const T* off, long long n, long long it) {
+  long long lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const long long mid = (lo + hi + 1) >> 1;
+    if ((long long)off[mid] <= it) lo = mid; else hi = mid - 1;
   }
-  return base;
+  return lo;
 }
 
-__global__ void __launch_bounds__(256, 2) k_adjoint(AdjParams P) {
-  if (*P.status != 0) return;
-  const int lane = threadIdx.x & 31;
+// items: one thread per item slot; the run and segment of the item, the bins it
+// covers (knot s passed for s > s0, knot s + 1 not passed for s < s1, as the output
+// kernel assigns them), its sub-piece and the per-segment constants.  Slots past
+// the item count get zero bins.
+__global__ void k_adj_items(AdjParams P) {
+  const long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (it >= P.item_cap) return;
   const long long nitems = P.item_off[P.run_cap];
-  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long it = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; it < nitems; it += wstride) {
-    // run of this item: last r with item_off[r] <= it (32 probes per round)
-    const long long r = last_le_warp(P.item_off, P.run_cap, it, lane);
-    const Run R = P.runs[r];
-    const int s = R.s0 + (int)(it - P.item_off[r]);
-    const RunBins B = P.rb[r];
-    const ModeInfo M = P.modes[R.mode];
-    const WfInfo W = P.wf[M.wf];
-    const SegCore C = P.core[M.seg_base + s];
-    const SegAmp64 Am = P.amp64[M.seg_base + s];   // times M.scale
-    // alpha, beta over the record's scale (one is 1); the amplitude sums are multiplied
-    // back by the scale in k_seg_sum
-    const bool amaj = alpha_major(M.alpha, M.beta);
-    const double ap = amaj ? 1.0 : M.rho, bp = amaj ? M.rho : 1.0;
-    const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
-    // per-segment constants of dA/du, d2F/du2 and dPhi_V/du
-    const double a3r = 3.0 * Am.re[3], a2r = 2.0 * Am.re[2], a3i = 3.0 * Am.im[3], a2i = 2.0 * Am.im[2];
-    const double d2c = 2.0 * C.d3, p2c = 2.0 * C.P2, p3c = 3.0 * C.P3;
-    // acc[0..3]: sum tD u^k (k = 0..3), combined with hsum after the loop into the
-    // frequency-coefficient derivatives sum (tD u^k + k hD u^(k-1)); acc[4..7] phase,
-    // acc[8..15] amplitude coefficients
-    double acc[16], hsum[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int q = 0; q < 16; q++) acc[q] = 0.0;
-    for (int sg = 0; sg < 2; sg++) {
-      const bool neg = sg == 1;
-      long long b0 = neg ? B.b0n : B.b0p, b1 = neg ? B.b1n : B.b1p;
-      if (b0 >= b1) continue;
-      // bins of this segment: knot s passed (s > s0) and knot s+1 not passed (s < s1)
+  // after a failed input check the run lists are not valid: no bins at all
+  if (it >= nitems || *P.status != 0) { P.adj_off[it] = 0; return; }
+  const long long r = last_le(P.item_off, P.run_cap, it);
+  const Run R = P.runs[r];
+  const int s = R.s0 + (int)(it - P.item_off[r]);
+  const RunBins B = P.rb[r];
+  const ModeInfo M = P.modes[R.mode];
+  AdjItem I;
+  I.run = (int)r; I.s = s; I.pad = 0;
+  int lo[2], hi[2];
+  for (int sg = 0; sg < 2; sg++) {
+    const bool neg = sg == 1;
+    const long long b0 = neg ? B.b0n : B.b0p, b1 = neg ? B.b1n : B.b1p;
+    long long lo_b = b0, hi_b = b1;
+    if (b0 < b1) {
       auto passed = [&](int k, long long b) {
         const double f = P.freqs[b];
         const long long key = ordkey(neg ? flip_sign(f) : f);
@@ -171,7 +171,6 @@ __global__ void __launch_bounds__(256, 2) k_adjoint(AdjParams P) {
         return R.dir > 0 ? (kk <= key) : (kk >= key);
       };
       const bool suffix = (R.dir > 0) != neg;   // passed(k, b) holds on a suffix of the bins
-      long long lo_b = b0, hi_b = b1;
       if (s > R.s0) {
         long long x = first_true(b0, b1, [&](long long b) { return suffix ? passed(s, b) : !passed(s, b); });
         if (suffix) lo_b = x; else hi_b = x;
@@ -180,87 +179,262 @@ __global__ void __launch_bounds__(256, 2) k_adjoint(AdjParams P) {
         long long x = first_true(b0, b1, [&](long long b) { return suffix ? passed(s + 1, b) : !passed(s + 1, b); });
         if (suffix) hi_b = min(hi_b, x); else lo_b = max(lo_b, x);
       }
-      for (long long b = lo_b + lane; b < hi_b; b += 32) {
-        const double g = neg ? flip_sign(P.freqs[b]) : P.freqs[b];
-        const double delta = g - C.A;
-        float uf, Df;
-        const double u = solve_root<6>(C, delta, ulo, uhi, R.dir, uf, Df);
-        const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
-        const long long Dbits = __double_as_longlong(Dd);
-        if (is_zero_bits(Dd)) continue;
-        const unsigned long long Th = phase_q64(C, g, delta, u, Dbits >= 0);
-        const double wgt = rsqrt_abs(Dd);
-        double Er, Ei;
-        cis_w_q64(Th, P.tab, wgt, Er, Ei);                    // E = |D|^{-1/2} e^{i psi}
-        const double Ar = fma(u, fma(u, fma(u, Am.re[3], Am.re[2]), Am.re[1]), Am.re[0]);
-        const double Ai = fma(u, fma(u, fma(u, Am.im[3], Am.im[2]), Am.im[1]), Am.im[0]);
-        const double dAr = fma(u, fma(u, a3r, a2r), Am.re[1]);
-        const double dAi = fma(u, fma(u, a3i, a2i), Am.im[1]);
-        const dbl4 Gb = P.G[b];
-        double Qr, Qi;
-        if (!neg) { Qr = ap * Gb.x + bp * Gb.w; Qi = -ap * Gb.y + bp * Gb.z; }
-        else { Qr = ap * Gb.x - bp * Gb.w; Qi = ap * Gb.y + bp * Gb.z; }
-        const double QEr = Qr * Er - Qi * Ei, QEi = Qr * Ei + Qi * Er;
-        const double QZr = QEr * Ar - QEi * Ai, QZi = QEr * Ai + QEi * Ar;
-        const double Dp = fma(d2c, u, C.c2);                  // d^2F/du^2
-        const double dpsi = kTwoPi * fma(-u, fma(p3c, u, p2c), fma(delta, C.h, -C.Q1));  // 2 pi g h - Phi_V'(u)
-        const double w2 = wgt * wgt;                          // 1/|dF/du| from the weight: no FP64 division
-        const double invD = Dbits >= 0 ? w2 : flip_sign(w2);
-        const double hD = -0.5 * QZr * invD;
-        const double T = fma(QEr, dAr, fma(-QEi, dAi, fma(hD, Dp, -QZi * dpsi)));
-        const double tD = -T * invD;
-        const double u2 = u * u, u3 = u2 * u;
-        acc[0] += tD;
-        acc[1] = fma(tD, u, acc[1]);
-        acc[2] = fma(tD, u2, acc[2]);
-        acc[3] = fma(tD, u3, acc[3]);
-        hsum[0] += hD;
-        hsum[1] = fma(hD, u, hsum[1]);
-        hsum[2] = fma(hD, u2, hsum[2]);
-        acc[4] += QZi;
-        acc[5] = fma(u, QZi, acc[5]);
-        acc[6] = fma(u2, QZi, acc[6]);
-        acc[7] = fma(u3, QZi, acc[7]);
-        acc[8] += QEr;
-        acc[9] = fma(u, QEr, acc[9]);
-        acc[10] = fma(u2, QEr, acc[10]);
-        acc[11] = fma(u3, QEr, acc[11]);
-        acc[12] -= QEi;
-        acc[13] = fma(-u, QEi, acc[13]);
-        acc[14] = fma(-u2, QEi, acc[14]);
-        acc[15] = fma(-u3, QEi, acc[15]);
+    }
+    if (hi_b < lo_b) hi_b = lo_b;
+    lo[sg] = (int)lo_b;
+    hi[sg] = (int)hi_b;
+  }
+  I.lo_p = lo[0]; I.hi_p = hi[0]; I.lo_n = lo[1]; I.hi_n = hi[1];
+  // sub-piece of segment s that this run covers
+  int piece = 0;
+  if (s == R.s0) {
+    const SegCrit X = P.crit[M.seg_base + s];
+    for (int c = 0; c < X.n; c++) if (X.u[c] <= R.u0) piece++;
+  }
+  I.piece = piece;
+  const SegAmp64 Am = P.amp64[M.seg_base + s];
+  const SegCore C = P.core[M.seg_base + s];
+  I.a3r = 3.0 * Am.re[3]; I.a2r = 2.0 * Am.re[2]; I.a3i = 3.0 * Am.im[3]; I.a2i = 2.0 * Am.im[2];
+  I.d2c = 2.0 * C.d3; I.p2c = 2.0 * C.P2; I.p3c = 3.0 * C.P3; I.pad2 = 0.0;
+  P.items[it] = I;
+  P.adj_off[it] = (long long)(hi[0] - lo[0]) + (hi[1] - lo[1]);
+}
+
+// exclusive scan of cnt[0..n) in place (int64), total written to cnt[n]; one block
+__global__ void k_scan64(long long* cnt, long long n) {
+  __shared__ long long part[1024];
+  const int tid = threadIdx.x;
+  const long long per = (n + blockDim.x - 1) / blockDim.x;
+  const long long b = tid * per, e = b + per < n ? b + per : n;
+  long long sum = 0;
+  for (long long i = b; i < e; i++) sum += cnt[i];
+  part[tid] = sum;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const long long v = tid >= o ? part[tid - o] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  long long run = part[tid] - sum;
+  for (long long i = b; i < e; i++) { const long long c = cnt[i]; cnt[i] = run; run += c; }
+  if (tid == blockDim.x - 1) cnt[n] = part[tid];
+}
+
+// the adjoint's per-lane state of one item
+struct AdjLane {
+  Run R;
+  SegCore C;
+  SegAmp64 Am;
+  AdjItem I;
+  double ap, bp;           // alpha, beta over the record's scale (one of them is 1)
+  double ulo, uhi;
+  long long seg;           // global (mode, segment) record
+};
+
+__device__ __forceinline__ void adj_load(const AdjParams& P, long long it, AdjLane& L) {
+  L.I = P.items[it];
+  L.R = P.runs[L.I.run];
+  const ModeInfo M = P.modes[L.R.mode];
+  L.seg = M.seg_base + L.I.s;
+  L.C = P.core[L.seg];
+  L.Am = P.amp64[L.seg];   // times M.scale
+  const bool amaj = alpha_major(M.alpha, M.beta);
+  L.ap = amaj ? 1.0 : M.rho;
+  L.bp = amaj ? M.rho : 1.0;
+  L.ulo = (L.I.s == L.R.s0) ? L.R.u0 : 0.0;
+  L.uhi = (L.I.s == L.R.s1) ? L.R.u1 : 1.0;
+}
+
+// The adjoint's bin stream: the bins of every item, item after item (positive branch
+// first), adj_off[i] the position of item i's first bin.  Lane g of the G lanes of the
+// grid takes the contiguous positions [N g/G, N (g + 1)/G), so every lane has the same
+// number of bins (no lane idles at the end of an item) and a lane's bins mostly belong
+// to one item.  Per bin the lane recomputes the forward's root, phase, weight and
+// amplitude (spa_math.cuh) and accumulates the item's 16 coefficient sums in
+// registers.  An item that starts and ends inside a lane is written to its slot by
+// that lane; the first and last item of each lane (which may continue in its
+// neighbours) go to shared memory, where 16 lanes of the warp sum them per item in
+// lane order; items that continue past the warp's range go to the warp's two boundary
+// records, summed in warp order by k_adj_fixup.  Every sum has a fixed order.
+__global__ void __launch_bounds__(32 * kAdjWarpsPerCta, kAdjCtasPerSm) k_adjoint(AdjParams P) {
+  extern __shared__ __align__(16) double adj_smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double* rows = adj_smem + (size_t)wib * 64 * 16;                              // [64][16]
+  int* ids = reinterpret_cast<int*>(adj_smem + (size_t)kAdjWarpsPerCta * 64 * 16) + wib * 64;  // [64]
+  const long long nw = (long long)gridDim.x * kAdjWarpsPerCta;
+  const long long gw = (long long)blockIdx.x * kAdjWarpsPerCta + wib;
+  if (*P.status != 0) {
+    if (lane < 2) P.bnd_id[2 * gw + lane] = -2;
+    return;
+  }
+  const long long N = P.adj_off[P.item_cap];
+  const long long G = 32 * nw, g = 32 * gw + lane;
+  const long long p0 = N / G * g + (N % G) * g / G, p1 = N / G * (g + 1) + (N % G) * (g + 1) / G;
+  const long long wp0 = N / G * (32 * gw) + (N % G) * (32 * gw) / G;
+  const long long wp1 = N / G * (32 * gw + 32) + (N % G) * (32 * gw + 32) / G;
+  ids[2 * lane] = -1;
+  ids[2 * lane + 1] = -1;
+  if (p0 < p1) {
+    // the item holding position p0: the last i with adj_off[i] <= p0 (empty items
+    // before it have the same offset and are skipped by taking the last)
+    long long it = last_le(P.adj_off, P.item_cap, p0);
+    long long it_end = P.adj_off[it + 1];
+    AdjLane L;
+    adj_load(P, it, L);
+    bool first_open = true;
+    double acc[16], hsum[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < 16; q++) acc[q] = 0.0;
+    for (long long pos = p0; pos < p1; pos++) {
+      if (pos >= it_end) {
+        // item it is finished for this lane: its frequency sums combined, then kept for
+        // the warp's combination (the lane's first item) or written (an inner item)
+        acc[1] += hsum[0];
+        acc[2] = fma(2.0, hsum[1], acc[2]);
+        acc[3] = fma(3.0, hsum[2], acc[3]);
+        double* dst;
+        if (first_open) {
+          dst = rows + 2 * lane * 16;
+          ids[2 * lane] = (int)it;
+          first_open = false;
+        } else {
+          dst = P.slots + (L.seg * 3 + L.I.piece) * 16;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; q++) dst[q] = acc[q];
+        do { it++; it_end = P.adj_off[it + 1]; } while (it_end <= pos);
+        adj_load(P, it, L);
+#pragma unroll
+        for (int q = 0; q < 16; q++) acc[q] = 0.0;
+        hsum[0] = hsum[1] = hsum[2] = 0.0;
       }
+      const long long k = pos - P.adj_off[it];
+      const long long np = L.I.hi_p - L.I.lo_p;
+      const bool neg = k >= np;
+      const long long b = neg ? L.I.lo_n + (k - np) : L.I.lo_p + k;
+      const SegCore& C = L.C;
+      const SegAmp64& Am = L.Am;
+      const double g0 = P.freqs[b];
+      const double gg = neg ? flip_sign(g0) : g0;
+      const double delta = gg - C.A;
+      float uf, Df;
+      const double u = solve_root<6>(C, delta, L.ulo, L.uhi, L.I.s == L.R.s0 ? L.R.u0f[0] : 0.f,
+                                     L.I.s == L.R.s1 ? L.R.u1f[0] : 1.f, L.R.dir, uf, Df);
+      const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
+      const long long Dbits = __double_as_longlong(Dd);
+      if (is_zero_bits(Dd)) continue;
+      const unsigned long long Th = phase_q64(C, gg, delta, u, Dbits >= 0);
+      const double wgt = rsqrt_abs(Dd);
+      double Er, Ei;
+      cis_w_q64(Th, P.tab, wgt, Er, Ei);                    // E = |D|^{-1/2} e^{i psi}
+      const double Ar = fma(u, fma(u, fma(u, Am.re[3], Am.re[2]), Am.re[1]), Am.re[0]);
+      const double Ai = fma(u, fma(u, fma(u, Am.im[3], Am.im[2]), Am.im[1]), Am.im[0]);
+      const double dAr = fma(u, fma(u, L.I.a3r, L.I.a2r), Am.re[1]);
+      const double dAi = fma(u, fma(u, L.I.a3i, L.I.a2i), Am.im[1]);
+      const dbl4 Gb = P.G[b];
+      double Qr, Qi;
+      if (!neg) { Qr = L.ap * Gb.x + L.bp * Gb.w; Qi = -L.ap * Gb.y + L.bp * Gb.z; }
+      else { Qr = L.ap * Gb.x - L.bp * Gb.w; Qi = L.ap * Gb.y + L.bp * Gb.z; }
+      const double QEr = Qr * Er - Qi * Ei, QEi = Qr * Ei + Qi * Er;
+      const double QZr = QEr * Ar - QEi * Ai, QZi = QEr * Ai + QEi * Ar;
+      const double Dp = fma(L.I.d2c, u, C.c2);              // d^2F/du^2
+      const double dpsi = kTwoPi * fma(-u, fma(L.I.p3c, u, L.I.p2c), fma(delta, C.h, -C.Q1));  // 2 pi g h - Phi_V'(u)
+      const double w2 = wgt * wgt;                          // 1/|dF/du| from the weight: no FP64 division
+      const double invD = Dbits >= 0 ? w2 : flip_sign(w2);
+      const double hD = -0.5 * QZr * invD;
+      const double T = fma(QEr, dAr, fma(-QEi, dAi, fma(hD, Dp, -QZi * dpsi)));
+      const double tD = -T * invD;
+      const double u2 = u * u, u3 = u2 * u;
+      acc[0] += tD;
+      acc[1] = fma(tD, u, acc[1]);
+      acc[2] = fma(tD, u2, acc[2]);
+      acc[3] = fma(tD, u3, acc[3]);
+      hsum[0] += hD;
+      hsum[1] = fma(hD, u, hsum[1]);
+      hsum[2] = fma(hD, u2, hsum[2]);
+      acc[4] += QZi;
+      acc[5] = fma(u, QZi, acc[5]);
+      acc[6] = fma(u2, QZi, acc[6]);
+      acc[7] = fma(u3, QZi, acc[7]);
+      acc[8] += QEr;
+      acc[9] = fma(u, QEr, acc[9]);
+      acc[10] = fma(u2, QEr, acc[10]);
+      acc[11] = fma(u3, QEr, acc[11]);
+      acc[12] -= QEi;
+      acc[13] = fma(-u, QEi, acc[13]);
+      acc[14] = fma(-u2, QEi, acc[14]);
+      acc[15] = fma(-u3, QEi, acc[15]);
     }
     acc[1] += hsum[0];
     acc[2] = fma(2.0, hsum[1], acc[2]);
     acc[3] = fma(3.0, hsum[2], acc[3]);
-    // fixed-order transposed warp reduction of the 16 sums: at each halving step a
-    // lane keeps half of its values and adds its partner's copy of them, so after
-    // 8 + 4 + 2 + 1 exchanges and a final pair sum, lanes 2q and 2q + 1 hold sum q
-    // (16 shuffles and adds per lane instead of 80)
+    double* dst = rows + (2 * lane + 1) * 16;
 #pragma unroll
-    for (int w = 8; w >= 1; w >>= 1) {
-      const bool upper = (lane & (2 * w)) != 0;   // keeps the upper half of its current values
-#pragma unroll
-      for (int j = 0; j < w; j++) {
-        const double send = upper ? acc[j] : acc[j + w];
-        const double keep = upper ? acc[j + w] : acc[j];
-        acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * w);
-      }
-    }
-    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
-    {
-      // sub-piece of segment s that this run covers
-      int piece = 0;
-      if (s == R.s0) {
-        const SegCrit X = P.crit[M.seg_base + s];
-        for (int c = 0; c < X.n; c++) if (X.u[c] <= R.u0) piece++;
-      }
-      double* dst = P.slots + ((M.seg_base + s) * 3 + piece) * 16;
-      if ((lane & 1) == 0) dst[lane >> 1] = acc[0];
-    }
-    (void)W;
+    for (int q = 0; q < 16; q++) dst[q] = acc[q];
+    ids[2 * lane + 1] = (int)it;
   }
+  __syncwarp();
+  // per item, the lanes' first and last partials in lane order; an item inside the
+  // warp's range is complete, one cut by its start or end goes to a boundary record
+  if (lane < 16) {
+    int cur = -1, nb0 = -1, nb1 = -1;
+    double sum = 0.0;
+    for (int row = 0; row <= 64; row++) {
+      const int id = row < 64 ? ids[row] : -1;
+      if (row < 64 && id < 0) continue;
+      if (id != cur) {
+        if (cur >= 0) {
+          const long long a = P.adj_off[cur], e = P.adj_off[cur + 1];
+          if (a < wp0) {
+            P.bnd[(2 * gw) * 16 + lane] = sum;
+            nb0 = cur;
+          } else if (e > wp1) {
+            P.bnd[(2 * gw + 1) * 16 + lane] = sum;
+            nb1 = cur;
+          } else {
+            const AdjItem I = P.items[cur];
+            const Run R = P.runs[I.run];
+            const long long seg = P.modes[R.mode].seg_base + I.s;
+            P.slots[(seg * 3 + I.piece) * 16 + lane] = sum;
+          }
+        }
+        cur = id;
+        if (row < 64) sum = rows[row * 16 + lane];
+      } else {
+        sum += rows[row * 16 + lane];
+      }
+    }
+    if (lane == 0) {
+      P.bnd_id[2 * gw] = wp0 < wp1 ? nb0 : -2;
+      P.bnd_id[2 * gw + 1] = wp0 < wp1 ? nb1 : -2;
+    }
+  }
+}
+
+// items cut by warp ranges: the warp where an item starts holds its first partial in
+// its second boundary record; the following warps hold the rest in their first
+// records; one thread per warp sums a chain in warp order and writes the item's slot
+__global__ void k_adj_fixup(AdjParams P, long long nw) {
+  const long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (w >= nw || *P.status != 0) return;
+  const int it = P.bnd_id[2 * w + 1];
+  if (it < 0) return;
+  double sum[16];
+#pragma unroll
+  for (int q = 0; q < 16; q++) sum[q] = P.bnd[(2 * w + 1) * 16 + q];
+  for (long long w2 = w + 1; w2 < nw; w2++) {
+    const int id = P.bnd_id[2 * w2];
+    if (id == -2) continue;          // a warp with no positions
+    if (id != it) break;
+#pragma unroll
+    for (int q = 0; q < 16; q++) sum[q] += P.bnd[(2 * w2) * 16 + q];
+  }
+  const AdjItem I = P.items[it];
+  const Run R = P.runs[I.run];
+  const long long seg = P.modes[R.mode].seg_base + I.s;
+#pragma unroll
+  for (int q = 0; q < 16; q++) P.slots[(seg * 3 + I.piece) * 16 + q] = sum[q];
 }
 
 // per (mode, segment): sum the sub-piece slots into slot 0 and scale the
@@ -500,6 +674,8 @@ void launch_loglike(const CallShape& cs, const LikeInputs& li, const DevScratch&
   k_loglike_final<<<cs.n_wf, 256, 0, st>>>(cs.n_wf, s.Lpart, li.loglike);
 }
 
+size_t adjoint_item_bytes() { return sizeof(AdjItem); }
+
 void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& li, const DevScratch& s, int num_sms,
                     cudaStream_t st) {
   k_item_len<<<(unsigned)((s.run_cap + 255) / 256), 256, 0, st>>>(s.run_cnt + cs.nm_total, s.runs, s.run_cap,
@@ -510,7 +686,16 @@ void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& 
   p.wf = s.wf; p.modes = s.modes; p.core = s.core; p.amp64 = s.amp64; p.crit = s.crit; p.keyF = s.keyF;
   p.runs = s.runs; p.rb = s.rbins; p.freqs = in.freqs; p.G = reinterpret_cast<const dbl4*>(s.Gbuf);
   p.item_off = s.item_off; p.run_cap = s.run_cap; p.tab = s.tab; p.slots = s.slots; p.status = s.status;
-  k_adjoint<<<(unsigned)(num_sms * 2), 256, 0, st>>>(p);   // two resident CTAs per SM (128 registers)
+  p.items = static_cast<AdjItem*>(s.adj_items); p.adj_off = s.adj_off; p.bnd = s.adj_bnd; p.bnd_id = s.adj_bnd_id;
+  // the item slots of this call's segments (at most three runs touch a segment)
+  p.item_cap = 3 * cs.seg_total;
+  k_adj_items<<<(unsigned)((p.item_cap + 255) / 256 + 1), 256, 0, st>>>(p);
+  k_scan64<<<1, 1024, 0, st>>>(s.adj_off, p.item_cap);
+  const size_t smem = (size_t)kAdjWarpsPerCta * 64 * (16 * sizeof(double) + sizeof(int));
+  cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const long long nw = (long long)num_sms * kAdjCtasPerSm * kAdjWarpsPerCta;
+  k_adjoint<<<(unsigned)(num_sms * kAdjCtasPerSm), 32 * kAdjWarpsPerCta, smem, st>>>(p);
+  k_adj_fixup<<<(unsigned)((nw + 127) / 128), 128, 0, st>>>(p, nw);
   k_seg_sum<<<(unsigned)((cs.seg_total + 255) / 256), 256, 0, st>>>(cs.seg_total, s.wf, s.modes, cs.n_wf, s.core,
                                                                     in.prefactor, s.slots);
   k_amp_knot<<<(unsigned)((cs.amp_total + 255) / 256), 256, 0, st>>>(cs.amp_total, cs.n_wf, s.wf, s.modes, in.t,

@@ -74,7 +74,8 @@ struct __align__(16) SegCore {
   double h;                // segment length [s]
   double ts;               // segment start time [s]
   unsigned long long theta0; // Q0.64 of frac(Phi_V(t_s)/2pi - m phi/2pi)
-  float bf, cf, df, pad;   // FP32 copies of b, c, d for the root's initial guess
+  float bf, cf, df;        // FP32 copies of b, c, d for the root's initial guess
+  float rbf;               // 1/b in FP32 (0 when b is 0 or 1/b is not a finite float)
 };
 static_assert(sizeof(SegCore) == 112, "SegCore layout");
 
@@ -266,6 +267,11 @@ struct DevScratch {
   double* Gbuf;                   // [sum N_f][4] 4 df (d - h)/S, both channels
   double* Lpart;                  // [max_waveforms][kLChunks] partial sums of L
   int* item_off;                  // [run_cap + 1] adjoint items (run, segment), scanned
+  void* adj_items;                // [3 seg_cap] AdjItem records (adjoint.cu)
+  long long* adj_off;             // [3 seg_cap + 1] bins per item, exclusive-scanned: the adjoint's bin stream
+  double* adj_bnd;                // [adjoint warps][2][16] partial sums of items cut by a warp's range
+  int* adj_bnd_id;                // [adjoint warps][2] their items (-1: none, -2: the warp's range is empty)
+  long long adj_item_cap;         // 3 seg_cap
   double* slots;                  // [sum N_m (K-1)][3 sub-pieces][16] per-segment gradients
   double *agY, *agM;              // [sum N_m K][2] amplitude knot-value / second-derivative gradients
   double *fgY, *fgM;              // [4][sum K] fundamental series, same
@@ -296,7 +302,10 @@ struct CallShape {
 
 constexpr int kLChunks = 512;      // per-waveform chunks of the likelihood's partial sums
 constexpr int kPrepKernels = 11;   // kernels launched by launch_prep (memsets excluded)
-constexpr int kAdjointKernels = 8; // kernels launched by launch_adjoint
+constexpr int kAdjointKernels = 11; // kernels launched by launch_adjoint
+constexpr int kAdjCtasPerSm = 2;     // resident CTAs of the adjoint kernel per SM (128 registers, 8 warps)
+constexpr int kAdjWarpsPerCta = 8;
+size_t adjoint_item_bytes();        // sizeof(AdjItem)
 
 // freqs_ready (optional): an event the kernels that read in.freqs must wait for
 void launch_prep(const CallShape& cs, const DevInputs& in, const DevScratch& s, cudaStream_t st,

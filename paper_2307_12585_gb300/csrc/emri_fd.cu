@@ -6,6 +6,7 @@
 #include <vector>
 
 #include <cufft.h>
+#include <nvtx3/nvToolsExt.h>   // header-only NVTX: ranges are no-ops unless a profiler attaches
 
 #include "../../include/emri_fd.h"
 #include "common.cuh"
@@ -198,6 +199,15 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
     AL(s.Gbuf, 4 * p->cap_nf);
     AL(s.Lpart, (long long)kLChunks * d->max_waveforms);
     AL(s.item_off, s.run_cap + 1);
+    s.adj_item_cap = 3 * p->cap_seg;
+    {
+      unsigned char* ai = nullptr;
+      AL(ai, adjoint_item_bytes() * (size_t)s.adj_item_cap);
+      s.adj_items = ai;
+    }
+    AL(s.adj_off, s.adj_item_cap + 1);
+    AL(s.adj_bnd, 32LL * kAdjCtasPerSm * kAdjWarpsPerCta * p->num_sms);
+    AL(s.adj_bnd_id, 2LL * kAdjCtasPerSm * kAdjWarpsPerCta * p->num_sms);
     AL(s.slots, 48 * p->cap_seg);
     AL(s.agY, 2 * p->cap_amp);
     AL(s.agM, 2 * p->cap_amp);
@@ -389,7 +399,9 @@ void run_forward(emri_fd_plan_s* p, const CallShape& cs, const DevInputs& in, si
   const cudaEvent_t freqs_ready = p->freqs_side ? p->ev_freqs : nullptr;
   p->freqs_side = false;
   if (cs.nm_total > 0) {
+    nvtxRangePushA("emri_fd: preparation (splines, records, runs)");
     launch_prep(cs, in, p->s, stm, freqs_ready);
+    nvtxRangePop();
     p->launches += kPrepKernels;
   } else {
     // no modes: every run list is empty
@@ -406,13 +418,19 @@ void run_forward(emri_fd_plan_s* p, const CallShape& cs, const DevInputs& in, si
       in2.h_plus = p->s.wbuf_p;
       in2.h_cross = p->s.wbuf_c;
       if (E) cudaEventRecord(E[1], stm);
+      nvtxRangePushA("emri_fd: SPA output kernel");
       launch_spa(cs, in2, p->s, p->num_sms, stm);
+      nvtxRangePop();
       if (E) cudaEventRecord(E[2], stm);
+      nvtxRangePushA("emri_fd: Hann window");
       launch_window(cs, p->s, in.freqs, in2.h_plus, in2.h_cross, in.h_plus, in.h_cross, p->num_sms, stm);
+      nvtxRangePop();
       p->launches += 2;
     } else {
       if (E) cudaEventRecord(E[1], stm);
+      nvtxRangePushA("emri_fd: SPA output kernel");
       launch_spa(cs, in, p->s, p->num_sms, stm);
+      nvtxRangePop();
       if (E) cudaEventRecord(E[2], stm);
       p->launches += 1;
     }
@@ -709,7 +727,9 @@ emri_fd_status emri_fd_loglike_and_grad(emri_fd_plan_t p, int n_wf, const long l
   run_forward(p, cs, in, 16 * (size_t)cs.nf_total);
   cudaStream_t stm = p->stream;
   if (cs.nf_total > 0) {
+    nvtxRangePushA("emri_fd: residual and likelihood");
     launch_loglike(cs, li, p->s, stm);
+    nvtxRangePop();
     p->launches += 2;
   } else {
     cudaMemsetAsync(li.loglike, 0, 8 * (size_t)n_wf, stm);
@@ -719,7 +739,9 @@ emri_fd_status emri_fd_loglike_and_grad(emri_fd_plan_t p, int n_wf, const long l
     for (int k = 0; k < 5; k++)
       if (gdev[k]) cudaMemsetAsync(gdev[k], 0, k < 4 ? kb : 16 * (size_t)cs.amp_total, stm);
     if (cs.nm_total > 0 && cs.nf_total > 0) {
+      nvtxRangePushA("emri_fd: adjoint (knot gradients)");
       launch_adjoint(cs, in, li, p->s, p->num_sms, stm);
+      nvtxRangePop();
       p->launches += kAdjointKernels;
     }
   }

@@ -426,7 +426,14 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
   // theta0 = frac((m Phi_phi_s + n Phi_r_s - m phi)/2pi): integer combination of
   // the Q0.64 knot phases (wraps modulo one turn)
   C.theta0 = (unsigned long long)(long long)m * (Fs.q[0] - Fs.q[2]) + (unsigned long long)(long long)n * Fs.q[1];
-  C.bf = d2f_bits(C.b); C.cf = d2f_bits(C.c); C.df = d2f_bits(C.d); C.pad = 0.f;   // truncated: start values only
+  // mixed plans: minus frac(A t_s), exactly from the integer product of the mantissas, so
+  // that their output kernel forms the phase from delta t = (g - A) t instead of g t
+  if (amp32) C.theta0 -= q64_mul(C.A, ts);
+  C.bf = d2f_bits(C.b); C.cf = d2f_bits(C.c); C.df = d2f_bits(C.d);   // truncated: start values only
+  {
+    const float r = C.b != 0.0 ? (float)(1.0 / C.b) : 0.f;
+    C.rbf = (fabsf(r) < 1e30f && fabsf(r) > 1e-30f) ? r : 0.f;
+  }
   core[r] = C;
   if (yk) yk[r] = 0.47746482927568600731 / h;   // 3/(2 pi h), extended SPA
 

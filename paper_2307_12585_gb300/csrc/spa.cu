@@ -82,8 +82,10 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
   const ff gx = neg ? ff_neg(fx) : fx;
   const ff dl = ff_sub(gx, Ax);
   // a6: FP32 start, then Newton with the residual in FP32 pairs
-  float Df;
-  const float uf = root_f32<EMRI_FD_X_ROOT_NIT>(C.bf, C.cf, C.df, dl.hi, ulo.hi, uhi.hi, dir, Df);
+  float Df, rDs, sts;
+  bool sok;
+  float uf = root_f32_series(C.bf, C.cf, C.df, C.rbf, dl.hi, ulo.hi, uhi.hi, Df, rDs, sts, sok);
+  if (!sok) uf = root_f32<EMRI_FD_X_ROOT_NIT>(C.bf, C.cf, C.df, dl.hi, ulo.hi, uhi.hi, dir, Df);
   ff t = ff_add(ff_mul_f(dx, uf), cx_);
   t = ff_add(ff_mul_f(t, uf), bx);
   ff res = ff_sub(ff_mul_f(t, uf), dl);
@@ -121,7 +123,7 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
   if (!EXT && coal) return false;
   const bool pos = D.hi > 0.f;
   const ff Da = pos ? D : ff_neg(D);
-  // extended form: y = 1/X in FP32 where |y| <= 1e-4, else in FP64
+  // extended form: y = 1/X in FP32 where |y| <= 1e-3 (|R - 1| <= 7e-5), else in FP64
   float yf = 0.f;
   double yd = 0.0, D2d = 0.0;
   bool slow = false;
@@ -130,7 +132,7 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
     const float r0 = rsqrtf(Da.hi), r2 = r0 * r0;
     yf = __fdividef((float)kExt3Over2Pi, X.h[0]) * D2f * D2f * (r2 * r2 * r2);
     if (!pos) yf = -yf;
-    if (coal || !(fabsf(yf) <= 1e-4f)) {
+    if (coal || !(fabsf(yf) <= 1e-3f)) {
       slow = true;
       D2d = fma(2.0 * C.d3, ff_to_double(u), C.c2);
       if (!coal) {
@@ -194,7 +196,7 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
   ai = ff_mul(ai, wgt);
   if constexpr (EXT) {
     if (!coal) {
-      if (!slow) {   // R = 1 + delta, |delta| <= 7e-6: the correction in FP32
+      if (!slow) {   // R = 1 + delta, |delta| <= 7e-5: the correction in FP32
         float dr, di;
         ext_delta_f32(yf, dr, di);
         const float cr = ar.hi * dr - ai.hi * di, ci = ar.hi * di + ai.hi * dr;
@@ -219,15 +221,46 @@ __device__ __forceinline__ bool body_fp64x(const SegCore& C, const SegFF& X, dou
   return true;
 }
 
-// mixed per-(branch, bin) body: FP64 root polish and in-segment phase, FP32
-// weight, sincos, amplitude and products; increments in v[0..3]
+// mixed per-(branch, bin) body: FP64 in-segment phase (and, in the extended form,
+// the root polish), FP32 root, weight, sincos, amplitude and products; increments in v[0..3]
 template <bool EXT>
 __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am, double f, bool neg, double ulo,
-                                           double uhi, int dir, float fa, float fb, float* v) {
+                                           double uhi, float ulof, float uhif, int dir, float fa, float fb,
+                                           float* v) {
   const double g = neg ? flip_sign(f) : f;
   const double delta = g - C.A;
   float uf, Df;
-  const double u = solve_root<4, EXT>(C, delta, ulo, uhi, dir, uf, Df);
+  double u;
+  if constexpr (EXT) {
+    u = solve_root<4, EXT>(C, delta, ulo, uhi, ulof, uhif, dir, uf, Df);
+  } else {
+    // an FP32 root: the phase is stationary at the root (Eq. 4), so a root error du
+    // moves it by only (1/2)(dF/du) h du^2 turns (below 1e-12 for an FP32 root's
+    // ~1e-7).  The series start and one Newton step settle it in well-conditioned
+    // pieces, the safeguarded iteration elsewhere.
+    const float dl = d2f_bits(delta);
+    float rD, step;
+    bool ok;
+    uf = root_f32_series(C.bf, C.cf, C.df, C.rbf, dl, ulof, uhif, Df, rD, step, ok);
+    if (!ok) {
+      uf = root_f32<4>(C.bf, C.cf, C.df, dl, ulof, uhif, dir, Df);
+      rD = __fdividef(1.f, Df);
+    }
+    // the weight needs dF/du to ~5e-7: its FP32 rounding, eps (|b| + 2|c| + 3|d|)/|D|,
+    // plus |F''| times the FP32 root's error, about 4 eps (|c| + 3|d|)(|dl| + |b|)/D^2
+    // (eps = 2^-23 for the truncated coefficients).  Next to a turnover, where that
+    // exceeds the bound, the root gets the FP64 polish and dF/du is taken in FP64.
+    const float r = fabsf(rD);
+    const float S1 = fmaf(3.f, fabsf(C.df), fmaf(2.f, fabsf(C.cf), fabsf(C.bf)));
+    const float S2 = fmaf(3.f, fabsf(C.df), fabsf(C.cf));
+    if (!(fmaf(4.f * S2, (fabsf(dl) + fabsf(C.bf)) * r, S1) * r <= 4.2f)) {
+      u = polish_root_f64<false>(C, delta, ulo, uhi, dir, uf, Df);
+      uf = d2f_bits(u);
+      Df = d2f_bits(fma(u, fma(u, C.d3, C.c2), C.b));
+    } else {
+      u = f2d_bits(uf);
+    }
+  }
   // the standard form needs dF/du only in FP32 (for the weight); its sign is the run's
   // direction, and a root with Df == 0 sits on a turnover (no contribution)
   double Dd = 0.0;
@@ -277,8 +310,13 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
       }
     }
   }
-  unsigned long long Th = phase_q64<false>(C, g, delta, u, pos);
-  if (coal) Th += pos ? (1ull << 61) : (0ull - (1ull << 61));
+  // a7: g t - Phi_V(t)/2pi = delta t - u inner(u) - theta0' turns, with t = t_s + u h,
+  // delta = g - A and theta0' = frac(Phi_V(t_s)/2pi - m phi/2pi - A t_s) (the mixed
+  // plan's record); |delta t| stays below a few thousand turns, so its FP64 rounding
+  // is ~1e-13 turn (the exact integer product g t_s is not needed at FP32 accuracy)
+  const double inner = fma(u, fma(u, C.P3, C.P2), C.Q1);
+  unsigned long long Th = q64_of(fma(delta, C.ts, u * fma(delta, C.h, -inner))) - C.theta0;
+  Th += coal ? 0ull : (pos ? (0ull - (1ull << 61)) : (1ull << 61));
   // half-turns in [-1, 1) from the top 46 bits of Th, without conversion instructions
   const long long ts_ = (long long)Th;
   const float th = small_int_to_float((int)(ts_ >> 42)) * 4.76837158203125e-07f +              // 2^-21
@@ -309,6 +347,10 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
 // workload).  The extended form's FP64 kernel keeps two.
 #ifndef EMRI_FD_SPA64_MINB
 #define EMRI_FD_SPA64_MINB 3
+#endif
+// and the extended-SPA FP64 kernel
+#ifndef EMRI_FD_SPA64_EXT_MINB
+#define EMRI_FD_SPA64_EXT_MINB 2
 #endif
 
 // store one bin of the FP32-pair forms: FP64X applies mu/d_L (an FP32 pair) and writes
@@ -343,7 +385,8 @@ constexpr int kBackPerFront = 8;   // back-of-queue (empty) tiles a CTA may take
 // of all members the same number of times: the tile and the exchanged flags are the
 // same for all members.
 template <int BPL, int PREC, bool EXT, int CL>
-__global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64_MINB) : EMRI_FD_SPA_MINB) k_spa(SpaParams P) {
+__global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT_MINB : EMRI_FD_SPA64_MINB)
+                                                      : EMRI_FD_SPA_MINB) k_spa(SpaParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<BPL, PREC>& S = *reinterpret_cast<Smem<BPL, PREC>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -500,7 +543,8 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
             // a6: root
             const double delta = g - C.A;
             float uf, Df;
-            const double u = solve_root<6, EXT>(C, delta, ulo, uhi, R.dir, uf, Df);
+            const double u = solve_root<6, EXT>(C, delta, ulo, uhi, s == R.s0 ? R.u0f[0] : 0.f,
+                                                s == R.s1 ? R.u1f[0] : 1.f, R.dir, uf, Df);
             // a8: dF/du
             const double Dd = fma(u, fma(u, C.d3, C.c2), C.b);
             const long long Dbits = __double_as_longlong(Dd);
@@ -509,7 +553,22 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
             const bool pos_slope = Dbits >= 0;
             const SegAmp64 Am = P.amp64[M.seg_base + s];
             double zr, zi, mp, mx;   // h+ += mp Z, hx += i mx Z (Z without the weight's factor)
-            if constexpr (!EXT) {
+            // extended form: R(X) = G_ext / G_std depends on y = 1/X = yk (d2F/du2)^2 / (dF/du)^3
+            // alone; where |y| <= 1e-3 (almost every bin) R - 1 is below 7e-5, so it is
+            // formed in FP32 and applied to the standard tail's Z (its error, ~1e-11 of Z,
+            // is far inside the FP64 bound).  Next to turnovers R comes from FP64 below.
+            float yf = 0.f;
+            bool fast = !EXT;
+            if constexpr (EXT) {
+              if (!coal) {
+                const float r0 = rsqrtf(d2f_bits(abs_bits(Dd))), r2 = r0 * r0;
+                const float D2f = fmaf(6.f * C.df, uf, 2.f * C.cf);
+                yf = d2f_bits(P.yk[M.seg_base + s]) * D2f * D2f * (r2 * r2 * r2);
+                if (!pos_slope) yf = -yf;
+                fast = fabsf(yf) <= 1e-3f;
+              }
+            }
+            if (fast) {
               // a7: phase in Q0.64 turns; e^{i psi} = T_k (1 - q)(1 + i x')
               const unsigned long long Th = phase_q64(C, g, delta, u, pos_slope);
               double2 T;
@@ -523,6 +582,13 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
               const double atr = fma(are, T.x, -aim * T.y), ati = fma(are, T.y, aim * T.x);
               zr = fma(-xp, ati, atr);
               zi = fma(xp, atr, ati);
+              if constexpr (EXT) {   // Z R = Z + Z (R - 1), the correction in FP32
+                float dr, di;
+                ext_delta_f32(yf, dr, di);
+                const float zrf = d2f_bits(zr), zif = d2f_bits(zi);
+                zr += f2d_bits(fmaf(zrf, dr, -zif * di));
+                zi += f2d_bits(fmaf(zrf, di, zif * dr));
+              }
               const double t = rho * cw;
               mp = amaj ? cw : t;
               mx = amaj ? t : cw;
@@ -590,7 +656,8 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? 2 : EMRI_FD_SPA64
                               s == R.s1 ? u1x : ff_make(1.f, 0.f), R.dir, fa, fb, P.tabf, v);
             } else {
               const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
-              ok = body_mixed<EXT>(C, P.amp32[M.seg_base + s], fqq, neg, ulo, uhi, R.dir, M.af[0], M.bf[0], v);
+              ok = body_mixed<EXT>(C, P.amp32[M.seg_base + s], fqq, neg, ulo, uhi, s == R.s0 ? R.u0f[0] : 0.f,
+                                   s == R.s1 ? R.u1f[0] : 1.f, R.dir, M.af[0], M.bf[0], v);
             }
             if (!ok) continue;
 #pragma unroll

@@ -100,17 +100,16 @@ static __device__ __noinline__ double solve_root_safe(const SegCore& C, double d
   return u;
 }
 
-// a6: FP32 start value, FP64 Newton polish (iterated where the predicted error of
-// one step exceeds 1e-13, i.e. near turnovers), clamped into [ulo, uhi].  With
-// SETTLE (the extended form, which is finite and well-conditioned next to
+// a6, FP64 polish of an FP32 root uf (with its FP32 dF/du Df): Newton steps with the
+// FP64 residual and the FP32 reciprocal derivative, iterated where the predicted
+// error of one step exceeds 1e-13 (i.e. near turnovers), clamped into [ulo, uhi].
+// With SETTLE (the extended form, which is finite and well-conditioned next to
 // turnovers), a polish that has not settled or had to be clamped is redone by
 // solve_root_safe; the standard form's weight diverges there anyway, and the
 // call's register cost is not worth paying in its hot loop.
-template <int NIT, bool SETTLE = false>
-__device__ __forceinline__ double solve_root(const SegCore& C, double delta, double ulo, double uhi, int dir,
-                                             float& uf_out, float& Df_out) {
-  float Df;
-  float uf = root_f32<NIT>(C.bf, C.cf, C.df, d2f_bits(delta), d2f_bits(ulo), d2f_bits(uhi), dir, Df);
+template <bool SETTLE = false>
+__device__ __forceinline__ double polish_root_f64(const SegCore& C, double delta, double ulo, double uhi, int dir,
+                                                  float& uf, float& Df) {
   double u = f2d_bits(uf);
   double res = fma(u, fma(u, fma(u, C.d, C.c), C.b), -delta);
   float rcf = __fdividef(1.f, Df);
@@ -140,6 +139,50 @@ __device__ __forceinline__ double solve_root(const SegCore& C, double delta, dou
     uf = d2f_bits(u);
     Df = (3.f * C.df * uf + 2.f * C.cf) * uf + C.bf;
   }
+  return u;
+}
+
+
+// a6, FP32 root in one pass for well-conditioned pieces: the inverse series of the
+// cubic b u + c u^2 + d u^3 = dl about u = 0 to third order in x = dl/b,
+// u0 = x - p x^2 + (2 p^2 - q) x^3 (p = c/b, q = d/b, from the record's rb = 1/b),
+// then one Newton step.  The series' error is O(p^3 x^4) and the step squares it, so
+// the result is taken when |p x| and |q x^2| are at most 1/32, the step keeps u in
+// [lo, hi], and the predicted error of a further step is below 1e-8; otherwise (near
+// turnovers, strong curvature) ok = false and the caller runs the safeguarded
+// iteration.  Returns u, dF/du at u0 (within |F''| |step| of dF/du(u)) and the
+// reciprocal of that derivative.
+__device__ __forceinline__ float root_f32_series(float bf, float cf, float df, float rbf, float dl, float lo,
+                                                 float hi, float& Dout, float& rDout, float& stepout, bool& ok) {
+  const float x = dl * rbf;
+  const float p = cf * rbf, q = df * rbf;
+  const float px = p * x, qxx = q * x * x;
+  const float u0 = x * fmaf(-x, fmaf(-x, fmaf(2.f * p, p, -q), p), 1.f);
+  const float D = fmaf(fmaf(3.f * df, u0, 2.f * cf), u0, bf);
+  const float fu = fmaf(fmaf(fmaf(df, u0, cf), u0, bf), u0, -dl);
+  const float rD = __fdividef(1.f, D);
+  const float step = fu * rD;
+  const float u = u0 - step;
+  ok = rbf != 0.f && fabsf(px) <= 0.03125f && fabsf(qxx) <= 0.03125f && u >= lo && u <= hi &&
+       fabsf(p) * step * step <= 1e-8f;
+  Dout = D;
+  rDout = rD;
+  stepout = step;
+  return u;
+}
+
+// a6: FP32 start value (the series and one Newton step where they settle it, the
+// safeguarded iteration elsewhere), then the FP64 polish above.  ulof, uhif: the
+// piece's bounds as floats (rounded; they only bracket the FP32 start)
+template <int NIT, bool SETTLE = false>
+__device__ __forceinline__ double solve_root(const SegCore& C, double delta, double ulo, double uhi, float ulof,
+                                             float uhif, int dir, float& uf_out, float& Df_out) {
+  float Df, rD, st;
+  bool ok;
+  const float dl = d2f_bits(delta);
+  float uf = root_f32_series(C.bf, C.cf, C.df, C.rbf, dl, ulof, uhif, Df, rD, st, ok);
+  if (!ok) uf = root_f32<NIT>(C.bf, C.cf, C.df, dl, ulof, uhif, dir, Df);
+  const double u = polish_root_f64<SETTLE>(C, delta, ulo, uhi, dir, uf, Df);
   uf_out = uf;
   Df_out = Df;
   return u;
