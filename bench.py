@@ -45,7 +45,8 @@ WORKLOAD = ("paper-shaped FP64 single waveform: T=2 yr, K=200 knots, 2000 modes 
 FP64_OPS_PER_MODE_BIN = 30      # 25 DFMA + 5 DMUL/DADD per mode-bin in k_spa<*, 0, 0> (counted from the source)
 FP64_FLOPS_PER_MODE_BIN = 55    # 25 x 2 + 5
 FP64_PER_CLK_PER_SM = 2          # GB300 FP64 issue rate (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
-MIXED_FP64_OPS_PER_MODE_BIN = 9  # the mixed form's FP64 left per mode-bin: difference 1, root polish 4, phase 4
+MIXED_FP64_OPS_PER_MODE_BIN = 6  # the mixed form's FP64 per mode-bin: g - A 1, in-segment phase 5 (the FP64
+                                 # root polish runs only next to turnovers)
 ADJ_FP64_OPS_PER_MODE_BIN = 75   # k_adjoint per mode-bin: the forward's 29 (with dA/du) + 46 for the derivatives
 ORACLE_STRIDE = 16               # both CPU-oracle legs evaluate every 16th bin of the workload per step
 
@@ -420,13 +421,12 @@ def run_paper(args, rank, world, local):
         oplan.close()
         ospa_s = ost["spa_ns"] * 1e-9 / max(1, ost["timed_calls"])
         if prec == "mixed" and spa == "standard":
-            # its FP64 (root polish, phase) against the FP64 pipe's measured rate; the ALU
-            # pipe (integer phase and keys) is about as busy
+            # its FP64 (g - A and the in-segment phase) against the FP64 pipe's measured rate;
+            # the kernel is bound by instruction issue (integer phase and keys, FP32 work)
             roof = fp64_roof(MIXED_FP64_OPS_PER_MODE_BIN, mb_per_launch / ospa_s, peaks, oclocks, n_sms, None,
-                             "output kernel alone; root polish and in-segment phase in FP64, the rest FP32 and "
-                             "integer work")
-            roof["bound"] = "alu"
-            roof["pipe"] = "fp64 + int"
+                             "output kernel alone; g - A and the in-segment phase in FP64, the rest FP32 and "
+                             "integer work; instruction issue is the limit")
+            roof["pipe"] = "issue (int + fp32); fp64 fraction shown"
         elif prec == "fp64x" and spa == "standard":
             # no FP64 per mode-bin: the FP64 form's flops of FP64-accurate arithmetic per
             # mode-bin, done in FP32 pairs, against the FP64 pipe's measured peak

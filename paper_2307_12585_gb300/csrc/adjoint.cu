@@ -200,25 +200,50 @@ __global__ void k_adj_items(AdjParams P) {
   P.adj_off[it] = (long long)(hi[0] - lo[0]) + (hi[1] - lo[1]);
 }
 
-// exclusive scan of cnt[0..n) in place (int64), total written to cnt[n]; one block
-__global__ void k_scan64(long long* cnt, long long n) {
-  __shared__ long long part[1024];
-  const int tid = threadIdx.x;
-  const long long per = (n + blockDim.x - 1) / blockDim.x;
-  const long long b = tid * per, e = b + per < n ? b + per : n;
-  long long sum = 0;
-  for (long long i = b; i < e; i++) sum += cnt[i];
-  part[tid] = sum;
-  __syncthreads();
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-    const long long v = tid >= o ? part[tid - o] : 0;
+// exclusive scan of cnt[0..n) in place (int64), total written to cnt[n]; one block of
+// 1024 threads stepping through the array 4096 entries at a time (each thread four
+// consecutive entries, so the loads and stores are coalesced), carrying the running total
+__global__ void __launch_bounds__(1024) k_scan64(long long* cnt, long long n) {
+  __shared__ long long wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  long long carry = 0;
+  for (long long base = 0; base < n; base += 4096) {
+    long long v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const long long i = base + 4 * tid + k;
+      v[k] = i < n ? cnt[i] : 0;
+      s += v[k];
+    }
+    long long x = s;   // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    part[tid] += v;
+    if (warp == 0) {
+      long long w = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    long long e = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - s;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const long long i = base + 4 * tid + k;
+      if (i < n) cnt[i] = e;
+      e += v[k];
+    }
+    carry += wsum[31];
     __syncthreads();
   }
-  long long run = part[tid] - sum;
-  for (long long i = b; i < e; i++) { const long long c = cnt[i]; cnt[i] = run; run += c; }
-  if (tid == blockDim.x - 1) cnt[n] = part[tid];
+  if (tid == 0) cnt[n] = carry;
 }
 
 // the adjoint's per-lane state of one item

@@ -318,6 +318,8 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
   unsigned long long Th = q64_of(fma(delta, C.ts, u * fma(delta, C.h, -inner))) - C.theta0;
   Th += coal ? 0ull : (pos ? (0ull - (1ull << 61)) : (1ull << 61));
   // half-turns in [-1, 1) from the top 46 bits of Th, without conversion instructions
+  // (sincospif measured faster here than a 1024-entry shared-memory table times a
+  // two-term e^{ix})
   const long long ts_ = (long long)Th;
   const float th = small_int_to_float((int)(ts_ >> 42)) * 4.76837158203125e-07f +              // 2^-21
                    small_int_to_float((int)((ts_ >> 20) & 0x3FFFFF)) * 1.1368683772161603e-13f;  // 2^-43
@@ -348,9 +350,14 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
 #ifndef EMRI_FD_SPA64_MINB
 #define EMRI_FD_SPA64_MINB 3
 #endif
+// 1: the FP64 kernel's loop over a lane's bins is rolled (one copy of the body), as in
+// the FP32-path kernels; 0: unrolled
+#ifndef EMRI_FD_SPA64_ROLLED
+#define EMRI_FD_SPA64_ROLLED 1
+#endif
 // and the extended-SPA FP64 kernel
 #ifndef EMRI_FD_SPA64_EXT_MINB
-#define EMRI_FD_SPA64_EXT_MINB 2
+#define EMRI_FD_SPA64_EXT_MINB 3
 #endif
 
 // store one bin of the FP32-pair forms: FP64X applies mu/d_L (an FP32 pair) and writes
@@ -530,11 +537,19 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
           // weight, cw and rho cw.  Sign flips are integer operations on the sign bit.
           const bool amaj = alpha_major(M.alpha, M.beta);
           const double rho = M.rho;
+#if EMRI_FD_SPA64_ROLLED
+#pragma unroll 1
+#else
 #pragma unroll
+#endif
           for (int q = 0; q < BPL; q++) {
             const long long bin = bin0 + lane + 32 * q;
             if (bin < b0 || bin >= b1) continue;
-            const double g = neg ? flip_sign(fq[q]) : fq[q];
+            double fqq = fq[0];   // the lane's q-th bin (a predicated select when the loop is rolled)
+#pragma unroll
+            for (int qq = 1; qq < BPL; qq++)
+              if (qq == q) fqq = fq[qq];
+            const double g = neg ? flip_sign(fqq) : fqq;
             const long long key = ordkey(g);
             // a5: segment holding the root
             const int s = run_segment(R, P.keyF, M.key_base, key);
@@ -626,10 +641,14 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
             }
             // a11: positive branch h+ += alpha Z, hx += i beta Z;
             //      negative branch h+ += alpha conj Z, hx += -i beta conj Z
-            acc[q][0] = fma(mp, zr, acc[q][0]);
-            acc[q][1] = fma(neg ? flip_sign(mp) : mp, zi, acc[q][1]);
-            acc[q][2] = fma(flip_sign(mx), zi, acc[q][2]);
-            acc[q][3] = fma(neg ? flip_sign(mx) : mx, zr, acc[q][3]);
+#pragma unroll
+            for (int qq = 0; qq < BPL; qq++) {
+              if (qq != q) continue;
+              acc[qq][0] = fma(mp, zr, acc[qq][0]);
+              acc[qq][1] = fma(neg ? flip_sign(mp) : mp, zi, acc[qq][1]);
+              acc[qq][2] = fma(flip_sign(mx), zi, acc[qq][2]);
+              acc[qq][3] = fma(neg ? flip_sign(mx) : mx, zr, acc[qq][3]);
+            }
           }
         } else {
           // FP64X and mixed: one copy of the per-bin body (rolled loop over the
