@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
             // a5: segment holding the root
             const int s = run_segment(R, P.keyF, M.key_base, key);
             const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
-            const SegCore C = P.core[M.seg_base + s];
+            const SegCore& C = P.core[M.seg_base + s];
             // a6: root
             const double delta = g - C.A;
             float uf, Df;
@@ -667,7 +667,9 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
             for (int qq = 1; qq < BPL; qq++)
               if (qq == q) { fqq = fq[qq]; kq_ = neg ? kn[qq] : kp[qq]; fx = fqf[qq]; }
             const int s = s_uni >= 0 ? s_uni : run_segment(R, P.keyF, M.key_base, kq_);
-            const SegCore C = P.core[M.seg_base + s];
+            // the record is read through a reference, so that fields used only on the rare
+            // slow paths (the FP64 root polish) are loaded there rather than held in registers
+            const SegCore& C = P.core[M.seg_base + s];
             float v[8];
             bool ok;
             if constexpr (PREC == 2) {

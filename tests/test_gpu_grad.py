@@ -173,3 +173,29 @@ def test_autograd_rejects_knots_changed_in_place(oracle):
     with pytest.raises(RuntimeError):
         L.backward()
     plan.close()
+
+
+@pytest.mark.parametrize("n_bins,n_modes", [(1 << 18, 1), (1 << 18, 2), (600, 2)])
+def test_gradient_stream_extremes(oracle, n_bins, n_modes):
+    """The adjoint's bin stream at its extremes, against the oracle's gradient: one or two
+    voices on five knots over a dense grid, so that each (run, segment) item holds tens of
+    thousands of bins and runs through hundreds of warps' ranges (the cross-warp chains);
+    and 600 bins, fewer positions than the grid has lanes (warps with empty ranges)."""
+    base = synth.small_config(0, n_bins=16)
+    idx = np.array([0, 25, 50, 75, 99])
+    w = base.with_modes([3, 14][:n_modes])   # (2, 1, -2) and (2, 2, -2)
+    for k in ("t", "phi_phi", "phi_r", "omega_phi", "omega_r"):
+        setattr(w, k, getattr(w, k)[idx].copy())
+    w.amp = np.ascontiguousarray(w.amp[:, idx])
+    F = [(m * w.omega_phi + n * w.omega_r) / (2 * np.pi) for m, n in zip(w.m, w.n)]
+    lo = min(np.abs(x).min() for x in F)
+    hi = max(np.abs(x).max() for x in F)
+    w = w.with_freqs(np.linspace(lo * 1.001, hi * 0.999, n_bins))
+    w.meta["T"] = w.t[-1] - w.t[0]
+    w, d = _case(oracle, w)
+    L, g = _gpu_like(w, d)
+    Lo, go = oracle.loglike_grad(w, *d)
+    assert abs(L[0] - Lo) <= 1e-10 * abs(Lo)
+    for k in ("phi_phi", "phi_r", "omega_phi", "omega_r"):
+        assert rel_l2(g[k], go[k]) <= 1e-8, k
+    assert rel_l2(g["amp"], go["amp"].reshape(-1)) <= 1e-8
