@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--waveforms", type=int, default=8)
     ap.add_argument("--tile-bins", type=int, default=128)
-    ap.add_argument("--config", default="paper", choices=["paper", "batch", "mixed-batch", "likelihood", "td", "select"])
+    ap.add_argument("--config", default="paper",
+                    choices=["paper", "batch", "mixed-batch", "likelihood", "td", "select", "probe"])
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batches", action="store_true")
@@ -243,7 +244,7 @@ FORM_TILE = {"fp64x": 64, "mixed": 64}
 DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
 # DRAM bytes (read + write) of one k_spa<4,0,0> launch (FP64, standard SPA, 128-bin tiles) on
 # this workload, from one ncu capture of the kernel as it stands
-TRAFFIC_FP64_SPA = 102.095104e6 + 72.666368e6
+TRAFFIC_FP64_SPA = 102.114560e6 + 66.614016e6
 
 
 def base_line(args, world, metric, value, unit, ms, workload, extra=None):
@@ -777,6 +778,16 @@ def batched_measure(args, rank, world, local, mixed, nb, steps, warmup, peaks, t
     return workload, world * nb * steps / sec, ms, extra, prec
 
 
+def run_probe(args, rank, world, local):
+    """--config probe: the FP64 and FP32 FMA peak rates alone."""
+    peaks = measure_fma_peaks(local)
+    if rank == 0:
+        line = base_line(args, world, "FP64 FMA rate", world * peaks["fp64"]["fma_per_s"], "FMA/s",
+                         peaks["fp64"]["ms_per_launch"] * args.steps, "emri_fd_fma_probe: 8 CTAs of 256 threads per SM, "
+                         "8 independent FMA chains per thread", {"fma_peaks": peaks})
+        print(json.dumps(line), flush=True)
+
+
 def run_batched(args, rank, world, local, mixed):
     """--config batch | mixed-batch: one line for the batched workload."""
     peaks = measure_fma_peaks(local)
@@ -882,6 +893,8 @@ def main():
         run_td(args, rank, world, local)
     elif args.config == "select":
         run_select(args, rank, world, local)
+    elif args.config == "probe":
+        run_probe(args, rank, world, local)
     if world > 1:
         dist.destroy_process_group()
 
