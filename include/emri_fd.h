@@ -76,11 +76,16 @@ typedef enum {
   EMRI_FD_ERR_CAPACITY = 6,   /* a size above the plan's maxima, or branch storage exhausted */
   EMRI_FD_ERR_CUDA = 7,       /* a CUDA runtime call failed */
   EMRI_FD_ERR_OOM = 8,        /* device allocation failed */
-  EMRI_FD_ERR_TIMEOUT = 9     /* reserved for a bounded device wait that runs out.  No kernel of
+  EMRI_FD_ERR_TIMEOUT = 9,    /* reserved for a bounded device wait that runs out.  No kernel of
                                  this version waits on a flag, a peer or another CTA's progress
                                  (work is claimed with atomics, and thread-block cluster barriers
                                  are reached by every member the same number of times), so no
                                  call returns it. */
+  EMRI_FD_ERR_INTERNAL = 10   /* a device-side index check failed: only libraries built with
+                                 -DEMRI_FD_CHECKS=1 (see the package's build script) test the
+                                 indices their kernels derive from the device-built run lists,
+                                 latch this status and skip the access instead of reading or
+                                 writing out of bounds */
 } emri_fd_status;
 
 enum { EMRI_FD_FP64 = 0, EMRI_FD_MIXED = 1, EMRI_FD_FP64X = 2 };

@@ -17,7 +17,7 @@ from . import build as _build
 EMRI_FD_FP64, EMRI_FD_MIXED, EMRI_FD_FP64X = 0, 1, 2
 STATUS = {0: "EMRI_FD_OK", 1: "EMRI_FD_ERR_ARG", 2: "EMRI_FD_ERR_KNOTS", 3: "EMRI_FD_ERR_FREQ",
           4: "EMRI_FD_ERR_MODE", 5: "EMRI_FD_ERR_NONFINITE", 6: "EMRI_FD_ERR_CAPACITY",
-          7: "EMRI_FD_ERR_CUDA", 8: "EMRI_FD_ERR_OOM", 9: "EMRI_FD_ERR_TIMEOUT"}
+          7: "EMRI_FD_ERR_CUDA", 8: "EMRI_FD_ERR_OOM", 9: "EMRI_FD_ERR_TIMEOUT", 10: "EMRI_FD_ERR_INTERNAL"}
 EXPORTS = ("emri_fd_plan", "emri_fd_sum_modes", "emri_fd_loglike_and_grad", "emri_fd_sync", "emri_fd_stats",
            "emri_fd_profile", "emri_fd_plan_destroy", "emri_fd_strerror", "emri_fd_sum_modes_noalloc",
            "emri_fd_set_tile", "emri_fd_set_tile_split", "emri_fd_capture", "emri_fd_replay", "emri_fd_graph_destroy",
@@ -45,7 +45,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: $EMRI_FD_LIBRARY if set (e.g. the checked build,
+    build.LIB_CHECKED), else the in-tree build."""
+    return os.environ.get("EMRI_FD_LIBRARY") or _build.LIB
 
 
 def lib():

@@ -128,6 +128,7 @@ struct AdjParams {
   const double2* tab;      // e^{2 pi i k/65536}
   double* slots;           // [3 * seg_total][16]
   const int* status;
+  long long nm_total, seg_total, nf_total;   // array sizes (checked builds)
 };
 
 // last r in [0, n) with off[r] <= it, for ascending off with off[0] <= it (one thread)
@@ -257,11 +258,17 @@ struct AdjLane {
   long long seg;           // global (mode, segment) record
 };
 
-__device__ __forceinline__ void adj_load(const AdjParams& P, long long it, AdjLane& L) {
+__device__ __forceinline__ bool adj_load(const AdjParams& P, long long it, AdjLane& L) {
   L.I = P.items[it];
+  if (check_fails(L.I.run >= 0 && L.I.run < P.run_cap, P.status)) return false;
   L.R = P.runs[L.I.run];
+  if (check_fails(L.R.mode >= 0 && L.R.mode < P.nm_total, P.status)) return false;
   const ModeInfo M = P.modes[L.R.mode];
   L.seg = M.seg_base + L.I.s;
+  if (check_fails(L.I.s >= L.R.s0 && L.I.s <= L.R.s1 && L.seg < P.seg_total && L.I.lo_p >= 0 &&
+                      L.I.hi_p <= P.nf_total && L.I.lo_n >= 0 && L.I.hi_n <= P.nf_total,
+                  P.status))
+    return false;
   L.C = P.core[L.seg];
   L.Am = P.amp64[L.seg];   // times M.scale
   const bool amaj = alpha_major(M.alpha, M.beta);
@@ -269,6 +276,7 @@ __device__ __forceinline__ void adj_load(const AdjParams& P, long long it, AdjLa
   L.bp = amaj ? M.rho : 1.0;
   L.ulo = (L.I.s == L.R.s0) ? L.R.u0 : 0.0;
   L.uhi = (L.I.s == L.R.s1) ? L.R.u1 : 1.0;
+  return true;
 }
 
 // The adjoint's bin stream: the bins of every item, item after item (positive branch
@@ -306,7 +314,7 @@ __global__ void __launch_bounds__(32 * kAdjWarpsPerCta, kAdjCtasPerSm) k_adjoint
     long long it = last_le(P.adj_off, P.item_cap, p0);
     long long it_end = P.adj_off[it + 1];
     AdjLane L;
-    adj_load(P, it, L);
+    if (!adj_load(P, it, L)) return;
     bool first_open = true;
     double acc[16], hsum[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -329,7 +337,7 @@ __global__ void __launch_bounds__(32 * kAdjWarpsPerCta, kAdjCtasPerSm) k_adjoint
 #pragma unroll
         for (int q = 0; q < 16; q++) dst[q] = acc[q];
         do { it++; it_end = P.adj_off[it + 1]; } while (it_end <= pos);
-        adj_load(P, it, L);
+        if (!adj_load(P, it, L)) return;
 #pragma unroll
         for (int q = 0; q < 16; q++) acc[q] = 0.0;
         hsum[0] = hsum[1] = hsum[2] = 0.0;
@@ -712,6 +720,7 @@ void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& 
   p.runs = s.runs; p.rb = s.rbins; p.freqs = in.freqs; p.G = reinterpret_cast<const dbl4*>(s.Gbuf);
   p.item_off = s.item_off; p.run_cap = s.run_cap; p.tab = s.tab; p.slots = s.slots; p.status = s.status;
   p.items = static_cast<AdjItem*>(s.adj_items); p.adj_off = s.adj_off; p.bnd = s.adj_bnd; p.bnd_id = s.adj_bnd_id;
+  p.nm_total = cs.nm_total; p.seg_total = cs.seg_total; p.nf_total = cs.nf_total;
   // the item slots of this call's segments (at most three runs touch a segment)
   p.item_cap = 3 * cs.seg_total;
   k_adj_items<<<(unsigned)((p.item_cap + 255) / 256 + 1), 256, 0, st>>>(p);

@@ -35,10 +35,31 @@ constexpr int kTab64N = 1 << kTab64Bits;
 constexpr int kListCap = 2048;            // (run, sign) entries buffered per tile pass
 
 // status bits latched in the plan's device status word (no kernel of this library
-// waits on a flag, a peer or a barrier it does not own, so none has a timeout bit)
+// waits on a flag, a peer or a barrier it does not own, so none has a timeout bit);
+// ST_BOUNDS is latched only by the index checks of checked builds (below)
 enum : int {
-  ST_KNOTS = 1, ST_FREQ = 2, ST_MODE = 4, ST_NONFINITE = 8, ST_CAPACITY = 16
+  ST_KNOTS = 1, ST_FREQ = 2, ST_MODE = 4, ST_NONFINITE = 8, ST_CAPACITY = 16, ST_BOUNDS = 32
 };
+
+// Checked builds (-DEMRI_FD_CHECKS=1) test the indices the hot kernels derive from the
+// device-built run lists (run, mode, segment, bin) against their arrays.  A failed check
+// latches ST_BOUNDS and the access is skipped; nothing traps, so the context stays usable
+// and the call reports EMRI_FD_ERR_INTERNAL.  In normal builds the checks compile away.
+#ifndef EMRI_FD_CHECKS
+#define EMRI_FD_CHECKS 0
+#endif
+__device__ __forceinline__ bool check_fails(bool ok, const int* status) {
+#if EMRI_FD_CHECKS
+  if (!ok) {
+    atomicOr(const_cast<int*>(status), ST_BOUNDS);
+    return true;
+  }
+#else
+  (void)ok;
+  (void)status;
+#endif
+  return false;
+}
 
 struct WfInfo {
   long long ko, K;         // knot slice

@@ -102,6 +102,7 @@ const char* emri_fd_strerror(emri_fd_status s) {
     case EMRI_FD_ERR_CUDA: return "CUDA runtime error";
     case EMRI_FD_ERR_OOM: return "device allocation failed";
     case EMRI_FD_ERR_TIMEOUT: return "bounded device wait timed out (reserved; not returned by this version)";
+    case EMRI_FD_ERR_INTERNAL: return "a device-side index check failed (checked builds)";
   }
   return "unknown status";
 }
@@ -383,6 +384,7 @@ emri_fd_status sync_status(emri_fd_plan_s* p) {
   if (hs & ST_MODE) return EMRI_FD_ERR_MODE;
   if (hs & ST_NONFINITE) return EMRI_FD_ERR_NONFINITE;
   if (hs & ST_CAPACITY) return EMRI_FD_ERR_CAPACITY;
+  if (hs & ST_BOUNDS) return EMRI_FD_ERR_INTERNAL;
   return EMRI_FD_OK;
 }
 

@@ -175,5 +175,6 @@ extern "C" emri_fd_status emri_fd_sum_modes_noalloc(int conj_partners, long long
   if (hs & ST_MODE) return EMRI_FD_ERR_MODE;
   if (hs & ST_NONFINITE) return EMRI_FD_ERR_NONFINITE;
   if (hs & ST_CAPACITY) return EMRI_FD_ERR_CAPACITY;
+  if (hs & ST_BOUNDS) return EMRI_FD_ERR_INTERNAL;
   return EMRI_FD_OK;
 }

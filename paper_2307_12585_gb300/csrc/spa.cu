@@ -60,6 +60,7 @@ struct SpaParams {
   unsigned long long* counters;
   const int* status;
   long long tiles_total;
+  long long run_cap, nm_total, seg_total, nf_total;   // array sizes (checked builds)
 };
 
 template <int BPL, int PREC>
@@ -514,9 +515,14 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
         const int ent = S.list[e];
         const long long r = W.run_base + (ent >> 1);
         const bool neg = ent & 1;
+        if (check_fails(r >= 0 && r < P.run_cap, P.status)) continue;
         const Run R = P.runs[r];
         const RunBins B = P.rb[r];
         const int b0 = neg ? B.b0n : B.b0p, b1 = neg ? B.b1n : B.b1p;
+        if (check_fails(R.mode >= 0 && R.mode < P.nm_total && R.s0 >= 0 && R.s0 <= R.s1 && b0 >= 0 &&
+                            b1 <= P.nf_total,
+                        P.status))
+          continue;
         const ModeInfo M = P.modes[R.mode];
         // a5 for the whole warp (FP32-path kernels, which are issue-bound; in the FP64
         // kernel the per-bin integer search overlaps the FP64 pipe for free): when the
@@ -553,6 +559,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
             const long long key = ordkey(g);
             // a5: segment holding the root
             const int s = run_segment(R, P.keyF, M.key_base, key);
+            if (check_fails(s >= R.s0 && s <= R.s1 && M.seg_base + s < P.seg_total, P.status)) continue;
             const double ulo = (s == R.s0) ? R.u0 : 0.0, uhi = (s == R.s1) ? R.u1 : 1.0;
             const SegCore& C = P.core[M.seg_base + s];
             // a6: root
@@ -667,6 +674,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
             for (int qq = 1; qq < BPL; qq++)
               if (qq == q) { fqq = fq[qq]; kq_ = neg ? kn[qq] : kp[qq]; fx = fqf[qq]; }
             const int s = s_uni >= 0 ? s_uni : run_segment(R, P.keyF, M.key_base, kq_);
+            if (check_fails(s >= R.s0 && s <= R.s1 && M.seg_base + s < P.seg_total, P.status)) continue;
             // the record is read through a reference, so that fields used only on the rare
             // slow paths (the FP64 root polish) are loaded there rather than held in registers
             const SegCore& C = P.core[M.seg_base + s];
@@ -903,6 +911,7 @@ void launch_spa(const CallShape& cs, const DevInputs& in, const DevScratch& s, i
   p.wf = s.wf; p.n_wf = cs.n_wf; p.modes = s.modes; p.core = s.core; p.amp64 = s.amp64; p.amp32 = s.amp32;
   p.keyF = s.keyF; p.runs = s.runs; p.rb = s.rbins; p.freqs = in.freqs; p.hp = in.h_plus; p.hc = in.h_cross;
   p.tab = s.tab; p.counters = s.counters; p.status = s.status; p.tiles_total = cs.tiles_total;
+  p.run_cap = s.run_cap; p.nm_total = cs.nm_total; p.seg_total = cs.seg_total; p.nf_total = cs.nf_total;
   p.segff = s.segff; p.tabf = s.tabf; p.prefactor = in.prefactor; p.yk = s.yk;
   cudaMemsetAsync(s.counters, 0, sizeof(unsigned long long), st);
   const int bpl = cs.tile_bins / 32;

@@ -39,7 +39,7 @@ def test_binding_names_match_header():
 
 def test_strerror_and_null_arguments(L):
     from paper_2307_12585_gb300 import api
-    for code in range(10):
+    for code in range(11):
         assert L.emri_fd_strerror(code)
     assert L.emri_fd_plan(None, None, None) == 1            # EMRI_FD_ERR_ARG, no device touched
     h = C.c_void_p()
