@@ -318,14 +318,18 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
   const double inner = fma(u, fma(u, C.P3, C.P2), C.Q1);
   unsigned long long Th = q64_of(fma(delta, C.ts, u * fma(delta, C.h, -inner))) - C.theta0;
   Th += coal ? 0ull : (pos ? (0ull - (1ull << 61)) : (1ull << 61));
-  // half-turns in [-1, 1) from the top 46 bits of Th, without conversion instructions
-  // (sincospif measured faster here than a 1024-entry shared-memory table times a
-  // two-term e^{ix})
+  // half-turns in [-1, 1) from the top 46 bits of Th, without conversion instructions,
+  // then the hardware sine and cosine of pi th in [-pi, pi) (the XU pipe; absolute error
+  // below 4e-7, as the FP32 form's other steps)
   const long long ts_ = (long long)Th;
   const float th = small_int_to_float((int)(ts_ >> 42)) * 4.76837158203125e-07f +              // 2^-21
                    small_int_to_float((int)((ts_ >> 20) & 0x3FFFFF)) * 1.1368683772161603e-13f;  // 2^-43
   float sn, cs;
+#if EMRI_FD_MIXED_SINCOSPIF
   sincospif(th, &sn, &cs);
+#else
+  __sincosf(th * 3.14159265358979f, &sn, &cs);
+#endif
   float are = ((Am.re[3] * uf + Am.re[2]) * uf + Am.re[1]) * uf + Am.re[0];
   float aim = ((Am.im[3] * uf + Am.im[2]) * uf + Am.im[1]) * uf + Am.im[0];
   are *= wgt;
@@ -350,6 +354,10 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
 // workload).  The extended form's FP64 kernel keeps two.
 #ifndef EMRI_FD_SPA64_MINB
 #define EMRI_FD_SPA64_MINB 3
+#endif
+// 1: the mixed form takes e^{i psi} from sincospif; 0: from the hardware sine and cosine
+#ifndef EMRI_FD_MIXED_SINCOSPIF
+#define EMRI_FD_MIXED_SINCOSPIF 0
 #endif
 // 1: the FP64 kernel's loop over a lane's bins is rolled (one copy of the body), as in
 // the FP32-path kernels; 0: unrolled

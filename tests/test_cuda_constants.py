@@ -48,6 +48,7 @@ def _cases(mp):
         ("spa.cu", r"\* " + f + r"f \+\s+// 2\^-21", two ** -21, "f32"),
         ("spa.cu", r"\* " + f + r"f;\s+// 2\^-43", two ** -43, "f32"),
         ("td.cu", r"\* " + f + r"f;\s+// 2 pi / 2\^32", 2 * pi / two ** 32, "f32"),
+        ("spa.cu", r"__sincosf\(th \* " + f + r"f, &sn", pi, "f32"),
         ("adjoint.cu", r"kTwoPi = " + f + ";", 2 * pi, "f64"),
         ("adjoint.cu", r"kInv2Pi = " + f + ";", 1 / (2 * pi), "f64"),
         ("prep.cu", r"kTwoPi = " + f + ";", 2 * pi, "f64"),
