@@ -249,8 +249,9 @@ struct DevInputs {
   void *h_plus, *h_cross;
 };
 
-// per knot segment of a waveform: the u-coefficients (c1, c2, c3, 0) of the four
-// fundamental series (Phi_phi, Phi_r, Omega_phi, Omega_r) and, as Q0.64 turns,
+// per knot segment of a waveform: the u-coefficients (c1, c2, c3, .) of the four
+// fundamental series (Phi_phi, Phi_r, Omega_phi, Omega_r; the fourth slot holds
+// sqrt(h) in the Phi_phi record and 0 in the others) and, as Q0.64 turns,
 // frac(Phi_phi_s / 2 pi), frac(Phi_r_s / 2 pi) and frac(phi / 2 pi)
 struct FundSeg {
   dbl4 P[4];

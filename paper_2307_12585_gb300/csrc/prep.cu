@@ -364,7 +364,9 @@ __global__ void k_spline_solve(int n_wf, const WfInfo* wf, const ModeInfo* modes
       double c[4];
       ucoef(ys[s], ys[s + 1], Ms[s], Ms[s + 1], h * h, c);
       FundSeg* F = fund + W.ko + s;
-      F->P[which] = mk_dbl4(c[1], c[2], c[3], 0.0);
+      // the fourth slot of the Phi_phi record carries sqrt(h), which every mode's
+      // amplitude record of this segment needs (one square root per segment, not per mode)
+      F->P[which] = mk_dbl4(c[1], c[2], c[3], which == 0 ? sqrt(h) : 0.0);
       dd x;
       if (which < 2) x = dd_mul(dd{ys[s], 0.0}, dd{kInv2PiHi, kInv2PiLo});
       else if (which == 2) x = dd_mul(dd{in.phi[w], 0.0}, dd{kInv2PiHi, kInv2PiLo});
@@ -412,15 +414,15 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
   const double dm = (double)m, dn = (double)n;
   SegCore C;
   C.A = knot_freq(m, n, in.omega_phi[i0], in.omega_r[i0]);
-  C.b = (dm * cOp.x + dn * cOr.x) * kInv2PiHi;
-  C.c = (dm * cOp.y + dn * cOr.y) * kInv2PiHi;
-  C.d = (dm * cOp.z + dn * cOr.z) * kInv2PiHi;
+  C.b = fma(dm, cOp.x, dn * cOr.x) * kInv2PiHi;
+  C.c = fma(dm, cOp.y, dn * cOr.y) * kInv2PiHi;
+  C.d = fma(dm, cOp.z, dn * cOr.z) * kInv2PiHi;
   C.c2 = 2.0 * C.c;
   C.d3 = 3.0 * C.d;
-  double P1 = (dm * cPp.x + dn * cPr.x) * kInv2PiHi;
+  double P1 = fma(dm, cPp.x, dn * cPr.x) * kInv2PiHi;
   C.Q1 = fma(-C.A, h, P1);
-  C.P2 = (dm * cPp.y + dn * cPr.y) * kInv2PiHi;
-  C.P3 = (dm * cPp.z + dn * cPr.z) * kInv2PiHi;
+  C.P2 = fma(dm, cPp.y, dn * cPr.y) * kInv2PiHi;
+  C.P3 = fma(dm, cPp.z, dn * cPr.z) * kInv2PiHi;
   C.h = h;
   C.ts = ts;
   // theta0 = frac((m Phi_phi_s + n Phi_r_s - m phi)/2pi): integer combination of
@@ -431,14 +433,15 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
   if (amp32) C.theta0 -= q64_mul(C.A, ts);
   C.bf = d2f_bits(C.b); C.cf = d2f_bits(C.c); C.df = d2f_bits(C.d);   // truncated: start values only
   {
-    const float r = C.b != 0.0 ? (float)(1.0 / C.b) : 0.f;
+    const float r = C.bf != 0.f ? 1.f / C.bf : 0.f;   // FP32: it only scales the FP32 start value
     C.rbf = (fabsf(r) < 1e30f && fabsf(r) > 1e-30f) ? r : 0.f;
   }
   core[r] = C;
   if (yk) yk[r] = 0.47746482927568600731 / h;   // 3/(2 pi h), extended SPA
 
-  // amplitude, scaled by prefactor sqrt(h) (the weight is sqrt(h)/sqrt|dF/du|)
-  double sc = in.prefactor[lo] * sqrt(h);
+  // amplitude, scaled by prefactor sqrt(h) (the weight is sqrt(h)/sqrt|dF/du|); sqrt(h)
+  // from the segment's fundamental record
+  double sc = in.prefactor[lo] * cPp.w;
   const double* am = ampM + 2 * (Mi.key_base + s);
   const double* ay = in.amp + 2 * (Mi.key_base + s);
   double cre[4], cim[4];
@@ -460,7 +463,7 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
     put_ff(X.A, C.A); put_ff(X.b, C.b); put_ff(X.c, C.c); put_ff(X.d, C.d);
     put_ff(X.c2, C.c2); put_ff(X.d3, C.d3);
     put_ff(X.Q1, C.Q1); put_ff(X.P2, C.P2); put_ff(X.P3, C.P3); put_ff(X.h, h);
-    const double sh = sqrt(h);
+    const double sh = cPp.w;   // sqrt(h)
     for (int q = 0; q < 4; q++) { put_ff(X.are[q], sh * cre[q]); put_ff(X.aim[q], sh * cim[q]); }
     segff[r] = X;
   }
