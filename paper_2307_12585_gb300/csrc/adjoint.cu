@@ -39,17 +39,23 @@ __global__ void k_residual(const WfInfo* wf, const double2* hp, const double2* h
   const double df = dfs[blockIdx.y];
   double acc = 0.0;
   int bad = 0;
+  const double c4 = 4.0 * df;
   for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
     const double S = psd[b];
-    if (!(S > 0.0) || !isfinite(S)) bad = ST_NONFINITE;
+    // S positive and finite, tested on its bits as a signed integer (0 < bits < +inf's)
+    // so that the test takes no FP64-pipe slots
+    const long long sb = __double_as_longlong(S);
+    if (!(sb > 0 && sb < 0x7ff0000000000000LL)) bad = ST_NONFINITE;
     const double2 a = hp[b], c = hc[b], x = dp[b], y = dc[b];
     const double rpr = x.x - a.x, rpi = x.y - a.y, rcr = y.x - c.x, rci = y.y - c.y;
-    const double w = 4.0 * df * rcp_d(S);
-    acc += (rpr * rpr + rpi * rpi + rcr * rcr + rci * rci) * (-0.5 * w);
+    const double w = c4 * rcp_d(S);
+    acc = fma(rpr * rpr + rpi * rpi + rcr * rcr + rci * rci, w, acc);
     G[b] = mk_dbl4(w * rpr, w * rpi, w * rcr, w * rci);
   }
   if (bad) atomicOr(status, bad);
-  red[threadIdx.x] = acc;
+  // -1/2 once per thread: a power of two, so every partial is the same as with -w/2
+  // applied per bin
+  red[threadIdx.x] = -0.5 * acc;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
@@ -86,17 +92,6 @@ __global__ void k_item_len(const int* run_total, const Run* runs, long long run_
   len[r] = v;
 }
 
-// first index b in [lo, hi) with pred(b) true, for a monotone predicate
-// (false...false true...true); hi if none
-template <typename P>
-__device__ __forceinline__ long long first_true(long long lo, long long hi, P pred) {
-  while (lo < hi) {
-    long long c = (lo + hi) >> 1;
-    if (pred(c)) hi = c; else lo = c + 1;
-  }
-  return lo;
-}
-
 // One adjoint item: a (run, segment) pair, with the bins of both branch signs that it
 // covers and per-segment constants of its derivatives
 struct __align__(16) AdjItem {
@@ -122,6 +117,7 @@ struct AdjParams {
   long long run_cap;
   AdjItem* items;          // [item_cap]
   long long* adj_off;      // [item_cap + 1] exclusive scan of the items' bin counts (the bin stream)
+  long long* adj_blk;      // [item blocks + 1] bins per block of kAdjItemBlock items, scanned
   long long item_cap;
   double* bnd;             // [warps][2][16]
   int* bnd_id;             // [warps][2]
@@ -142,16 +138,14 @@ __device__ __forceinline__ long long last_le(const T* off, long long n, long lon
   return lo;
 }
 
-// items: one thread per item slot; the run and segment of the item, the bins it
-// covers (knot s passed for s > s0, knot s + 1 not passed for s < s1, as the output
-// kernel assigns them), its sub-piece and the per-segment constants.  Slots past
-// the item count get zero bins.
-__global__ void k_adj_items(AdjParams P) {
-  const long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (it >= P.item_cap) return;
+// one item slot: the run and segment of the item, the bins it covers (knot s passed
+// for s > s0, knot s + 1 not passed for s < s1, as the output kernel assigns them), its
+// sub-piece and the per-segment constants.  Returns the item's bin count; slots past
+// the item count, and every slot after a failed input check (the run lists are then
+// not valid), get zero bins.
+__device__ __forceinline__ long long adj_item(const AdjParams& P, long long it) {
   const long long nitems = P.item_off[P.run_cap];
-  // after a failed input check the run lists are not valid: no bins at all
-  if (it >= nitems || *P.status != 0) { P.adj_off[it] = 0; return; }
+  if (it >= nitems || *P.status != 0) return 0;
   const long long r = last_le(P.item_off, P.run_cap, it);
   const Run R = P.runs[r];
   const int s = R.s0 + (int)(it - P.item_off[r]);
@@ -159,27 +153,50 @@ __global__ void k_adj_items(AdjParams P) {
   const ModeInfo M = P.modes[R.mode];
   AdjItem I;
   I.run = (int)r; I.s = s; I.pad = 0;
-  int lo[2], hi[2];
+  // the bins of each branch sign, cut at knot s (for s > s0) and knot s + 1 (for
+  // s < s1): the first bin at which "knot passed" flips, found by binary search.  The
+  // (up to) four searches q = 2 sign + (0: knot s, 1: knot s + 1) advance in lockstep so
+  // that their loads overlap.
+  long long b0s[2], b1s[2], slo[4], shi[4], kk[4];
+  bool sneg[4], ssuf[4];
+#pragma unroll
   for (int sg = 0; sg < 2; sg++) {
-    const bool neg = sg == 1;
-    const long long b0 = neg ? B.b0n : B.b0p, b1 = neg ? B.b1n : B.b1p;
-    long long lo_b = b0, hi_b = b1;
-    if (b0 < b1) {
-      auto passed = [&](int k, long long b) {
-        const double f = P.freqs[b];
-        const long long key = ordkey(neg ? flip_sign(f) : f);
-        const long long kk = P.keyF[M.key_base + k];
-        return R.dir > 0 ? (kk <= key) : (kk >= key);
-      };
-      const bool suffix = (R.dir > 0) != neg;   // passed(k, b) holds on a suffix of the bins
-      if (s > R.s0) {
-        long long x = first_true(b0, b1, [&](long long b) { return suffix ? passed(s, b) : !passed(s, b); });
-        if (suffix) lo_b = x; else hi_b = x;
+    b0s[sg] = sg ? B.b0n : B.b0p;
+    b1s[sg] = sg ? B.b1n : B.b1p;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int sg = q >> 1, k = s + (q & 1);
+    const bool want = (b0s[sg] < b1s[sg]) && ((q & 1) ? (s < R.s1) : (s > R.s0));
+    slo[q] = b0s[sg];
+    shi[q] = want ? b1s[sg] : b0s[sg];   // an empty range: not searched
+    sneg[q] = sg == 1;
+    ssuf[q] = (R.dir > 0) != (sg == 1);   // "passed" holds on a suffix of the bins
+    kk[q] = want ? P.keyF[M.key_base + k] : 0;
+  }
+  for (;;) {
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (slo[q] < shi[q]) {
+        const long long c = (slo[q] + shi[q]) >> 1;
+        const double f = P.freqs[c];
+        const long long key = ordkey(sneg[q] ? flip_sign(f) : f);
+        const bool passed = R.dir > 0 ? (kk[q] <= key) : (kk[q] >= key);
+        if (passed == ssuf[q]) shi[q] = c; else slo[q] = c + 1;
+        any = true;
       }
-      if (s < R.s1) {
-        long long x = first_true(b0, b1, [&](long long b) { return suffix ? passed(s + 1, b) : !passed(s + 1, b); });
-        if (suffix) hi_b = min(hi_b, x); else lo_b = max(lo_b, x);
-      }
+    }
+    if (!any) break;
+  }
+  int lo[2], hi[2];
+#pragma unroll
+  for (int sg = 0; sg < 2; sg++) {
+    long long lo_b = b0s[sg], hi_b = b1s[sg];
+    if (lo_b < hi_b) {
+      const bool suffix = ssuf[2 * sg];
+      if (s > R.s0) { const long long x = slo[2 * sg]; if (suffix) lo_b = x; else hi_b = x; }
+      if (s < R.s1) { const long long x = slo[2 * sg + 1]; if (suffix) hi_b = min(hi_b, x); else lo_b = max(lo_b, x); }
     }
     if (hi_b < lo_b) hi_b = lo_b;
     lo[sg] = (int)lo_b;
@@ -189,8 +206,8 @@ __global__ void k_adj_items(AdjParams P) {
   // sub-piece of segment s that this run covers
   int piece = 0;
   if (s == R.s0) {
-    const SegCrit X = P.crit[M.seg_base + s];
-    for (int c = 0; c < X.n; c++) if (X.u[c] <= R.u0) piece++;
+    const SegCrit X = P.crit[M.seg_base + s];   // at most two critical points
+    piece = (X.n > 0 && X.u[0] <= R.u0) + (X.n > 1 && X.u[1] <= R.u0);
   }
   I.piece = piece;
   const SegAmp64 Am = P.amp64[M.seg_base + s];
@@ -198,7 +215,50 @@ __global__ void k_adj_items(AdjParams P) {
   I.a3r = 3.0 * Am.re[3]; I.a2r = 2.0 * Am.re[2]; I.a3i = 3.0 * Am.im[3]; I.a2i = 2.0 * Am.im[2];
   I.d2c = 2.0 * C.d3; I.p2c = 2.0 * C.P2; I.p3c = 3.0 * C.P3; I.pad2 = 0.0;
   P.items[it] = I;
-  P.adj_off[it] = (long long)(hi[0] - lo[0]) + (hi[1] - lo[1]);
+  return (long long)(hi[0] - lo[0]) + (hi[1] - lo[1]);
+}
+
+// exclusive scan over the 256 threads of a CTA (int64); *total gets the CTA's sum
+__device__ __forceinline__ long long cta_exclusive_scan(long long v, long long* wsum, long long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  long long before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kAdjItemBlock / 32; w++) {
+    const long long t = wsum[w];
+    if (w < warp) before += t;
+    all += t;
+  }
+  *total = all;
+  return before + x - v;
+}
+
+// items, one thread per item slot, kAdjItemBlock slots per CTA: each slot's record
+// and bin count; the counts are scanned within the CTA (adj_off gets the offset of
+// the item inside its block) and the block's total goes to adj_blk
+__global__ void __launch_bounds__(kAdjItemBlock) k_adj_items(AdjParams P) {
+  __shared__ long long wsum[kAdjItemBlock / 32];
+  const long long it = blockIdx.x * (long long)kAdjItemBlock + threadIdx.x;
+  const long long n = it < P.item_cap ? adj_item(P, it) : 0;
+  long long total;
+  const long long e = cta_exclusive_scan(n, wsum, &total);
+  if (it < P.item_cap) P.adj_off[it] = e;
+  if (threadIdx.x == 0) P.adj_blk[blockIdx.x] = total;
+}
+
+// the bin stream's offsets: adj_off[i] += the scanned total of the blocks before i's
+// block; adj_off[item_cap] = the stream's length
+__global__ void k_adj_offsets(long long* adj_off, const long long* blk, long long item_cap) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < item_cap) adj_off[i] += blk[i / kAdjItemBlock];
+  else if (i == item_cap) adj_off[i] = blk[(item_cap + kAdjItemBlock - 1) / kAdjItemBlock];
 }
 
 // exclusive scan of cnt[0..n) in place (int64), total written to cnt[n]; one block of
@@ -474,33 +534,44 @@ __global__ void k_adj_fixup(AdjParams P, long long nw) {
 // amplitude part to the unscaled spline coefficients (the record holds
 // prefactor sqrt(h) scale times them, and the sums were formed with alpha and
 // beta over the mode's scale)
+// four threads per (mode, segment) record, each taking four of its 16 coefficients
+// (q = 4j .. 4j + 3) in 16-byte loads: the three sub-piece slots are summed and the
+// amplitude coefficients (q >= 8) scaled by prefactor sqrt(h) scale
 __global__ void k_seg_sum(long long seg_total, const WfInfo* wf, const ModeInfo* modes, int n_wf, const SegCore* core,
                           const double* pref, double* slots) {
-  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long tidg = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long r = tidg >> 2;
+  const int j = (int)(tidg & 3);
   if (r >= seg_total) return;
-  int lo = 0, hi = n_wf - 1;
-  while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (wf[mid].seg_base <= r) lo = mid; else hi = mid - 1; }
-  double* a = slots + r * 3 * 16;
-  const WfInfo W = wf[lo];
-  const ModeInfo& M = modes[W.mo + (r - W.seg_base) / (W.K - 1)];
-  const double sc = pref[lo] * sqrt(core[r].h) * M.scale;
-  for (int q = 0; q < 16; q++) {
-    double v = a[q] + a[16 + q] + a[32 + q];
-    a[q] = q >= 8 ? v * sc : v;
+  double2* a = reinterpret_cast<double2*>(slots + r * 3 * 16 + 4 * j);
+  const double2 x0 = a[0], x1 = a[1], y0 = a[8], y1 = a[9], z0 = a[16], z1 = a[17];
+  double2 v0 = make_double2(x0.x + y0.x + z0.x, x0.y + y0.y + z0.y);
+  double2 v1 = make_double2(x1.x + y1.x + z1.x, x1.y + y1.y + z1.y);
+  if (j >= 2) {
+    int lo = 0, hi = n_wf - 1;
+    while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (wf[mid].seg_base <= r) lo = mid; else hi = mid - 1; }
+    const WfInfo W = wf[lo];
+    const ModeInfo& M = modes[W.mo + (r - W.seg_base) / (W.K - 1)];
+    const double sc = pref[lo] * sqrt(core[r].h) * M.scale;
+    v0.x *= sc; v0.y *= sc; v1.x *= sc; v1.y *= sc;
   }
+  a[0] = v0;
+  a[1] = v1;
 }
 
 // u-coefficient gradients (a, b, c, d) of segment s -> gradients of
 // (y_s, y_{s+1}, M_s, M_{s+1}), with a = y_s, b = y_{s+1} - y_s - h^2 (2 M_s + M_{s+1})/6,
 // c = h^2 M_s / 2, d = h^2 (M_{s+1} - M_s)/6; accumulated per knot
+// (1/3 and 1/6 as products with their nearest doubles: no FP64 divisions)
 __device__ __forceinline__ void ucoef_adj(const double* gq, double h2, int side, double& gy, double& gM) {
+  constexpr double kThird = 1.0 / 3.0, kSixth = 1.0 / 6.0;
   const double ga = gq[0], gb = gq[1], gc = gq[2], gd = gq[3];
   if (side == 0) {   // the segment starting at this knot
     gy += ga - gb;
-    gM += h2 * (-gb / 3.0 + 0.5 * gc - gd / 6.0);
+    gM += h2 * (-gb * kThird + 0.5 * gc - gd * kSixth);
   } else {           // the segment ending at this knot
     gy += gb;
-    gM += h2 * (-gb / 6.0 + gd / 6.0);
+    gM += h2 * ((gd - gb) * kSixth);
   }
 }
 
@@ -535,7 +606,7 @@ __global__ void k_amp_knot(long long amp_total, int n_wf, const WfInfo* wf, cons
 // waveform's modes; writes u-coefficient gradients of Phi_phi, Phi_r (rad) and
 // Om_phi, Om_r (rad/s) for that segment: [4 series][4]
 __global__ void k_fund_seg(const WfInfo* wf, const ModeInfo* modes, const double* slots, double* fseg) {
-  __shared__ double red[256][16];
+  __shared__ double red[256][17];   // a 17-double row stride: no shared-memory bank conflicts
   const WfInfo W = wf[blockIdx.y];
   const int s = blockIdx.x;
   if (s >= W.K - 1) return;
@@ -719,19 +790,23 @@ void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& 
   p.wf = s.wf; p.modes = s.modes; p.core = s.core; p.amp64 = s.amp64; p.crit = s.crit; p.keyF = s.keyF;
   p.runs = s.runs; p.rb = s.rbins; p.freqs = in.freqs; p.G = reinterpret_cast<const dbl4*>(s.Gbuf);
   p.item_off = s.item_off; p.run_cap = s.run_cap; p.tab = s.tab; p.slots = s.slots; p.status = s.status;
-  p.items = static_cast<AdjItem*>(s.adj_items); p.adj_off = s.adj_off; p.bnd = s.adj_bnd; p.bnd_id = s.adj_bnd_id;
+  p.items = static_cast<AdjItem*>(s.adj_items); p.adj_off = s.adj_off; p.adj_blk = s.adj_blk; p.bnd = s.adj_bnd; p.bnd_id = s.adj_bnd_id;
   p.nm_total = cs.nm_total; p.seg_total = cs.seg_total; p.nf_total = cs.nf_total;
   // the item slots of this call's segments (at most three runs touch a segment)
   p.item_cap = 3 * cs.seg_total;
-  k_adj_items<<<(unsigned)((p.item_cap + 255) / 256 + 1), 256, 0, st>>>(p);
-  k_scan64<<<1, 1024, 0, st>>>(s.adj_off, p.item_cap);
+  // the bin stream: per-block scans of the items' bin counts, a scan of the block
+  // totals, then each item's offset
+  const long long nblk = (p.item_cap + kAdjItemBlock - 1) / kAdjItemBlock;
+  k_adj_items<<<(unsigned)nblk, kAdjItemBlock, 0, st>>>(p);
+  k_scan64<<<1, 1024, 0, st>>>(s.adj_blk, nblk);
+  k_adj_offsets<<<(unsigned)((p.item_cap + 256) / 256), 256, 0, st>>>(s.adj_off, s.adj_blk, p.item_cap);
   const size_t smem = (size_t)kAdjWarpsPerCta * 64 * (16 * sizeof(double) + sizeof(int));
   cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const long long nw = (long long)num_sms * kAdjCtasPerSm * kAdjWarpsPerCta;
   k_adjoint<<<(unsigned)(num_sms * kAdjCtasPerSm), 32 * kAdjWarpsPerCta, smem, st>>>(p);
   k_adj_fixup<<<(unsigned)((nw + 127) / 128), 128, 0, st>>>(p, nw);
-  k_seg_sum<<<(unsigned)((cs.seg_total + 255) / 256), 256, 0, st>>>(cs.seg_total, s.wf, s.modes, cs.n_wf, s.core,
-                                                                    in.prefactor, s.slots);
+  k_seg_sum<<<(unsigned)((4 * cs.seg_total + 255) / 256), 256, 0, st>>>(cs.seg_total, s.wf, s.modes, cs.n_wf,
+                                                                        s.core, in.prefactor, s.slots);
   k_amp_knot<<<(unsigned)((cs.amp_total + 255) / 256), 256, 0, st>>>(cs.amp_total, cs.n_wf, s.wf, s.modes, in.t,
                                                                      s.slots, s.agY, s.agM);
   dim3 gs(cs.max_K, cs.n_wf);

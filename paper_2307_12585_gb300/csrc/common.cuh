@@ -291,6 +291,7 @@ struct DevScratch {
   int* item_off;                  // [run_cap + 1] adjoint items (run, segment), scanned
   void* adj_items;                // [3 seg_cap] AdjItem records (adjoint.cu)
   long long* adj_off;             // [3 seg_cap + 1] bins per item, exclusive-scanned: the adjoint's bin stream
+  long long* adj_blk;             // [item blocks + 1] bins per block of kAdjItemBlock items, exclusive-scanned
   double* adj_bnd;                // [adjoint warps][2][16] partial sums of items cut by a warp's range
   int* adj_bnd_id;                // [adjoint warps][2] their items (-1: none, -2: the warp's range is empty)
   long long adj_item_cap;         // 3 seg_cap
@@ -324,9 +325,10 @@ struct CallShape {
 
 constexpr int kLChunks = 512;      // per-waveform chunks of the likelihood's partial sums
 constexpr int kPrepKernels = 11;   // kernels launched by launch_prep (memsets excluded)
-constexpr int kAdjointKernels = 11; // kernels launched by launch_adjoint
+constexpr int kAdjointKernels = 12; // kernels launched by launch_adjoint
 constexpr int kAdjCtasPerSm = 2;     // resident CTAs of the adjoint kernel per SM (128 registers, 8 warps)
 constexpr int kAdjWarpsPerCta = 8;
+constexpr int kAdjItemBlock = 256;   // items per CTA of the item kernel (its local scan)
 size_t adjoint_item_bytes();        // sizeof(AdjItem)
 
 // freqs_ready (optional): an event the kernels that read in.freqs must wait for

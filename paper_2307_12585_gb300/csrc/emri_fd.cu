@@ -207,6 +207,7 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
       s.adj_items = ai;
     }
     AL(s.adj_off, s.adj_item_cap + 1);
+    AL(s.adj_blk, (s.adj_item_cap + kAdjItemBlock - 1) / kAdjItemBlock + 1);
     AL(s.adj_bnd, 32LL * kAdjCtasPerSm * kAdjWarpsPerCta * p->num_sms);
     AL(s.adj_bnd_id, 2LL * kAdjCtasPerSm * kAdjWarpsPerCta * p->num_sms);
     AL(s.slots, 48 * p->cap_seg);
