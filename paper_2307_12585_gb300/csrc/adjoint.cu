@@ -534,30 +534,8 @@ __global__ void k_adj_fixup(AdjParams P, long long nw) {
 // amplitude part to the unscaled spline coefficients (the record holds
 // prefactor sqrt(h) scale times them, and the sums were formed with alpha and
 // beta over the mode's scale)
-// four threads per (mode, segment) record, each taking four of its 16 coefficients
-// (q = 4j .. 4j + 3) in 16-byte loads: the three sub-piece slots are summed and the
-// amplitude coefficients (q >= 8) scaled by prefactor sqrt(h) scale
-__global__ void k_seg_sum(long long seg_total, const WfInfo* wf, const ModeInfo* modes, int n_wf, const SegCore* core,
-                          const double* pref, double* slots) {
-  const long long tidg = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long r = tidg >> 2;
-  const int j = (int)(tidg & 3);
-  if (r >= seg_total) return;
-  double2* a = reinterpret_cast<double2*>(slots + r * 3 * 16 + 4 * j);
-  const double2 x0 = a[0], x1 = a[1], y0 = a[8], y1 = a[9], z0 = a[16], z1 = a[17];
-  double2 v0 = make_double2(x0.x + y0.x + z0.x, x0.y + y0.y + z0.y);
-  double2 v1 = make_double2(x1.x + y1.x + z1.x, x1.y + y1.y + z1.y);
-  if (j >= 2) {
-    int lo = 0, hi = n_wf - 1;
-    while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (wf[mid].seg_base <= r) lo = mid; else hi = mid - 1; }
-    const WfInfo W = wf[lo];
-    const ModeInfo& M = modes[W.mo + (r - W.seg_base) / (W.K - 1)];
-    const double sc = pref[lo] * sqrt(core[r].h) * M.scale;
-    v0.x *= sc; v0.y *= sc; v1.x *= sc; v1.y *= sc;
-  }
-  a[0] = v0;
-  a[1] = v1;
-}
+// one coefficient of a (mode, segment) record's gradient: its three sub-piece slots summed
+__device__ __forceinline__ double slot_sum(const double* a, int q) { return a[q] + a[16 + q] + a[32 + q]; }
 
 // u-coefficient gradients (a, b, c, d) of segment s -> gradients of
 // (y_s, y_{s+1}, M_s, M_{s+1}), with a = y_s, b = y_{s+1} - y_s - h^2 (2 M_s + M_{s+1})/6,
@@ -572,33 +550,6 @@ __device__ __forceinline__ void ucoef_adj(const double* gq, double h2, int side,
   } else {           // the segment ending at this knot
     gy += gb;
     gM += h2 * ((gd - gb) * kSixth);
-  }
-}
-
-// amplitude series: per (mode, knot) -> gY, gM of Re and Im
-__global__ void k_amp_knot(long long amp_total, int n_wf, const WfInfo* wf, const ModeInfo* modes, const double* t,
-                           const double* slots, double* gY, double* gMv) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= amp_total) return;
-  int lo = 0, hi = n_wf - 1;
-  while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (wf[mid].amp_base <= i) lo = mid; else hi = mid - 1; }
-  const WfInfo W = wf[lo];
-  const long long rel = i - W.amp_base;
-  const long long jm = rel / W.K;
-  const int k = (int)(rel - jm * W.K);
-  const long long seg0 = W.seg_base + jm * (W.K - 1);
-  for (int part = 0; part < 2; part++) {
-    double gy = 0.0, gM = 0.0;
-    if (k < W.K - 1) {
-      const double h = t[W.ko + k + 1] - t[W.ko + k];
-      ucoef_adj(slots + (seg0 + k) * 3 * 16 + 8 + 4 * part, h * h, 0, gy, gM);
-    }
-    if (k > 0) {
-      const double h = t[W.ko + k] - t[W.ko + k - 1];
-      ucoef_adj(slots + (seg0 + k - 1) * 3 * 16 + 8 + 4 * part, h * h, 1, gy, gM);
-    }
-    gY[2 * i + part] = gy;
-    gMv[2 * i + part] = gM;
   }
 }
 
@@ -617,10 +568,11 @@ __global__ void k_fund_seg(const WfInfo* wf, const ModeInfo* modes, const double
     const double* a = slots + (M.seg_base + s) * 3 * 16;
     const double dm = (double)M.m, dn = (double)M.n;
     for (int k = 0; k < 4; k++) {
-      acc[k] += dm * a[4 + k];                 // Phi_phi
-      acc[4 + k] += dn * a[4 + k];             // Phi_r
-      acc[8 + k] += dm * kInv2Pi * a[k];       // Om_phi
-      acc[12 + k] += dn * kInv2Pi * a[k];      // Om_r
+      const double gp = slot_sum(a, 4 + k), gf = slot_sum(a, k);
+      acc[k] += dm * gp;                       // Phi_phi
+      acc[4 + k] += dn * gp;                   // Phi_r
+      acc[8 + k] += dm * kInv2Pi * gf;         // Om_phi
+      acc[12 + k] += dn * kInv2Pi * gf;        // Om_r
     }
   }
   for (int q = 0; q < 16; q++) red[threadIdx.x][q] = acc[q];
@@ -633,30 +585,11 @@ __global__ void k_fund_seg(const WfInfo* wf, const ModeInfo* modes, const double
   if (threadIdx.x < 16) fseg[(W.ko + s) * 16 + threadIdx.x] = red[0][threadIdx.x];
 }
 
-__global__ void k_fund_knot(int n_wf, const WfInfo* wf, const double* t, const double* fseg, long long K_total,
-                            double* gY, double* gMv) {
-  const WfInfo W = wf[blockIdx.y];
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= W.K) return;
-  for (int q = 0; q < 4; q++) {
-    double gy = 0.0, gM = 0.0;
-    if (k < W.K - 1) {
-      const double h = t[W.ko + k + 1] - t[W.ko + k];
-      ucoef_adj(fseg + (W.ko + k) * 16 + 4 * q, h * h, 0, gy, gM);
-    }
-    if (k > 0) {
-      const double h = t[W.ko + k] - t[W.ko + k - 1];
-      ucoef_adj(fseg + (W.ko + k - 1) * 16 + 4 * q, h * h, 1, gy, gM);
-    }
-    gY[q * K_total + W.ko + k] = gy;
-    gMv[q * K_total + W.ko + k] = gM;
-  }
-}
-
 // Transpose of the not-a-knot map y -> M (the forward solve of the preparation)
 // applied to gM, added to gY: out = gY + (dM/dy)^T gM.  One warp per series; the
 // two triangular sweeps of the transposed factorisation are warp scans of affine
-// maps, as in the forward solve.
+// maps, as in the forward solve.  On entry out[i os] holds gY_i and z[i os] gM_i,
+// each written by lane i mod 32.
 struct AffT { double p, q; };
 __device__ __forceinline__ AffT afft_after(const AffT& g, const AffT& f) {
   AffT r; r.p = g.p * f.p; r.q = fma(g.p, f.q, g.q); return r;
@@ -674,10 +607,8 @@ __device__ __forceinline__ double afft_scan_exclusive(AffT S, int lane) {
   return lane == 0 ? 0.0 : x;
 }
 
-__device__ void spline_adjoint_warp(const double* t, const double* ih, int K, const double* gY, long long ys,
-                                    const double* gM0, long long ms, const dbl4* fac, double* out, long long os,
-                                    double* z, int lane) {
-  for (int i = lane; i < K; i += 32) z[i * os] = gM0[i * ms];
+__device__ void spline_adjoint_warp(const double* t, const double* ih, int K, const dbl4* fac, double* out,
+                                    long long os, double* z, int lane) {
   __syncwarp();
   if (lane == 0) {
     // adjoint of M_0 = (1 + h0/h1) M_1 - (h0/h1) M_2 and of its mirror at the far end
@@ -732,7 +663,7 @@ __device__ void spline_adjoint_warp(const double* t, const double* ih, int K, co
     return 1.0;
   };
   for (int j = lane; j < K; j += 32) {
-    double v = gY[j * ys];
+    double v = out[j * os];   // gY_j, written by this lane
     if (j - 1 >= 1 && j - 1 <= K - 2) v += 6.0 * z[(j - 1) * os] * srow(j - 1) * ih[j - 1];
     if (j >= 1 && j <= K - 2) v -= 6.0 * z[j * os] * srow(j) * (ih[j] + ih[j - 1]);
     if (j + 1 <= K - 2) v += 6.0 * z[(j + 1) * os] * srow(j + 1) * ih[j];
@@ -740,9 +671,14 @@ __device__ void spline_adjoint_warp(const double* t, const double* ih, int K, co
   }
 }
 
+// One warp per series: the four fundamental series of each waveform, then the real and
+// imaginary amplitude series of each mode.  Each lane first maps the u-coefficient
+// gradients of the segments on either side of its knots to (y, M) gradients (for an
+// amplitude series: the record's three sub-piece slots summed, scaled by
+// prefactor sqrt(h) scale), then the warp applies the transposed not-a-knot solve.
 __global__ void k_spline_adj(int n_wf, const WfInfo* wf, const ModeInfo* modes, long long nm_total, const double* t,
-                             const dbl4* fac, const double* ihall, const double* fgY, const double* fgM,
-                             long long K_total, const double* agY, const double* agM, double* zf, double* za,
+                             const dbl4* fac, const double* ihall, const FundSeg* fund, const double* pref,
+                             const double* slots, const double* fseg, long long K_total, double* zf, double* za,
                              double* g_pp, double* g_pr, double* g_op, double* g_or, double* g_amp) {
   long long sid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -752,8 +688,23 @@ __global__ void k_spline_adj(int n_wf, const WfInfo* wf, const ModeInfo* modes, 
     const WfInfo W = wf[w];
     double* outp = q == 0 ? g_pp : q == 1 ? g_pr : q == 2 ? g_op : g_or;
     if (!outp) return;
-    spline_adjoint_warp(t + W.ko, ihall + W.ko, (int)W.K, fgY + q * K_total + W.ko, 1, fgM + q * K_total + W.ko, 1,
-                        fac + W.ko, outp + W.ko, 1, zf + q * K_total + W.ko, lane);
+    double* out = outp + W.ko;
+    double* z = zf + q * K_total + W.ko;
+    const double* tw = t + W.ko;
+    for (int i = lane; i < W.K; i += 32) {
+      double gy = 0.0, gM = 0.0;
+      if (i < W.K - 1) {
+        const double h = tw[i + 1] - tw[i];
+        ucoef_adj(fseg + (W.ko + i) * 16 + 4 * q, h * h, 0, gy, gM);
+      }
+      if (i > 0) {
+        const double h = tw[i] - tw[i - 1];
+        ucoef_adj(fseg + (W.ko + i - 1) * 16 + 4 * q, h * h, 1, gy, gM);
+      }
+      out[i] = gy;
+      z[i] = gM;
+    }
+    spline_adjoint_warp(tw, ihall + W.ko, (int)W.K, fac + W.ko, out, 1, z, lane);
     return;
   }
   sid -= nfund;
@@ -762,8 +713,34 @@ __global__ void k_spline_adj(int n_wf, const WfInfo* wf, const ModeInfo* modes, 
   int part = (int)(sid & 1);
   const ModeInfo M = modes[j];
   const WfInfo W = wf[M.wf];
-  spline_adjoint_warp(t + W.ko, ihall + W.ko, (int)W.K, agY + 2 * M.key_base + part, 2, agM + 2 * M.key_base + part, 2,
-                      fac + W.ko, g_amp + 2 * M.key_base + part, 2, za + 2 * M.key_base + part, lane);
+  double* out = g_amp + 2 * M.key_base + part;
+  double* z = za + 2 * M.key_base + part;
+  const double* tw = t + W.ko;
+  const double pw = pref[M.wf];
+  // the amplitude u-coefficient gradients of segment s, summed over its sub-pieces and
+  // scaled (sqrt(h) is the fourth entry of the knot segment's Phi_phi record)
+  auto seg_coef = [&](int s, double* g) {
+    const double* a = slots + (M.seg_base + s) * 3 * 16 + 8 + 4 * part;
+    const double sc = pw * fund[W.ko + s].P[0].w * M.scale;
+#pragma unroll
+    for (int c = 0; c < 4; c++) g[c] = slot_sum(a, c) * sc;
+  };
+  for (int i = lane; i < W.K; i += 32) {
+    double gy = 0.0, gM = 0.0, g[4];
+    if (i < W.K - 1) {
+      const double h = tw[i + 1] - tw[i];
+      seg_coef(i, g);
+      ucoef_adj(g, h * h, 0, gy, gM);
+    }
+    if (i > 0) {
+      const double h = tw[i] - tw[i - 1];
+      seg_coef(i - 1, g);
+      ucoef_adj(g, h * h, 1, gy, gM);
+    }
+    out[2 * i] = gy;
+    z[2 * i] = gM;
+  }
+  spline_adjoint_warp(tw, ihall + W.ko, (int)W.K, fac + W.ko, out, 2, z, lane);
 }
 
 }  // namespace
@@ -805,18 +782,12 @@ void launch_adjoint(const CallShape& cs, const DevInputs& in, const LikeInputs& 
   const long long nw = (long long)num_sms * kAdjCtasPerSm * kAdjWarpsPerCta;
   k_adjoint<<<(unsigned)(num_sms * kAdjCtasPerSm), 32 * kAdjWarpsPerCta, smem, st>>>(p);
   k_adj_fixup<<<(unsigned)((nw + 127) / 128), 128, 0, st>>>(p, nw);
-  k_seg_sum<<<(unsigned)((4 * cs.seg_total + 255) / 256), 256, 0, st>>>(cs.seg_total, s.wf, s.modes, cs.n_wf,
-                                                                        s.core, in.prefactor, s.slots);
-  k_amp_knot<<<(unsigned)((cs.amp_total + 255) / 256), 256, 0, st>>>(cs.amp_total, cs.n_wf, s.wf, s.modes, in.t,
-                                                                     s.slots, s.agY, s.agM);
   dim3 gs(cs.max_K, cs.n_wf);
   k_fund_seg<<<gs, 256, 0, st>>>(s.wf, s.modes, s.slots, s.fseg);
-  dim3 gk((cs.max_K + 127) / 128, cs.n_wf);
-  k_fund_knot<<<gk, 128, 0, st>>>(cs.n_wf, s.wf, in.t, s.fseg, cs.K_total, s.fgY, s.fgM);
   long long nser = 4LL * cs.n_wf + 2 * cs.nm_total;
   k_spline_adj<<<(unsigned)((nser * 32 + 255) / 256), 256, 0, st>>>(
-      cs.n_wf, s.wf, s.modes, cs.nm_total, in.t, s.spl_fac, s.spl_ih, s.fgY, s.fgM, cs.K_total, s.agY, s.agM, s.zf,
-      s.za, li.g_phi_phi, li.g_phi_r, li.g_omega_phi, li.g_omega_r, li.g_amp);
+      cs.n_wf, s.wf, s.modes, cs.nm_total, in.t, s.spl_fac, s.spl_ih, s.fund, in.prefactor, s.slots, s.fseg,
+      cs.K_total, s.zf, s.za, li.g_phi_phi, li.g_phi_r, li.g_omega_phi, li.g_omega_r, li.g_amp);
 }
 
 }  // namespace emrifd

@@ -296,8 +296,6 @@ struct DevScratch {
   int* adj_bnd_id;                // [adjoint warps][2] their items (-1: none, -2: the warp's range is empty)
   long long adj_item_cap;         // 3 seg_cap
   double* slots;                  // [sum N_m (K-1)][3 sub-pieces][16] per-segment gradients
-  double *agY, *agM;              // [sum N_m K][2] amplitude knot-value / second-derivative gradients
-  double *fgY, *fgM;              // [4][sum K] fundamental series, same
   double* fseg;                   // [sum K][16] fundamental u-coefficient gradients per segment
   double *zf, *za;                // transposed-solve work arrays
 };
@@ -325,7 +323,7 @@ struct CallShape {
 
 constexpr int kLChunks = 512;      // per-waveform chunks of the likelihood's partial sums
 constexpr int kPrepKernels = 11;   // kernels launched by launch_prep (memsets excluded)
-constexpr int kAdjointKernels = 12; // kernels launched by launch_adjoint
+constexpr int kAdjointKernels = 9; // kernels launched by launch_adjoint
 constexpr int kAdjCtasPerSm = 2;     // resident CTAs of the adjoint kernel per SM (128 registers, 8 warps)
 constexpr int kAdjWarpsPerCta = 8;
 constexpr int kAdjItemBlock = 256;   // items per CTA of the item kernel (its local scan)

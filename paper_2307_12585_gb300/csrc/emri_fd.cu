@@ -211,11 +211,7 @@ emri_fd_status emri_fd_plan(emri_fd_plan_t* out, const emri_fd_desc* d, void* st
     AL(s.adj_bnd, 32LL * kAdjCtasPerSm * kAdjWarpsPerCta * p->num_sms);
     AL(s.adj_bnd_id, 2LL * kAdjCtasPerSm * kAdjWarpsPerCta * p->num_sms);
     AL(s.slots, 48 * p->cap_seg);
-    AL(s.agY, 2 * p->cap_amp);
-    AL(s.agM, 2 * p->cap_amp);
     AL(s.za, 2 * p->cap_amp);
-    AL(s.fgY, 4 * p->cap_K);
-    AL(s.fgM, 4 * p->cap_K);
     AL(s.zf, 4 * p->cap_K);
     AL(s.fseg, 16 * p->cap_K);
   }
