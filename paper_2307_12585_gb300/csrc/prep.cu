@@ -184,6 +184,16 @@ __device__ __forceinline__ void ucoef(double y0, double y1, double M0, double M1
   c[3] = h2 * (M1 - M0) * (1.0 / 6.0);
 }
 
+// the same coefficients times sc, with sc folded into the h^2 factors (k6 = sc h^2/6,
+// k2 = sc h^2/2) instead of multiplying the four results
+__device__ __forceinline__ void ucoef_scaled(double y0, double y1, double M0, double M1, double sc, double k6,
+                                             double k2, double* c) {
+  c[0] = sc * y0;
+  c[1] = fma(-k6, fma(2.0, M0, M1), sc * (y1 - y0));
+  c[2] = k2 * M0;
+  c[3] = k6 * (M1 - M0);
+}
+
 // ---- warp-parallel forms of the two sequential sweeps (GB300's FP64 latency
 // makes a 200-step dependent chain per thread slow, so each sweep is written as
 // a scan over the warp: every lane composes its stretch of consecutive steps,
@@ -445,13 +455,15 @@ __global__ void k_seg_prep(int n_wf, const WfInfo* wf, const ModeInfo* modes, De
   const double* am = ampM + 2 * (Mi.key_base + s);
   const double* ay = in.amp + 2 * (Mi.key_base + s);
   double cre[4], cim[4];
-  ucoef(ay[0], ay[2], am[0], am[2], h2, cre);
-  ucoef(ay[1], ay[3], am[1], am[3], h2, cim);
   if (amp64) {   // FP64 records also carry the mode's polarisation scale
     SegAmp64 A;
-    const double sc64 = sc * Mi.scale;
-    for (int q = 0; q < 4; q++) { A.re[q] = sc64 * cre[q]; A.im[q] = sc64 * cim[q]; }
+    const double sc64 = sc * Mi.scale, sh2 = sc64 * h2, k6 = sh2 * (1.0 / 6.0), k2 = 0.5 * sh2;
+    ucoef_scaled(ay[0], ay[2], am[0], am[2], sc64, k6, k2, A.re);
+    ucoef_scaled(ay[1], ay[3], am[1], am[3], sc64, k6, k2, A.im);
     amp64[r] = A;
+  } else {
+    ucoef(ay[0], ay[2], am[0], am[2], h2, cre);
+    ucoef(ay[1], ay[3], am[1], am[3], h2, cim);
   }
   if (amp32) {
     SegAmp32 A;

@@ -541,8 +541,16 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
           const long long lo_b = max((long long)b0, bin0), hi_b = min((long long)b1, binEnd) - 1;
           const double flo = P.freqs[lo_b], fhi = P.freqs[hi_b];
           const int s_lo = run_segment_warp(R, P.keyF, M.key_base, ordkey(neg ? flip_sign(flo) : flo), lane);
-          const int s_hi = run_segment_warp(R, P.keyF, M.key_base, ordkey(neg ? flip_sign(fhi) : fhi), lane);
-          s_uni = s_lo == s_hi ? s_lo : -1;
+          // the last bin is in segment s_lo when it has passed knot s_lo (or s_lo is the
+          // run's first segment) and not knot s_lo + 1 (or s_lo is the last): the
+          // segment is monotone in the bin, so every bin between is in s_lo too
+          const long long khi = ordkey(neg ? flip_sign(fhi) : fhi);
+          auto passed = [&](int k) {
+            const long long kk = P.keyF[M.key_base + k];
+            return R.dir > 0 ? (kk <= khi) : (kk >= khi);
+          };
+          const bool in_lo = (s_lo == R.s0 || passed(s_lo)) && (s_lo == R.s1 || !passed(s_lo + 1));
+          s_uni = in_lo ? s_lo : -1;
         }
         if constexpr (PREC == 0) {
           // h+ += alpha Z~, hx += i beta Z~ (conjugates on the negative branch).  The
