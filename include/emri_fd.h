@@ -334,8 +334,8 @@ emri_fd_status emri_fd_profile(emri_fd_plan_t plan, int enable);
  *   passed by value.  Every array must be DEVICE memory (host pointers give
  *   EMRI_FD_ERR_ARG).  stream: a cudaStream_t on the current device.
  *   Set-up: the first call on a device (with that device current) looks up the
- *   array's device address and fills a sin/cos table in it; make that first
- *   call before any stream capture.  The set-up is kept per device ordinal for
+ *   array's device address and fills a sin/cos table in it, synchronising the
+ *   stream.  The set-up is kept per device ordinal for
  *   the life of the process: it does not survive cudaDeviceReset (or any other
  *   teardown of the device's primary context), after which this entry point
  *   must not be called again in that process.
