@@ -542,17 +542,18 @@ struct SubPieces {
   double ua[3], ub[3], Fa[3], Fb[3];
 };
 
+// (fixed indices and selects: X.n <= 2, so the pieces stay in registers)
 __device__ __forceinline__ void sub_pieces(const SegCrit& X, double F0, double F1, SubPieces& P) {
-  double us[4], Fs[4];
-  int np = 0;
-  us[np] = 0.0; Fs[np++] = F0;
-  for (int i = 0; i < X.n; i++) { us[np] = X.u[i]; Fs[np++] = X.F[i]; }
-  us[np] = 1.0; Fs[np++] = F1;
-  P.n = np - 1;
-  for (int i = 0; i < P.n; i++) {
-    P.ua[i] = us[i]; P.ub[i] = us[i + 1]; P.Fa[i] = Fs[i]; P.Fb[i] = Fs[i + 1];
-    P.dir[i] = Fs[i + 1] > Fs[i] ? 1 : (Fs[i + 1] < Fs[i] ? -1 : 0);
-  }
+  const bool c1 = X.n > 0, c2 = X.n > 1;
+  P.n = X.n + 1;
+  P.ua[0] = 0.0;      P.Fa[0] = F0;
+  P.ub[0] = c1 ? X.u[0] : 1.0;  P.Fb[0] = c1 ? X.F[0] : F1;
+  P.ua[1] = X.u[0];   P.Fa[1] = X.F[0];
+  P.ub[1] = c2 ? X.u[1] : 1.0;  P.Fb[1] = c2 ? X.F[1] : F1;
+  P.ua[2] = X.u[1];   P.Fa[2] = X.F[1];
+  P.ub[2] = 1.0;      P.Fb[2] = F1;
+#pragma unroll
+  for (int i = 0; i < 3; i++) P.dir[i] = P.Fb[i] > P.Fa[i] ? 1 : (P.Fb[i] < P.Fa[i] ? -1 : 0);
 }
 
 // warp per mode; FILL=false counts runs into run_cnt, FILL=true writes them
@@ -581,14 +582,16 @@ __global__ void k_runs(const WfInfo* wf, const ModeInfo* modes, long long nm_tot
       sub_pieces(X, C.A, F1, P);
     }
     int first_dir = (valid && P.n > 0) ? P.dir[0] : 0;
-    int last_dir = (valid && P.n > 0) ? P.dir[P.n - 1] : 0;
+    int last_dir = (valid && P.n > 0) ? (P.n == 1 ? P.dir[0] : P.n == 2 ? P.dir[1] : P.dir[2]) : 0;
     int prev_last = __shfl_up_sync(0xffffffffu, last_dir, 1);
     if (lane == 0) prev_last = carry_dir;
     int next_first = __shfl_down_sync(0xffffffffu, first_dir, 1);
     if (lane == 31 || s + 1 >= nseg) next_first = 0;   // next chunk's first handled by its own start test
     int starts = 0;
     int pd = prev_last;
-    for (int i = 0; i < P.n; i++) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      if (i >= P.n) break;
       if (P.dir[i] != 0 && P.dir[i] != pd) starts++;
       pd = P.dir[i];
     }
@@ -603,7 +606,9 @@ __global__ void k_runs(const WfInfo* wf, const ModeInfo* modes, long long nm_tot
     if (FILL && valid) {
       int idx = carry_cnt + excl;     // runs started before this segment (within the mode)
       pd = prev_last;
-      for (int i = 0; i < P.n; i++) {
+#pragma unroll
+      for (int i = 0; i < 3; i++) {
+        if (i >= P.n) break;
         int d = P.dir[i];
         if (d != 0 && d != pd) {
           long long rid = base + idx;
@@ -621,7 +626,7 @@ __global__ void k_runs(const WfInfo* wf, const ModeInfo* modes, long long nm_tot
           idx++;
         }
         // end of a run: next sub-piece (in this segment or the next) has another direction
-        int nd = (i + 1 < P.n) ? P.dir[i + 1] : (s + 1 < nseg ? -2 : 0);
+        int nd = (i + 1 < P.n) ? P.dir[i < 2 ? i + 1 : 2] : (s + 1 < nseg ? -2 : 0);
         bool ends;
         if (nd == -2) {
           // first sub-piece of segment s+1: taken from the next lane, or re-derived at a chunk edge
