@@ -240,7 +240,7 @@ def job_rate(units_per_rank, world, ms):
 
 
 # tile sizes of the other forms on this workload (the fastest of 32/64/128 bins when measured)
-FORM_TILE = {"fp64x": 64, "mixed": 64}
+FORM_TILE = {"fp64x": 32, "mixed": 64}
 DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
 # DRAM bytes (read + write) of one k_spa<4,0,0> launch (FP64, standard SPA, 128-bin tiles) on
 # this workload, from one ncu capture of the kernel as it stands
