@@ -1,8 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-FP64 form: relative L2 <= 1e-10 per channel (h+ and hx), the tolerance the
-benchmark spec of the method fixes; integer work (which bins a branch
-covers, mode-bin counts) is compared exactly.  Mixed form: <= 1e-5."""
+FP64 form: relative L2 <= 1e-10 per channel (h+ and hx), the FP64 parity bar of
+this path; integer work (which bins a branch covers, mode-bin counts) is compared
+exactly.  Mixed form: <= 1e-5."""
 import numpy as np
 import pytest
 
