@@ -66,6 +66,7 @@ struct SpaParams {
 template <int BPL, int PREC>
 struct Smem {
   int list[kListCap];
+  int suni[PREC == 0 ? 1 : kListCap];   // FP32-path kernels: each entry's segment when one holds all its tile bins
   int wsum[kWarps + 1];
   long long tile;
   int anyv[4];     // cluster members' "has entries" flags (tile split)
@@ -518,6 +519,40 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
       }
       if (rcur == 0) rcur = 1;   // no runs at all: leave the loop after this pass
 
+      // ---- FP32-path kernels: each entry's segment when one segment holds all of its
+      // tile bins (-1 otherwise), one thread per entry.  A search per thread, all of
+      // them at once, instead of each warp searching at the head of every entry it
+      // evaluates, where the search's dependent loads sat on the entry's critical path.
+      // The segment is monotone in the bin: the first bin's segment holds the last bin
+      // when that bin has passed the segment's first knot (or it is the run's first
+      // segment) and not its next knot (or it is the run's last).
+      if constexpr (PREC != 0) {
+        for (int e = tid; e < cnt; e += kThreads) {
+          const int ent = S.list[e];
+          const long long r = W.run_base + (ent >> 1);
+          const bool neg = ent & 1;
+          int su = -1;
+          if (r >= 0 && r < P.run_cap) {
+            const Run R = P.runs[r];
+            const RunBins B = P.rb[r];
+            const int b0 = neg ? B.b0n : B.b0p, b1 = neg ? B.b1n : B.b1p;
+            if (R.mode >= 0 && R.mode < P.nm_total && R.s0 >= 0 && R.s0 <= R.s1 && b0 >= 0 && b1 <= P.nf_total) {
+              const long long kb = P.modes[R.mode].key_base;
+              const long long lo_b = max((long long)b0, bin0), hi_b = min((long long)b1, binEnd) - 1;
+              const double flo = P.freqs[lo_b], fhi = P.freqs[hi_b];
+              const int s_lo = run_segment(R, P.keyF, kb, ordkey(neg ? flip_sign(flo) : flo));
+              const long long khi = ordkey(neg ? flip_sign(fhi) : fhi);
+              auto passed = [&](int k) {
+                const long long kk = P.keyF[kb + k];
+                return R.dir > 0 ? (kk <= khi) : (kk >= khi);
+              };
+              if ((s_lo == R.s0 || passed(s_lo)) && (s_lo == R.s1 || !passed(s_lo + 1))) su = s_lo;
+            }
+          }
+          S.suni[e] = su;
+        }
+        __syncthreads();
+      }
       // ---- evaluate: warp w takes entries w, w + kWarps, ...
       for (int e = warp; e < cnt; e += kWarps) {
         const int ent = S.list[e];
@@ -532,26 +567,10 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
                         P.status))
           continue;
         const ModeInfo M = P.modes[R.mode];
-        // a5 for the whole warp (FP32-path kernels, which are issue-bound; in the FP64
-        // kernel the per-bin integer search overlaps the FP64 pipe for free): when the
-        // first and last of the tile's bins this entry covers lie in one segment,
-        // every bin between does too
-        int s_uni = -1;
-        if constexpr (PREC != 0) {
-          const long long lo_b = max((long long)b0, bin0), hi_b = min((long long)b1, binEnd) - 1;
-          const double flo = P.freqs[lo_b], fhi = P.freqs[hi_b];
-          const int s_lo = run_segment_warp(R, P.keyF, M.key_base, ordkey(neg ? flip_sign(flo) : flo), lane);
-          // the last bin is in segment s_lo when it has passed knot s_lo (or s_lo is the
-          // run's first segment) and not knot s_lo + 1 (or s_lo is the last): the
-          // segment is monotone in the bin, so every bin between is in s_lo too
-          const long long khi = ordkey(neg ? flip_sign(fhi) : fhi);
-          auto passed = [&](int k) {
-            const long long kk = P.keyF[M.key_base + k];
-            return R.dir > 0 ? (kk <= khi) : (kk >= khi);
-          };
-          const bool in_lo = (s_lo == R.s0 || passed(s_lo)) && (s_lo == R.s1 || !passed(s_lo + 1));
-          s_uni = in_lo ? s_lo : -1;
-        }
+        // a5 for the whole entry where one segment holds all its tile bins (FP32-path
+        // kernels, found in the setup step above; in the FP64 kernel the per-bin integer
+        // search overlaps the FP64 pipe for free)
+        const int s_uni = PREC != 0 ? S.suni[e] : -1;
         if constexpr (PREC == 0) {
           // h+ += alpha Z~, hx += i beta Z~ (conjugates on the negative branch).  The
           // amplitude record carries the factor scale (alpha or beta, the larger in

@@ -49,29 +49,6 @@ __device__ __forceinline__ int run_segment(const Run& R, const long long* keyF, 
   return a - 1;
 }
 
-// a5, one warp, all lanes with the same key: the same segment as run_segment,
-// found with ballots over up to 32 probes per round (two rounds for runs of up
-// to 1024 segments).  "Passed" is monotone along the run, so the probes that
-// pass are a prefix; each round narrows the search to the chunk after the
-// last passed probe.
-__device__ __forceinline__ int run_segment_warp(const Run& R, const long long* keyF, long long key_base,
-                                                long long key, int lane) {
-  int base = 0, len = R.s1 - R.s0;   // candidates: knots s0 + 1 + base .. s0 + base + len
-  while (len > 0) {
-    const int step = (len + 31) >> 5;
-    bool passed = false;
-    if (lane * step < len) {
-      const long long kk = keyF[key_base + R.s0 + 1 + base + lane * step];
-      passed = R.dir > 0 ? (kk <= key) : (kk >= key);
-    }
-    const int c = __popc(__ballot_sync(0xffffffffu, passed));
-    if (c == 0) break;
-    base += (c - 1) * step + 1;
-    len = min(step - 1, len - (c - 1) * step - 1);
-  }
-  return R.s0 + base;
-}
-
 // a6 fallback: bracketed Newton-bisection in FP64 on [ulo, uhi] for the rare
 // roots the fast path does not settle: next to a turnover the FP32 cubic can
 // lose the root altogether (its coefficients' rounding exceeds |F* - f|) and
