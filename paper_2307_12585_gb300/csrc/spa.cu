@@ -66,12 +66,16 @@ struct SpaParams {
 template <int BPL, int PREC>
 struct Smem {
   int list[kListCap];
-  int suni[PREC == 0 ? 1 : kListCap];   // FP32-path kernels: each entry's segment when one holds all its tile bins
   int wsum[kWarps + 1];
   long long tile;
   int anyv[4];     // cluster members' "has entries" flags (tile split)
   float2 pf;       // the waveform's prefactor as an FP32 pair (FP64X)
-  double red[kWarps][32 * BPL][4];   // FP64 partials, or FP32-pair partials in the same bytes
+  // The two are never live together: suni while a pass evaluates its entries, red after
+  // a tile's last pass (barriers separate the uses), so they share their bytes.
+  union {
+    int suni[kListCap];                // FP32-path kernels: each entry's segment when one holds all its tile bins
+    double red[kWarps][32 * BPL][4];   // FP64 partials, or FP32-pair partials in the same bytes
+  };
 };
 
 // FP64X per-(branch, bin) body: returns the four increments (h+ re, h+ im,
