@@ -73,10 +73,15 @@ struct Smem {
   // The two are never live together: suni while a pass evaluates its entries, red after
   // a tile's last pass (barriers separate the uses), so they share their bytes.
   union {
-    int suni[kListCap];                // FP32-path kernels: each entry's segment when one holds all its tile bins
+    struct {
+      int suni[kListCap];              // FP32-path kernels: each entry's segment when one holds all its tile bins
+      int smode[BPL >= 2 ? kListCap : 1];   // and (tiles of 64 bins or more) its run's mode
+    } ent;
     double red[kWarps][32 * BPL][4];   // FP64 partials, or FP32-pair partials in the same bytes
   };
 };
+// the entry table fits in the reduction buffer (with the mode only where it has room)
+static_assert(sizeof(int) * (kListCap + kListCap) <= sizeof(double) * kWarps * 32 * 2 * 4, "entry table");
 
 // FP64X per-(branch, bin) body: returns the four increments (h+ re, h+ im,
 // hx re, hx im) as FP32 pairs in v[0..7]; false if the root has Fdot == 0
@@ -535,12 +540,13 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
           const int ent = S.list[e];
           const long long r = W.run_base + (ent >> 1);
           const bool neg = ent & 1;
-          int su = -1;
+          int su = -1, md = 0;
           if (r >= 0 && r < P.run_cap) {
             const Run R = P.runs[r];
             const RunBins B = P.rb[r];
             const int b0 = neg ? B.b0n : B.b0p, b1 = neg ? B.b1n : B.b1p;
             if (R.mode >= 0 && R.mode < P.nm_total && R.s0 >= 0 && R.s0 <= R.s1 && b0 >= 0 && b1 <= P.nf_total) {
+              md = R.mode;
               const long long kb = P.modes[R.mode].key_base;
               const long long lo_b = max((long long)b0, bin0), hi_b = min((long long)b1, binEnd) - 1;
               const double flo = P.freqs[lo_b], fhi = P.freqs[hi_b];
@@ -553,7 +559,8 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
               if ((s_lo == R.s0 || passed(s_lo)) && (s_lo == R.s1 || !passed(s_lo + 1))) su = s_lo;
             }
           }
-          S.suni[e] = su;
+          S.ent.suni[e] = su;
+          if constexpr (BPL >= 2) S.ent.smode[e] = md;
         }
         __syncthreads();
       }
@@ -570,11 +577,11 @@ __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT
                             b1 <= P.nf_total,
                         P.status))
           continue;
-        const ModeInfo M = P.modes[R.mode];
+        const ModeInfo M = P.modes[(PREC != 0 && BPL >= 2) ? S.ent.smode[e] : R.mode];
         // a5 for the whole entry where one segment holds all its tile bins (FP32-path
         // kernels, found in the setup step above; in the FP64 kernel the per-bin integer
         // search overlaps the FP64 pipe for free)
-        const int s_uni = PREC != 0 ? S.suni[e] : -1;
+        const int s_uni = PREC != 0 ? S.ent.suni[e] : -1;
         if constexpr (PREC == 0) {
           // h+ += alpha Z~, hx += i beta Z~ (conjugates on the negative branch).  The
           // amplitude record carries the factor scale (alpha or beta, the larger in
