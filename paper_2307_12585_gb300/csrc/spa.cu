@@ -359,6 +359,11 @@ __device__ __forceinline__ bool body_mixed(const SegCore& C, const SegAmp32& Am,
 #ifndef EMRI_FD_SPA_MINB
 #define EMRI_FD_SPA_MINB 4
 #endif
+// and the standard FP64X kernel (five CTAs: 51 registers; 3% faster than four on the 2-yr,
+// 2000-mode workload at 32-bin tiles, where four leave its 63 registers unspilled)
+#ifndef EMRI_FD_SPAX_MINB
+#define EMRI_FD_SPAX_MINB 5
+#endif
 // and the standard-SPA FP64 kernel (three CTAs of 256 threads: 80 registers, a few
 // spilled; 1.4% faster than two CTAs at 128 registers on the 2-yr, 2000-mode
 // workload).  The extended form's FP64 kernel keeps two.
@@ -412,7 +417,8 @@ constexpr int kBackPerFront = 8;   // back-of-queue (empty) tiles a CTA may take
 // same for all members.
 template <int BPL, int PREC, bool EXT, int CL>
 __global__ void __launch_bounds__(kThreads, PREC == 0 ? (EXT ? EMRI_FD_SPA64_EXT_MINB : EMRI_FD_SPA64_MINB)
-                                                      : EMRI_FD_SPA_MINB) k_spa(SpaParams P) {
+                                                      : (PREC == 2 && !EXT ? EMRI_FD_SPAX_MINB : EMRI_FD_SPA_MINB))
+    k_spa(SpaParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<BPL, PREC>& S = *reinterpret_cast<Smem<BPL, PREC>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
