@@ -244,7 +244,7 @@ FORM_TILE = {"fp64x": 32, "mixed": 64}
 DTYPES = {"fp64": "f64", "fp64x": "f32x2+i64 (double-float, FP64-accurate)", "mixed": "f64+f32"}
 # DRAM bytes (read + write) of one k_spa<4,0,0> launch (FP64, standard SPA, 128-bin tiles) on
 # this workload, from one ncu capture of the kernel as it stands
-TRAFFIC_FP64_SPA = 102.114560e6 + 66.614016e6
+TRAFFIC_FP64_SPA = 102.028288e6 + 66.534400e6
 
 
 def base_line(args, world, metric, value, unit, ms, workload, extra=None):
